@@ -1,0 +1,142 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds geometry and density generators only: none of the method's
+arithmetic (no kernels, expansions, trees or lists). Every generator draws from
+numpy's PCG64 with an explicit seed, in a fixed order, so both sides see the
+same bits.
+
+Families (they stand in for the paper's complexified wobbly curve/surface of
+Sec. 7.1, Eqs. wobble_2D_cplx / complex_wobble, whose discretisations need
+external packages):
+
+* ``curve2d``: points on the curve t -> (t, h*exp(-t^2)), t uniform, with the
+  x1 coordinate complexified by phi(t) = s*sign(t)*max(|t|-t_flat, 0)
+  (Lipschitz constant s). Normals are (gamma_2'(t), -gamma_1'(t)) of the
+  complexified curve, unnormalised (Sec. 2.1 double layer, read for complex
+  points as a caller-supplied complex normal).
+* ``surface3d``: (x, y) from the Halton sequence (bases 2, 3) scaled to a
+  square, z = a*exp(-(x^2+y^2)/w^2), imaginary part
+  s*max(rho-rho0, 0)*(x, y)/rho in (x1, x2) and 0 in x3.
+* ``densities``: i.i.d. complex Gaussians (real and imaginary N(0,1)).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["curve2d", "surface3d", "densities", "halton", "Geometry",
+           "config1", "config2", "config3"]
+
+
+class Geometry:
+    """Points (and optional normals) as real/imaginary [n][dim] float64 arrays."""
+
+    def __init__(self, re, im, nrm_re=None, nrm_im=None, meta=None):
+        self.re = np.ascontiguousarray(re, dtype=np.float64)
+        self.im = np.ascontiguousarray(im, dtype=np.float64)
+        self.nrm_re = None if nrm_re is None else np.ascontiguousarray(nrm_re, dtype=np.float64)
+        self.nrm_im = None if nrm_im is None else np.ascontiguousarray(nrm_im, dtype=np.float64)
+        self.meta = dict(meta or {})
+
+    @property
+    def n(self):
+        return self.re.shape[0]
+
+    @property
+    def dim(self):
+        return self.re.shape[1]
+
+    def subset(self, idx):
+        idx = np.asarray(idx)
+        return Geometry(self.re[idx], self.im[idx],
+                        None if self.nrm_re is None else self.nrm_re[idx],
+                        None if self.nrm_im is None else self.nrm_im[idx],
+                        self.meta)
+
+
+def curve2d(n, seed=0, t_half=10.0, height=0.3, slope=0.5, t_flat=4.0,
+            random_height=None):
+    """Complexified bump curve in C x R.
+
+    ``random_height=(lo, hi)`` draws the bump height once, before the t's.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if random_height is not None:
+        height = float(rng.uniform(random_height[0], random_height[1]))
+    t = rng.uniform(-t_half, t_half, size=n)
+    g2 = height * np.exp(-t * t)
+    re = np.stack([t, g2], axis=1)
+    phi = slope * np.sign(t) * np.maximum(np.abs(t) - t_flat, 0.0)
+    im = np.stack([phi, np.zeros_like(t)], axis=1)
+    dphi = slope * (np.abs(t) > t_flat).astype(np.float64)
+    # gamma' = (1 + i phi', -2 t h e^{-t^2}); normal = (gamma_2', -gamma_1')
+    nrm_re = np.stack([-2.0 * t * g2, -np.ones_like(t)], axis=1)
+    nrm_im = np.stack([np.zeros_like(t), -dphi], axis=1)
+    return Geometry(re, im, nrm_re, nrm_im,
+                    dict(family="curve2d", n=n, seed=seed, t_half=t_half,
+                         height=height, slope=slope, t_flat=t_flat))
+
+
+def halton(n, base, start=1):
+    """Radical-inverse (van der Corput) sequence in `base` for indices start..start+n-1."""
+    idx = np.arange(start, start + n, dtype=np.int64)
+    out = np.zeros(n, dtype=np.float64)
+    f = 1.0
+    i = idx.copy()
+    while np.any(i > 0):
+        f /= base
+        out += f * (i % base)
+        i //= base
+    return out
+
+
+def surface3d(n, seed=0, half=20.0, amp=0.5, width=1.0, slope=0.4, rho0=6.0,
+              random_shape=False):
+    """Complexified plane with a Gaussian bump in C^2 x R.
+
+    ``random_shape`` draws width ~ U[0.5, 3] and slope ~ U[0.2, 0.8] from the seed.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if random_shape:
+        width = float(rng.uniform(0.5, 3.0))
+        slope = float(rng.uniform(0.2, 0.8))
+    x = (2.0 * halton(n, 2) - 1.0) * half
+    y = (2.0 * halton(n, 3) - 1.0) * half
+    z = amp * np.exp(-(x * x + y * y) / (width * width))
+    rho = np.sqrt(x * x + y * y)
+    fac = np.where(rho > 0, slope * np.maximum(rho - rho0, 0.0) / np.where(rho > 0, rho, 1.0), 0.0)
+    re = np.stack([x, y, z], axis=1)
+    im = np.stack([fac * x, fac * y, np.zeros_like(x)], axis=1)
+    # normal of the real graph z(x, y), continued: (-z_x, -z_y, 1); the
+    # complexification leaves x3 real, so the normal is kept real here.
+    zx = -2.0 * x / (width * width) * z
+    zy = -2.0 * y / (width * width) * z
+    nrm_re = np.stack([-zx, -zy, np.ones_like(x)], axis=1)
+    nrm_im = np.zeros_like(nrm_re)
+    return Geometry(re, im, nrm_re, nrm_im,
+                    dict(family="surface3d", n=n, seed=seed, half=half,
+                         amp=amp, width=width, slope=slope, rho0=rho0))
+
+
+def densities(n, seed=0, nrhs=1, ncomp=1):
+    """Complex Gaussian densities, shape [nrhs][ncomp][n], complex128."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = rng.standard_normal((nrhs, ncomp, n, 2))
+    return (a[..., 0] + 1j * a[..., 1]).astype(np.complex128)
+
+
+# ---- the named workloads -------------------------------------------------
+
+def config1(n=4000, seed=0):
+    """2D Laplace SLP workload: t in [-10, 10], bump 0.3, slope 0.5."""
+    return curve2d(n, seed=seed, t_half=10.0, height=0.3, slope=0.5, t_flat=4.0)
+
+
+def config2(n=100000, seed=0):
+    """2D Helmholtz SLP+DLP workload: t in [-40, 40], bump height ~ U[0.3, 1]."""
+    return curve2d(n, seed=seed, t_half=40.0, slope=0.5, t_flat=4.0,
+                   random_height=(0.3, 1.0))
+
+
+def config3(n=1000000, seed=0):
+    """3D workload: complexified plane with bump, Halton points in [-20, 20]^2."""
+    return surface3d(n, seed=seed, half=20.0, amp=0.5, width=1.0, slope=0.4, rho0=6.0)
