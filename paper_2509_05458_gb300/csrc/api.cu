@@ -1,0 +1,491 @@
+// The C ABI (include/cfmm.h): argument checking, host/device staging, plan
+// life cycle, error reporting, and the host-side tables (Gauss-Laguerre rule
+// by Golub-Welsch).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "cfmm_special.cuh"
+#include "kernels.cuh"
+
+namespace cfmm {
+
+static thread_local int g_status = 0;
+static thread_local std::string g_msg;
+
+void set_error(int status, const std::string& msg) {
+    g_status = status;
+    g_msg = msg;
+}
+
+std::atomic<int64_t>& launch_counter() {
+    static std::atomic<int64_t> c{0};
+    return c;
+}
+
+// ---- Gauss-Laguerre rules (generalized, alpha = -1/2 and +1/2) ----------
+// Golub-Welsch: the nodes are the eigenvalues of the symmetric tridiagonal
+// Jacobi matrix of the monic Laguerre recurrence (diagonal 2i+alpha+1,
+// off-diagonal sqrt(i (i+alpha))), the weights Gamma(alpha+1) times the
+// squared first components of the normalised eigenvectors. The eigenproblem
+// is solved by implicit QL iterations with Wilkinson shifts, tracking only the
+// first row of the eigenvector matrix.
+static void gauss_laguerre(double alpha, int n, double* x, double* w) {
+    std::vector<double> d(n), e(n, 0.0), z(n, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = 2.0 * i + alpha + 1.0;
+    for (int i = 1; i < n; ++i) e[i - 1] = std::sqrt(i * (i + alpha));
+    z[0] = 1.0;
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter < 200; ++iter) {
+            int m = l;
+            for (; m < n - 1; ++m) {
+                double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-17 * dd) break;
+            }
+            if (m == l) break;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = m - 1;
+            for (; i >= l; --i) {
+                double f = s * e[i], b = c * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                double zf = z[i + 1];
+                z[i + 1] = s * z[i] + c * zf;
+                z[i] = c * z[i] - s * zf;
+            }
+            if (r == 0.0 && i >= l) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+        }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
+    double g0 = std::tgamma(alpha + 1.0);
+    for (int i = 0; i < n; ++i) {
+        x[i] = d[idx[i]];
+        w[i] = g0 * z[idx[i]] * z[idx[i]];
+    }
+}
+
+const LagRule& host_lag_rule() {
+    static LagRule R;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        gauss_laguerre(-0.5, kLagNodes, R.x[0], R.w[0]);
+        gauss_laguerre(0.5, kLagNodes, R.x[1], R.w[1]);
+    });
+    return R;
+}
+
+void ensure_device_tables() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    CFMM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (done[dev]) return;
+    host_lag_rule();
+    upload_lag_rule_p2p();
+    upload_lag_rule_fmm2d();
+    done[dev] = 1;
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy a caller array (host or device) of `count` doubles into a device buffer
+static void stage_in(DevBuf<double>& dst, const double* src, size_t count, cudaStream_t st) {
+    dst.alloc(count);
+    CFMM_CUDA(cudaMemcpyAsync(dst.get(), src, count * sizeof(double),
+                              is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+}
+
+template <class F>
+static int guarded(F f) {
+    try {
+        f();
+        return 0;
+    } catch (const Error& e) {
+        set_error(e.status, e.msg);
+        return e.status;
+    } catch (const std::exception& e) {
+        set_error(CFMM_ECUDA, e.what());
+        return CFMM_ECUDA;
+    }
+}
+
+// ---- apply-path helpers (permutation of densities and results) -----------
+__global__ void k_permute_dens(const cd* __restrict__ dens, const int* __restrict__ perm, int64_t n, int nrhs,
+                               int ncomp, int comp, cd* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    if (i >= n) return;
+    out[(int64_t)r * n + i] = dens[((int64_t)r * ncomp + comp) * n + perm[i]];
+}
+
+__global__ void k_unpermute(const cd* __restrict__ us, const int* __restrict__ perm, int64_t n, cd scale,
+                            cd* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    if (i >= n) return;
+    cd v = us[(int64_t)r * n + i];
+    out[(int64_t)r * n + perm[i]] = v * scale;
+}
+
+static cd green_scale(int dim, int ker) {
+    const double pi = 3.14159265358979323846;
+    if (dim == 2 && ker == CFMM_LAPLACE) return cd{-1.0 / (2.0 * pi), 0.0};
+    if (dim == 2) return cd{0.0, 0.25};
+    return cd{1.0 / (4.0 * pi), 0.0};
+}
+
+static void record(cfmm_plan_s* P, int i) {
+    if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev[i], P->stream));
+}
+
+// the full apply on device buffers (densities [nrhs][ncomp][n], out [nrhs][n])
+static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
+    cudaStream_t st = P->stream;
+    int64_t n = P->n;
+    int ncomp = (P->slp ? 1 : 0) + (P->dlp ? 1 : 0);
+    if (P->ws_nrhs < nrhs) {
+        P->dens_s.alloc((size_t)n * nrhs * ncomp);
+        P->out_s.alloc((size_t)n * nrhs);
+        P->ws_nrhs = nrhs;
+    }
+    cd* sg = P->slp ? P->dens_s.get() : nullptr;
+    cd* ta = P->dlp ? P->dens_s.get() + (P->slp ? (int64_t)n * nrhs : 0) : nullptr;
+    record(P, 0);
+    dim3 g((unsigned)((n + 255) / 256), nrhs);
+    int comp = 0;
+    if (P->slp) {
+        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, nrhs, ncomp, comp++, sg);
+        CFMM_LAUNCHED();
+    }
+    if (P->dlp) {
+        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, nrhs, ncomp, comp++, ta);
+        CFMM_LAUNCHED();
+    }
+    record(P, 1);
+    if (P->dim == 2) {
+        fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
+    } else {
+        // 3D: near field over List 1 only when the tree is a single leaf
+        CFMM_REQUIRE(P->tree.nboxes == 1, CFMM_EUNSUPPORTED, "3D FMM translations are not built yet");
+        KParams K{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->xr.get(), P->xi.get(), n, n,
+                  sg, ta, n, P->slp, P->dlp, P->kappa};
+        for (int i = 2; i <= 7; ++i) record(P, i);
+        launch_p2p(P->dim, P->kernel, K, P->tree.d_leaf_boxes.get(), P->tree.nleaves, P->tree.start.get(),
+                   P->tree.end.get(), P->tree.loff[0].get(), P->tree.lent[0].get(), P->out_s.get(), nrhs, false, st);
+    }
+    record(P, 8);
+    cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
+    k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, scale, out);
+    CFMM_LAUNCHED();
+    record(P, 9);
+    if (P->timing) {
+        CFMM_CUDA(cudaEventSynchronize(P->ev[9]));
+        for (int i = 0; i < 9; ++i) {
+            float ms = 0.f;
+            CFMM_CUDA(cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]));
+            P->step_ms[i] = ms;
+        }
+    }
+}
+
+static void destroy_plan(cfmm_plan_s* P) {
+    if (!P) return;
+    fmm2d_release(P);
+    for (auto& e : P->ev)
+        if (e) cudaEventDestroy(e);
+    delete P;
+}
+
+}  // namespace cfmm
+
+using namespace cfmm;
+
+extern "C" {
+
+int cfmm_last_status(void) { return g_status; }
+const char* cfmm_last_error(void) { return g_msg.c_str(); }
+const char* cfmm_version(void) { return "cfmm-gb300 0.1 (sm_103a)"; }
+int64_t cfmm_launch_count(void) { return launch_counter().load(); }
+
+cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
+                         const double* nrm_re, const double* nrm_im, int64_t n, const cfmm_opts* opts) {
+    cfmm_plan_s* P = nullptr;
+    int rc = guarded([&] {
+        CFMM_REQUIRE(dim == 2 || dim == 3, CFMM_EINVAL, "dim must be 2 or 3");
+        int ker = kernel & 0xF;
+        CFMM_REQUIRE(ker == CFMM_LAPLACE || ker == CFMM_HELMHOLTZ, CFMM_EINVAL, "kernel must be LAPLACE or HELMHOLTZ");
+        CFMM_REQUIRE((kernel & ~(0xF | CFMM_SLP | CFMM_DLP | CFMM_GREEN_SCALE)) == 0, CFMM_EINVAL, "unknown kernel flags");
+        CFMM_REQUIRE(ker == CFMM_LAPLACE || (std::isfinite(k) && k > 0.0), CFMM_EINVAL, "Helmholtz needs k > 0");
+        CFMM_REQUIRE(std::isfinite(eps) && eps >= 1e-15 && eps <= 0.1, CFMM_EINVAL, "eps must be in [1e-15, 0.1]");
+        CFMM_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), CFMM_EINVAL, "n must be in [1, 2^31)");
+        CFMM_REQUIRE(pts_re && pts_im, CFMM_EINVAL, "points are required");
+        bool dlp = (kernel & CFMM_DLP) != 0;
+        bool slp = (kernel & CFMM_SLP) != 0 || !dlp;
+        CFMM_REQUIRE(!dlp || (nrm_re && nrm_im), CFMM_EINVAL, "double layer needs normals");
+        cfmm_opts o{};
+        if (opts) o = *opts;
+        int leaf = o.leaf_size > 0 ? o.leaf_size : 64;
+        int sep = o.sep > 0 ? o.sep : 1;
+        CFMM_REQUIRE(leaf <= 4096, CFMM_EINVAL, "leaf_size must be <= 4096");
+        CFMM_REQUIRE(sep <= 3, CFMM_EINVAL, "sep must be 1, 2 or 3");
+        CFMM_REQUIRE(o.precision >= 0 && o.precision <= 2, CFMM_EINVAL, "bad precision mode");
+        P = new cfmm_plan_s();
+        P->dim = dim;
+        P->kernel = ker;
+        P->flags = kernel;
+        P->slp = slp;
+        P->dlp = dlp;
+        P->green = (kernel & CFMM_GREEN_SCALE) != 0;
+        P->kappa = ker == CFMM_HELMHOLTZ ? k : 0.0;
+        P->eps = eps;
+        P->n = n;
+        P->leaf_size = leaf;
+        P->sep = sep;
+        P->precision = o.precision == CFMM_AUTO ? (eps >= 1e-5 ? CFMM_MIXED : CFMM_FP64) : o.precision;
+        P->stream = (cudaStream_t)o.stream;
+        CFMM_CUDA(cudaGetDevice(&P->device));
+        ensure_device_tables();
+        for (auto& e : P->ev) CFMM_CUDA(cudaEventCreate(&e));
+        DevBuf<double> re, im, nre, nim;
+        size_t cnt = (size_t)n * dim;
+        stage_in(re, pts_re, cnt, P->stream);
+        stage_in(im, pts_im, cnt, P->stream);
+        if (dlp) {
+            stage_in(nre, nrm_re, cnt, P->stream);
+            stage_in(nim, nrm_im, cnt, P->stream);
+        }
+        build_tree(P, re.get(), im.get(), dlp ? nre.get() : nullptr, dlp ? nim.get() : nullptr, o.top_level);
+        if (dim == 2) fmm2d_setup(P);
+        CFMM_CUDA(cudaStreamSynchronize(P->stream));
+    });
+    if (rc != 0) {
+        destroy_plan(P);
+        return nullptr;
+    }
+    return P;
+}
+
+cfmm_plan_t cfmm_plan(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
+                      int64_t n) {
+    return cfmm_plan_ex(dim, kernel, k, eps, pts_re, pts_im, nullptr, nullptr, n, nullptr);
+}
+
+int cfmm_apply(cfmm_plan_t P, const double* densities, int nrhs, double* out) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        CFMM_REQUIRE(nrhs >= 1, CFMM_EINVAL, "nrhs must be >= 1");
+        CFMM_REQUIRE(densities && out, CFMM_EINVAL, "densities and out are required");
+        int ncomp = (P->slp ? 1 : 0) + (P->dlp ? 1 : 0);
+        size_t din = (size_t)nrhs * ncomp * P->n * 2, dout = (size_t)nrhs * P->n * 2;
+        bool dev_in = is_device_ptr(densities), dev_out = is_device_ptr(out);
+        const cd* d_in = reinterpret_cast<const cd*>(densities);
+        cd* d_out = reinterpret_cast<cd*>(out);
+        DevBuf<double> sin_, sout;
+        if (!dev_in) {
+            P->staging.alloc(din + dout);
+            CFMM_CUDA(cudaMemcpyAsync(P->staging.get(), densities, din * sizeof(double), cudaMemcpyHostToDevice,
+                                      P->stream));
+            d_in = reinterpret_cast<const cd*>(P->staging.get());
+        }
+        if (!dev_out) {
+            P->staging.alloc(din + dout);
+            d_out = reinterpret_cast<cd*>(P->staging.get() + din);
+            if (!dev_in) d_in = reinterpret_cast<const cd*>(P->staging.get());
+        }
+        apply_device(P, d_in, nrhs, d_out);
+        if (!dev_out) {
+            CFMM_CUDA(cudaMemcpyAsync(out, d_out, dout * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+            CFMM_CUDA(cudaStreamSynchronize(P->stream));
+        }
+    });
+}
+
+int cfmm_destroy(cfmm_plan_t P) {
+    return guarded([&] { destroy_plan(P); });
+}
+
+int cfmm_direct(int dim, int kernel, double k, const double* src_re, const double* src_im, const double* nrm_re,
+                const double* nrm_im, int64_t m, const double* trg_re, const double* trg_im, int64_t n,
+                const double* densities, int nrhs, double* out, int precision, void* stream) {
+    return guarded([&] {
+        CFMM_REQUIRE(dim == 2 || dim == 3, CFMM_EINVAL, "dim must be 2 or 3");
+        int ker = kernel & 0xF;
+        CFMM_REQUIRE(ker == CFMM_LAPLACE || ker == CFMM_HELMHOLTZ, CFMM_EINVAL, "bad kernel");
+        CFMM_REQUIRE(ker == CFMM_LAPLACE || (std::isfinite(k) && k > 0.0), CFMM_EINVAL, "Helmholtz needs k > 0");
+        CFMM_REQUIRE(m >= 1 && n >= 1 && nrhs >= 1, CFMM_EINVAL, "sizes must be positive");
+        CFMM_REQUIRE(precision == CFMM_FP64, CFMM_EUNSUPPORTED, "direct sum: only FP64 is built");
+        bool dlp = (kernel & CFMM_DLP) != 0;
+        bool slp = (kernel & CFMM_SLP) != 0 || !dlp;
+        CFMM_REQUIRE(!dlp || (nrm_re && nrm_im), CFMM_EINVAL, "double layer needs normals");
+        CFMM_REQUIRE(is_device_ptr(src_re) && is_device_ptr(trg_re) && is_device_ptr(densities) &&
+                         is_device_ptr(out),
+                     CFMM_EINVAL, "cfmm_direct takes device pointers");
+        ensure_device_tables();
+        cudaStream_t st = (cudaStream_t)stream;
+        // SoA copies of the [n][dim] inputs
+        auto soa = [&](DevBuf<double>& dst, const double* src, int64_t cnt) {
+            std::vector<double> tmp;
+            dst.alloc((size_t)cnt * dim);
+            // transpose on device through a small kernel-free path: 2D copy
+            CFMM_CUDA(cudaMemcpy2DAsync(dst.get(), sizeof(double), src, dim * sizeof(double), sizeof(double), cnt,
+                                        cudaMemcpyDeviceToDevice, st));
+            for (int a = 1; a < dim; ++a)
+                CFMM_CUDA(cudaMemcpy2DAsync(dst.get() + a * cnt, sizeof(double), src + a, dim * sizeof(double),
+                                            sizeof(double), cnt, cudaMemcpyDeviceToDevice, st));
+        };
+        DevBuf<double> sr, si, nr, ni, tr, ti;
+        soa(sr, src_re, m);
+        soa(si, src_im, m);
+        soa(tr, trg_re, n);
+        soa(ti, trg_im, n);
+        if (dlp) {
+            soa(nr, nrm_re, m);
+            soa(ni, nrm_im, m);
+        }
+        int ncomp = (slp ? 1 : 0) + (dlp ? 1 : 0);
+        // densities [nrhs][ncomp][m]: sigma = comp 0, tau = last comp; stride between rhs = ncomp*m
+        const cd* d = reinterpret_cast<const cd*>(densities);
+        KParams K{sr.get(), si.get(), dlp ? nr.get() : nullptr, dlp ? ni.get() : nullptr, tr.get(), ti.get(), m, n,
+                  slp ? d : nullptr, dlp ? d + (slp ? m : 0) : nullptr, ncomp * m, slp, dlp, k};
+        launch_direct(dim, ker, K, reinterpret_cast<cd*>(out), nrhs, st);
+        if (kernel & CFMM_GREEN_SCALE) {
+            DevBuf<int> id;
+            std::vector<int> h(n);
+            for (int64_t i = 0; i < n; ++i) h[i] = (int)i;
+            id.alloc(n);
+            CFMM_CUDA(cudaMemcpyAsync(id.get(), h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+            DevBuf<cd> tmp;
+            tmp.alloc((size_t)n * nrhs);
+            CFMM_CUDA(cudaMemcpyAsync(tmp.get(), out, sizeof(cd) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            dim3 g((unsigned)((n + 255) / 256), nrhs);
+            k_unpermute<<<g, 256, 0, st>>>(tmp.get(), id.get(), n, green_scale(dim, ker), reinterpret_cast<cd*>(out));
+            CFMM_LAUNCHED();
+            CFMM_CUDA(cudaStreamSynchronize(st));
+        }
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int cfmm_plan_get_info(cfmm_plan_t P, cfmm_plan_info* info) {
+    return guarded([&] {
+        CFMM_REQUIRE(P && info, CFMM_EINVAL, "null argument");
+        memset(info, 0, sizeof(*info));
+        info->dim = P->dim;
+        info->kernel = P->flags;
+        info->sep = P->sep;
+        info->leaf_size = P->leaf_size;
+        info->precision = P->precision;
+        info->nlevels = P->tree.nlevels;
+        info->nboxes = P->tree.nboxes;
+        info->nleaves = P->tree.nleaves;
+        info->l0 = P->tree.l0;
+        info->n = P->n;
+        for (int w = 0; w < 4; ++w) info->list_len[w] = P->tree.llen[w];
+        info->p2p_pairs = P->p2p_pairs;
+        info->m2l_pairs = P->m2l_pairs;
+        for (int d = 0; d < 3; ++d) info->root_lo[d] = P->lo[d];
+        info->root_width = P->W;
+    });
+}
+
+int cfmm_plan_get_orders(cfmm_plan_t P, int* p, int nlevels) {
+    return guarded([&] {
+        CFMM_REQUIRE(P && p, CFMM_EINVAL, "null argument");
+        for (int i = 0; i < nlevels && i < (int)P->P.size(); ++i) p[i] = P->P[i];
+    });
+}
+
+int cfmm_plan_export_tree(cfmm_plan_t P, int64_t* perm, uint64_t* keys, int32_t* box_level, uint64_t* box_prefix,
+                          int32_t* box_start, int32_t* box_end, int32_t* box_leaf, int32_t* box_parent,
+                          double* center_re, double* center_im) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        cudaStream_t st = P->stream;
+        const TreeDev& T = P->tree;
+        int nb = T.nboxes;
+        if (perm) {
+            std::vector<int> h(P->n);
+            CFMM_CUDA(cudaMemcpyAsync(h.data(), P->perm.get(), sizeof(int) * P->n, cudaMemcpyDeviceToHost, st));
+            CFMM_CUDA(cudaStreamSynchronize(st));
+            for (int64_t i = 0; i < P->n; ++i) perm[i] = h[i];
+        }
+        if (keys) CFMM_CUDA(cudaMemcpyAsync(keys, P->keys.get(), sizeof(uint64_t) * P->n, cudaMemcpyDeviceToHost, st));
+        if (box_level) CFMM_CUDA(cudaMemcpyAsync(box_level, T.level.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        if (box_prefix) CFMM_CUDA(cudaMemcpyAsync(box_prefix, T.prefix.get(), sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, st));
+        if (box_start) CFMM_CUDA(cudaMemcpyAsync(box_start, T.start.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        if (box_end) CFMM_CUDA(cudaMemcpyAsync(box_end, T.end.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        if (box_leaf) CFMM_CUDA(cudaMemcpyAsync(box_leaf, T.leaf.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        if (box_parent) CFMM_CUDA(cudaMemcpyAsync(box_parent, T.parent.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        if (center_re) CFMM_CUDA(cudaMemcpyAsync(center_re, T.cen_re.get(), sizeof(double) * nb * P->dim, cudaMemcpyDeviceToHost, st));
+        if (center_im) CFMM_CUDA(cudaMemcpyAsync(center_im, T.cen_im.get(), sizeof(double) * nb * P->dim, cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int cfmm_plan_export_list(cfmm_plan_t P, int which, int64_t* offsets, int32_t* entries) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        CFMM_REQUIRE(which >= 1 && which <= 4, CFMM_EINVAL, "which must be 1..4");
+        const TreeDev& T = P->tree;
+        int w = which - 1, nb = T.nboxes;
+        cudaStream_t st = P->stream;
+        if (offsets) {
+            std::vector<int> h(nb + 1);
+            CFMM_CUDA(cudaMemcpyAsync(h.data(), T.loff[w].get(), sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, st));
+            CFMM_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i <= nb; ++i) offsets[i] = h[i];
+        }
+        if (entries && T.llen[w] > 0)
+            CFMM_CUDA(cudaMemcpyAsync(entries, T.lent[w].get(), sizeof(int) * T.llen[w], cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int cfmm_plan_set_timing(cfmm_plan_t P, int on) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        P->timing = on != 0;
+    });
+}
+
+int cfmm_plan_timings(cfmm_plan_t P, double* t, int nsteps) {
+    int rc = guarded([&] {
+        CFMM_REQUIRE(P && t, CFMM_EINVAL, "null argument");
+        for (int i = 0; i < nsteps && i < 9; ++i) t[i] = P->step_ms[i];
+    });
+    return rc == 0 ? 9 : rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Common definitions of the CUDA path: complex arithmetic, status handling,
+// launch accounting and the plan object.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/cfmm.h"
+
+#define CFMM_HD __host__ __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// complex128 / complex64 value types (interleaved re, im)
+// ---------------------------------------------------------------------------
+struct cd {
+    double x, y;
+};
+struct cf {
+    float x, y;
+};
+
+CFMM_HD cd mk(double a, double b) { return cd{a, b}; }
+CFMM_HD cd operator+(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+CFMM_HD cd operator-(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+CFMM_HD cd operator-(cd a) { return cd{-a.x, -a.y}; }
+CFMM_HD cd operator*(cd a, cd b) { return cd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+CFMM_HD cd operator*(double s, cd a) { return cd{s * a.x, s * a.y}; }
+CFMM_HD cd operator*(cd a, double s) { return cd{s * a.x, s * a.y}; }
+CFMM_HD cd& operator+=(cd& a, cd b) { a.x += b.x; a.y += b.y; return a; }
+CFMM_HD cd& operator-=(cd& a, cd b) { a.x -= b.x; a.y -= b.y; return a; }
+CFMM_HD double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+CFMM_HD cd conjg(cd a) { return cd{a.x, -a.y}; }
+CFMM_HD cd mul_i(cd a) { return cd{-a.y, a.x}; }   // i * a
+// a / b with scaling against overflow (Smith's method)
+CFMM_HD cd operator/(cd a, cd b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, den = b.x + b.y * r;
+        return cd{(a.x + a.y * r) / den, (a.y - a.x * r) / den};
+    } else {
+        double r = b.x / b.y, den = b.x * r + b.y;
+        return cd{(a.x * r + a.y) / den, (a.y * r - a.x) / den};
+    }
+}
+CFMM_HD cd operator/(cd a, double s) { return cd{a.x / s, a.y / s}; }
+CFMM_HD cd cinv(cd b) { return cd{1.0, 0.0} / b; }
+
+CFMM_HD cf mkf(float a, float b) { return cf{a, b}; }
+CFMM_HD cf operator+(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+CFMM_HD cf operator-(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
+CFMM_HD cf operator*(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+CFMM_HD cf operator*(float s, cf a) { return cf{s * a.x, s * a.y}; }
+
+// ---------------------------------------------------------------------------
+// status + launch accounting
+// ---------------------------------------------------------------------------
+namespace cfmm {
+
+void set_error(int status, const std::string& msg);
+std::atomic<int64_t>& launch_counter();
+
+inline void count_launch(int n = 1) { launch_counter().fetch_add(n, std::memory_order_relaxed); }
+
+struct Error {
+    int status;
+    std::string msg;
+};
+
+#define CFMM_CUDA(call)                                                              \
+    do {                                                                             \
+        cudaError_t e__ = (call);                                                    \
+        if (e__ != cudaSuccess) {                                                    \
+            throw ::cfmm::Error{e__ == cudaErrorMemoryAllocation ? CFMM_ENOMEM       \
+                                                                  : CFMM_ECUDA,      \
+                                std::string(#call) + ": " + cudaGetErrorString(e__)}; \
+        }                                                                            \
+    } while (0)
+
+#define CFMM_LAUNCHED()                                                              \
+    do {                                                                             \
+        ::cfmm::count_launch();                                                      \
+        cudaError_t e__ = cudaGetLastError();                                        \
+        if (e__ != cudaSuccess)                                                      \
+            throw ::cfmm::Error{CFMM_ECUDA, std::string("launch: ") + cudaGetErrorString(e__)}; \
+    } while (0)
+
+#define CFMM_REQUIRE(cond, status, msg)                                              \
+    do {                                                                             \
+        if (!(cond)) throw ::cfmm::Error{status, msg};                               \
+    } while (0)
+
+// simple owning device buffer
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        if (count <= n && p) return;
+        release();
+        size_t bytes = (count ? count : 1) * sizeof(T);
+        CFMM_CUDA(cudaMalloc((void**)&p, bytes));
+        n = count;
+    }
+    T* get() const { return p; }
+};
+
+// ---------------------------------------------------------------------------
+// constants shared by host and device code of this library
+// ---------------------------------------------------------------------------
+constexpr int kMaxDim = 3;
+constexpr int kLagNodes = 24;       // Gauss-Laguerre nodes for Hankel functions
+constexpr double kHankelSeriesMax = 6.0;  // |z| at or below: ascending series
+
+// Gauss-Laguerre rules for weights u^{-1/2} e^{-u} (rule 0) and u^{1/2} e^{-u}
+// (rule 1), built on the host at library load (Golub-Welsch) and copied to
+// device constant memory.
+struct LagRule {
+    double x[2][kLagNodes];
+    double w[2][kLagNodes];
+};
+const LagRule& host_lag_rule();
+void ensure_device_tables();   // per device, idempotent
+
+// Tree and list storage of a plan (device pointers unless noted).
+struct TreeDev {
+    int nboxes = 0, nlevels = 0, nleaves = 0, l0 = 1;
+    std::vector<int> level_off;     // host copy [nlevels+1]
+    DevBuf<int> d_level_off;
+    DevBuf<int> level, start, end, parent, cbeg, cend, leaf;
+    DevBuf<uint64_t> prefix;
+    DevBuf<double> cen_re, cen_im;  // [nboxes][dim]
+    DevBuf<int> loff[4];            // CSR offsets [nboxes+1]
+    DevBuf<int> lent[4];            // CSR entries
+    int64_t llen[4] = {0, 0, 0, 0};
+    std::vector<int> leaf_boxes;    // host: box index of every leaf, Morton order
+    DevBuf<int> d_leaf_boxes;
+};
+
+}  // namespace cfmm
+
+struct cfmm_plan_s {
+    int dim = 2, kernel = 0, flags = 0, sep = 1, leaf_size = 64, precision = 0;
+    bool slp = true, dlp = false, green = false;
+    double kappa = 0.0, eps = 1e-6;
+    int64_t n = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    double lo[3] = {0, 0, 0};
+    double W = 1.0;
+    int B = 31;
+    // sorted geometry (SoA [dim][n])
+    cfmm::DevBuf<double> xr, xi, nr, ni;
+    cfmm::DevBuf<uint64_t> keys;
+    cfmm::DevBuf<int> perm;
+    cfmm::TreeDev tree;
+    std::vector<int> P;              // per level
+    // expansions: per box coefficient offsets (in complex units), levels >= l0
+    std::vector<int64_t> exp_off_h;
+    cfmm::DevBuf<int64_t> exp_off;
+    cfmm::DevBuf<int> box_P;         // P of the box's level
+    int64_t ncoef = 0;               // complex coefficients per rhs per kind
+    int maxP = 0;
+    // workspaces (grown on demand)
+    cfmm::DevBuf<cd> mpole, local, dens_s, out_s;
+    cfmm::DevBuf<double> staging;
+    int ws_nrhs = 0;
+    // diagnostics
+    int64_t p2p_pairs = 0, m2l_pairs = 0;
+    bool timing = false;
+    double step_ms[9] = {0};
+    cudaEvent_t ev[10] = {};
+};

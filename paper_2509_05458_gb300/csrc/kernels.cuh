@@ -1,0 +1,42 @@
+// Launch interfaces of the apply-path kernels (shared by the .cu files).
+#pragma once
+
+#include "cfmm_common.cuh"
+
+namespace cfmm {
+
+// Geometry and densities seen by the point-wise kernels. Points are SoA
+// [dim][n] float64 (sorted order); densities are complex128 with a stride of
+// dens_stride between right-hand sides.
+struct KParams {
+    const double* src_re;
+    const double* src_im;
+    const double* nrm_re;
+    const double* nrm_im;
+    const double* trg_re;
+    const double* trg_im;
+    int64_t n_src, n_trg;
+    const cd* sigma;
+    const cd* tau;
+    int64_t dens_stride;
+    bool slp, dlp;
+    double kappa;
+};
+
+void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
+                const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st);
+void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st);
+
+// tree construction (tree.cu)
+void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,
+                int top_level_opt);
+
+// 2D expansions (fmm2d.cu)
+void fmm2d_setup(cfmm_plan_s* P);
+void fmm2d_release(cfmm_plan_s* P);
+void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+
+void upload_lag_rule_p2p();
+void upload_lag_rule_fmm2d();
+
+}  // namespace cfmm

@@ -1,0 +1,1122 @@
+// Tree on the real parts of the points, level restriction, complexified
+// centres and Lists 1-4 (Sec. 6.1-6.2), built on the GPU.
+//
+// Representation: the tree is the Morton-ordered list of its leaves
+// (level, prefix, [start, end) into the sorted points). Splitting a leaf
+// replaces it by its non-empty children in place (count + scan + emit), so
+// refinement, level restriction and the forced split down to the top
+// expansion level are all "split these leaves" passes. Boxes of every level
+// are then the distinct level-l prefixes of the leaves at level >= l.
+//
+// Conventions shared with the specification of the method:
+//   root square: centre (min+max)/2, width W = max extent * (1 + 2^-20);
+//   q = floor((x - lo)/W * 2^B) clamped, B = 31 (2D) / 21 (3D), computed
+//   with explicitly rounded operations (no contraction);
+//   Morton key: bits of q interleaved, x lowest; stable LSD radix sort;
+//   near(a, b): ||x_a - x_b||_inf <= k/2 (w_a + w_b) in integer arithmetic;
+//   level restriction: no leaf near a box two levels finer;
+//   Lists as in Sec. 6.2 with the top expansion level l0.
+#include <algorithm>
+#include <cmath>
+
+#include "cfmm_common.cuh"
+
+namespace cfmm {
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (any length), returns the total
+// ---------------------------------------------------------------------------
+static constexpr int kScanThreads = 512;
+static constexpr int kScanItems = 4;
+static constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_scan_tile(const int* __restrict__ in, int* __restrict__ out, int n,
+                            int* __restrict__ block_sums) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = xi - x;
+        if (lane == kScanThreads / 32 - 1 && block_sums) block_sums[blockIdx.x] = xi;
+    }
+    __syncthreads();
+    int run = warp_tot[w] + incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ block_off) {
+    int idx = blockIdx.x * kScanTile + threadIdx.x;
+    int add = block_off[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i, idx += kScanThreads)
+        if (idx < n) out[idx] += add;
+}
+
+// exclusive scan in -> out (must not alias); returns the total (synchronises the stream)
+static int64_t scan_exclusive(const int* in, int* out, int n, cudaStream_t st) {
+    if (n <= 0) return 0;
+    int nb = (n + kScanTile - 1) / kScanTile;
+    DevBuf<int> sums, sums_x;
+    sums.alloc(nb);
+    k_scan_tile<<<nb, kScanThreads, 0, st>>>(in, out, n, sums.get());
+    CFMM_LAUNCHED();
+    if (nb > 1) {
+        sums_x.alloc(nb);
+        scan_exclusive(sums.get(), sums_x.get(), nb, st);
+        k_scan_add<<<nb, kScanThreads, 0, st>>>(out, n, sums_x.get());
+        CFMM_LAUNCHED();
+    }
+    // total = last exclusive value + last input
+    int last_out = 0, last_in = 0;
+    CFMM_CUDA(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    return (int64_t)last_out + last_in;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, int32 value), 4-bit digits, stable
+// ---------------------------------------------------------------------------
+static constexpr int kSortThreads = 256;
+static constexpr int kSortItems = 8;                 // chunks per tile
+static constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int n, int shift,
+                            int* __restrict__ hist, int ntiles) {
+    __shared__ int h[16];
+    if (threadIdx.x < 16) h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    for (int c = 0; c < kSortItems; ++c) {
+        int i = base + c * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 15u], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int* __restrict__ vin,
+                               uint64_t* __restrict__ kout, int* __restrict__ vout, int n,
+                               int shift, const int* __restrict__ offs, int ntiles) {
+    __shared__ int run[16];
+    __shared__ int wcnt[kSortThreads / 32][16];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 16) run[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+    int base = blockIdx.x * kSortTile;
+    __syncthreads();
+    for (int c = 0; c < kSortItems; ++c) {
+        int i = base + c * kSortThreads + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        int val = valid ? vin[i] : 0;
+        unsigned dig = valid ? (unsigned)((key >> shift) & 15u) : 16u;
+        unsigned same = __match_any_sync(0xffffffffu, dig);
+        unsigned lt = (1u << lane) - 1u;
+        int rank = __popc(same & lt);
+        if (lane < 16) wcnt[w][lane] = 0;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][dig] = __popc(same);
+        __syncthreads();
+        if (valid) {
+            int pre = run[dig];
+            for (int ww = 0; ww < w; ++ww) pre += wcnt[ww][dig];
+            int pos = pre + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        if (threadIdx.x < 16) {
+            int s = 0;
+            for (int ww = 0; ww < kSortThreads / 32; ++ww) s += wcnt[ww][threadIdx.x];
+            run[threadIdx.x] += s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_iota(int* v, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
+// sorts keys (in place, via ping-pong) with payload; nbits = significant bits
+static void radix_sort(DevBuf<uint64_t>& keys, DevBuf<int>& vals, int n, int nbits, cudaStream_t st) {
+    if (n <= 1) return;
+    DevBuf<uint64_t> k2;
+    DevBuf<int> v2, hist, offs;
+    k2.alloc(n);
+    v2.alloc(n);
+    int ntiles = (n + kSortTile - 1) / kSortTile;
+    hist.alloc(16 * ntiles);
+    offs.alloc(16 * ntiles);
+    uint64_t *ka = keys.get(), *kb = k2.get();
+    int *va = vals.get(), *vb = v2.get();
+    int passes = (nbits + 3) / 4;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 4 * p;
+        k_sort_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist.get(), ntiles);
+        CFMM_LAUNCHED();
+        scan_exclusive(hist.get(), offs.get(), 16 * ntiles, st);
+        k_sort_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs.get(), ntiles);
+        CFMM_LAUNCHED();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys.get()) {
+        CFMM_CUDA(cudaMemcpyAsync(keys.get(), ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(vals.get(), va, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    CFMM_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------
+// bounding box, keys, gather
+// ---------------------------------------------------------------------------
+__global__ void k_bbox(const double* __restrict__ re, int64_t n, int dim, double* __restrict__ part) {
+    // part[blockIdx][2*dim]: min then max per axis
+    __shared__ double smn[256][3], smx[256][3];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int d = 0; d < dim; ++d) {
+            double v = re[i * dim + d];
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        smn[threadIdx.x][d] = mn[d];
+        smx[threadIdx.x][d] = mx[d];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int d = 0; d < 3; ++d) {
+                smn[threadIdx.x][d] = fmin(smn[threadIdx.x][d], smn[threadIdx.x + s][d]);
+                smx[threadIdx.x][d] = fmax(smx[threadIdx.x][d], smx[threadIdx.x + s][d]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < dim; ++d) {
+            part[blockIdx.x * 2 * dim + d] = smn[0][d];
+            part[blockIdx.x * 2 * dim + dim + d] = smx[0][d];
+        }
+}
+
+__global__ void k_nonfinite(const double* __restrict__ a, int64_t m, int* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicOr(flag, 1);
+}
+
+__device__ __forceinline__ uint64_t spread_bits(uint64_t q, int dim, int B) {
+    uint64_t k = 0;
+    for (int b = 0; b < B; ++b) k |= ((q >> b) & 1ull) << (b * dim);
+    return k;
+}
+
+__global__ void k_keys(const double* __restrict__ re, int64_t n, int dim, int B,
+                       double lo0, double lo1, double lo2, double W,
+                       uint64_t* __restrict__ keys, int* __restrict__ idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo[3] = {lo0, lo1, lo2};
+    const double scale = (double)(1ull << B);
+    const double qmax = (double)((1ull << B) - 1ull);
+    uint64_t key = 0;
+    for (int d = 0; d < dim; ++d) {
+        // t = ((x - lo) / W) * 2^B with every operation rounded separately
+        double t = __dmul_rn(__ddiv_rn(__dsub_rn(re[i * dim + d], lo[d]), W), scale);
+        double qf = floor(t);
+        qf = qf < 0.0 ? 0.0 : (qf > qmax ? qmax : qf);
+        key |= spread_bits((uint64_t)qf, dim, B) << d;
+    }
+    keys[i] = key;
+    idx[i] = (int)i;
+}
+
+__global__ void k_gather_soa(const double* __restrict__ aos, const int* __restrict__ perm, int64_t n,
+                             int dim, double* __restrict__ soa) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int d = 0; d < dim; ++d) soa[d * n + i] = aos[j * dim + d];
+}
+
+// ---------------------------------------------------------------------------
+// box coordinates
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+__device__ __forceinline__ void decode(uint64_t p, int m, int dim, int64_t* I) {
+    for (int d = 0; d < dim; ++d) I[d] = 0;
+    for (int b = 0; b < m; ++b)
+        for (int d = 0; d < dim; ++d) I[d] |= (int64_t)((p >> (b * dim + d)) & 1ull) << b;
+}
+
+__device__ __forceinline__ uint64_t encode(const int64_t* I, int m, int dim) {
+    uint64_t p = 0;
+    for (int b = 0; b < m; ++b)
+        for (int d = 0; d < dim; ++d) p |= (uint64_t)((I[d] >> b) & 1) << (b * dim + d);
+    return p;
+}
+
+// range of J at level m near box (l, I) on one axis, clamped to the grid
+__device__ __forceinline__ void near_range(int l, int64_t I, int m, int k, int64_t* jlo, int64_t* jhi) {
+    int f = l > m ? l : m;
+    int64_t sb = 1ll << (f - l), sc = 1ll << (f - m);
+    int64_t c2 = (2 * I + 1) * sb;
+    int64_t lim = (int64_t)k * (sb + sc);
+    int64_t lo = -floordiv(-(c2 - lim - sc), 2 * sc);   // ceil
+    int64_t hi = floordiv(c2 + lim - sc, 2 * sc);
+    int64_t top = (1ll << m) - 1;
+    *jlo = lo < 0 ? 0 : lo;
+    *jhi = hi > top ? top : hi;
+}
+
+__device__ __forceinline__ bool near_boxes(int la, const int64_t* Ia, int lb, const int64_t* Ib, int dim, int k) {
+    int f = la > lb ? la : lb;
+    int64_t sa = 1ll << (f - la), sb = 1ll << (f - lb);
+    int64_t lim = (int64_t)k * (sa + sb);
+    for (int d = 0; d < dim; ++d) {
+        int64_t diff = (2 * Ia[d] + 1) * sa - (2 * Ib[d] + 1) * sb;
+        if (diff > lim || -diff > lim) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// leaves: split passes and level restriction
+// ---------------------------------------------------------------------------
+struct LeafArrays {
+    DevBuf<int> lev, st, en;
+    DevBuf<uint64_t> pre;
+    int n = 0;
+};
+
+__device__ __forceinline__ void child_bounds(const uint64_t* __restrict__ keys, int s, int e, uint64_t p,
+                                             int level, int dim, int B, int* bnd) {
+    // bnd[c] = first index in [s, e) whose level+1 prefix >= (p << dim | c); bnd[2^dim] = e
+    int shift = dim * (B - level - 1);
+    int nc = 1 << dim;
+    for (int c = 0; c < nc; ++c) {
+        uint64_t target = (p << dim) | (uint64_t)c;
+        int lo = s, hi = e;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if ((keys[mid] >> shift) < target) lo = mid + 1;
+            else hi = mid;
+        }
+        bnd[c] = lo;
+    }
+    bnd[nc] = e;
+}
+
+// mode 0: split when count > Ns or level < force; mode 1: split when flag[i]
+__global__ void k_leaf_count(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                             const int* __restrict__ st, const int* __restrict__ en,
+                             const uint64_t* __restrict__ keys, int dim, int B, int Ns, int force,
+                             const int* __restrict__ flag, int* __restrict__ cnt, int* __restrict__ any) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int l = lev[i];
+    bool split = l < B && (flag ? flag[i] != 0 : ((en[i] - st[i]) > Ns || l < force));
+    if (!split) {
+        cnt[i] = 1;
+        return;
+    }
+    atomicOr(any, 1);
+    int bnd[9];
+    child_bounds(keys, st[i], en[i], pre[i], l, dim, B, bnd);
+    int c = 0;
+    for (int j = 0; j < (1 << dim); ++j) c += bnd[j + 1] > bnd[j];
+    cnt[i] = c;
+}
+
+__global__ void k_leaf_emit(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                            const int* __restrict__ st, const int* __restrict__ en,
+                            const uint64_t* __restrict__ keys, int dim, int B, int Ns, int force,
+                            const int* __restrict__ flag, const int* __restrict__ off,
+                            int* __restrict__ olev, uint64_t* __restrict__ opre,
+                            int* __restrict__ ost, int* __restrict__ oen) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int l = lev[i];
+    bool split = l < B && (flag ? flag[i] != 0 : ((en[i] - st[i]) > Ns || l < force));
+    int o = off[i];
+    if (!split) {
+        olev[o] = l;
+        opre[o] = pre[i];
+        ost[o] = st[i];
+        oen[o] = en[i];
+        return;
+    }
+    int bnd[9];
+    child_bounds(keys, st[i], en[i], pre[i], l, dim, B, bnd);
+    for (int j = 0; j < (1 << dim); ++j) {
+        if (bnd[j + 1] > bnd[j]) {
+            olev[o] = l + 1;
+            opre[o] = (pre[i] << dim) | (uint64_t)j;
+            ost[o] = bnd[j];
+            oen[o] = bnd[j + 1];
+            ++o;
+        }
+    }
+}
+
+// box (m, J) exists iff the first leaf starting at or after J's first key lies inside J
+// and is at level >= m
+__device__ __forceinline__ bool box_exists(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                                           int dim, int B, int m, uint64_t q) {
+    int sh = dim * (B - m);
+    uint64_t ks = q << sh, ke = (q + 1) << sh;
+    int lo = 0, hi = nl;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        uint64_t s = pre[mid] << (dim * (B - lev[mid]));
+        if (s < ks) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= nl) return false;
+    uint64_t s = pre[lo] << (dim * (B - lev[lo]));
+    return s < ke && lev[lo] >= m;
+}
+
+__global__ void k_balance_flags(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                                int dim, int B, int k, int maxl, int* __restrict__ flag, int* __restrict__ any) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int l = lev[i];
+    int m = l + 2;
+    int f = 0;
+    if (m <= maxl) {
+        int64_t I[3], lo[3], hi[3];
+        decode(pre[i], l, dim, I);
+        for (int d = 0; d < dim; ++d) near_range(l, I[d], m, k, &lo[d], &hi[d]);
+        int64_t J[3] = {lo[0], lo[1], dim > 2 ? lo[2] : 0};
+        // iterate the window (lexicographic), skipping boxes inside the leaf
+        while (!f) {
+            bool inside = true;
+            for (int d = 0; d < dim; ++d) {
+                int64_t r = J[d] - 4 * I[d];
+                if (r < 0 || r > 3) inside = false;
+            }
+            if (!inside && box_exists(nl, lev, pre, dim, B, m, encode(J, m, dim))) f = 1;
+            int d = 0;
+            for (; d < dim; ++d) {
+                if (J[d] < hi[d]) { ++J[d]; break; }
+                J[d] = lo[d];
+            }
+            if (d == dim) break;
+        }
+    }
+    flag[i] = f;
+    if (f) atomicOr(any, 1);
+}
+
+__global__ void k_leaf_maxlevel(int nl, const int* __restrict__ lev, int* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nl) atomicMax(out, lev[i]);
+}
+
+static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// one split pass; returns true when some leaf was split
+static bool split_pass(LeafArrays& L, const uint64_t* keys, int dim, int B, int Ns, int force,
+                       const int* flag, cudaStream_t st) {
+    int nl = L.n;
+    DevBuf<int> cnt, off, any;
+    cnt.alloc(nl);
+    off.alloc(nl);
+    any.alloc(1);
+    CFMM_CUDA(cudaMemsetAsync(any.get(), 0, sizeof(int), st));
+    k_leaf_count<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(),
+                                                     keys, dim, B, Ns, force, flag, cnt.get(), any.get());
+    CFMM_LAUNCHED();
+    int64_t total = scan_exclusive(cnt.get(), off.get(), nl, st);
+    int h = 0;
+    CFMM_CUDA(cudaMemcpyAsync(&h, any.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    if (!h) return false;
+    LeafArrays N;
+    N.n = (int)total;
+    N.lev.alloc(N.n);
+    N.pre.alloc(N.n);
+    N.st.alloc(N.n);
+    N.en.alloc(N.n);
+    k_leaf_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(), keys,
+                                                    dim, B, Ns, force, flag, off.get(), N.lev.get(), N.pre.get(),
+                                                    N.st.get(), N.en.get());
+    CFMM_LAUNCHED();
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    std::swap(L.lev.p, N.lev.p);
+    std::swap(L.lev.n, N.lev.n);
+    std::swap(L.pre.p, N.pre.p);
+    std::swap(L.pre.n, N.pre.n);
+    std::swap(L.st.p, N.st.p);
+    std::swap(L.st.n, N.st.n);
+    std::swap(L.en.p, N.en.p);
+    std::swap(L.en.n, N.en.n);
+    L.n = N.n;
+    return true;
+}
+
+static int leaf_maxlevel(LeafArrays& L, cudaStream_t st) {
+    DevBuf<int> m;
+    m.alloc(1);
+    CFMM_CUDA(cudaMemsetAsync(m.get(), 0, sizeof(int), st));
+    k_leaf_maxlevel<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.lev.get(), m.get());
+    CFMM_LAUNCHED();
+    int h = 0;
+    CFMM_CUDA(cudaMemcpyAsync(&h, m.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    return h;
+}
+
+static void refine(LeafArrays& L, const uint64_t* keys, int dim, int B, int Ns, int force, cudaStream_t st) {
+    while (split_pass(L, keys, dim, B, Ns, force, nullptr, st)) {
+    }
+}
+
+static void balance(LeafArrays& L, const uint64_t* keys, int dim, int B, int k, cudaStream_t st) {
+    DevBuf<int> flag, any;
+    any.alloc(1);
+    for (;;) {
+        int maxl = leaf_maxlevel(L, st);
+        flag.alloc(L.n);
+        CFMM_CUDA(cudaMemsetAsync(any.get(), 0, sizeof(int), st));
+        k_balance_flags<<<blocks_for(L.n, 128), 128, 0, st>>>(L.n, L.lev.get(), L.pre.get(), dim, B, k, maxl,
+                                                             flag.get(), any.get());
+        CFMM_LAUNCHED();
+        int h = 0;
+        CFMM_CUDA(cudaMemcpyAsync(&h, any.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        if (!h) return;
+        split_pass(L, keys, dim, B, 0, 0, flag.get(), st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// boxes from leaves
+// ---------------------------------------------------------------------------
+__global__ void k_box_flags(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre, int dim,
+                            int m, int* __restrict__ head) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int l = lev[i];
+    bool q = l >= m;
+    bool h = false;
+    if (q) {
+        uint64_t pm = pre[i] >> (dim * (l - m));
+        if (i == 0) h = true;
+        else {
+            int lp = lev[i - 1];
+            h = lp < m || (pre[i - 1] >> (dim * (lp - m))) != pm;
+        }
+    }
+    head[i] = h ? 1 : 0;
+}
+
+__global__ void k_box_emit(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                           const int* __restrict__ st, const int* __restrict__ en, int dim, int m, int base,
+                           const int* __restrict__ head, const int* __restrict__ idx,
+                           int* __restrict__ blevel, uint64_t* __restrict__ bpre, int* __restrict__ bst,
+                           int* __restrict__ ben, int* __restrict__ bleaf, int* __restrict__ leaf_box) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int l = lev[i];
+    if (l < m) return;
+    uint64_t pm = pre[i] >> (dim * (l - m));
+    int b = base + idx[i] + head[i] - 1;
+    if (head[i]) {
+        blevel[b] = m;
+        bpre[b] = pm;
+        bst[b] = st[i];
+        bleaf[b] = (l == m);
+        if (l == m) leaf_box[i] = b;
+    }
+    bool tail;
+    if (i == nl - 1) tail = true;
+    else {
+        int ln = lev[i + 1];
+        tail = ln < m || (pre[i + 1] >> (dim * (ln - m))) != pm;
+    }
+    if (tail) ben[b] = en[i];
+}
+
+__device__ __forceinline__ int find_box(const uint64_t* __restrict__ bpre, const int* __restrict__ loff,
+                                        int nlev, int m, uint64_t q) {
+    if (m < 0 || m >= nlev) return -1;
+    int lo = loff[m], hi = loff[m + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (bpre[mid] < q) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < loff[m + 1] && bpre[lo] == q) return lo;
+    return -1;
+}
+
+__device__ __forceinline__ int lower_box(const uint64_t* __restrict__ bpre, int lo, int hi, uint64_t q) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (bpre[mid] < q) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_box_links(int nb, const int* __restrict__ blevel, const uint64_t* __restrict__ bpre,
+                            const int* __restrict__ loff, int nlev, int dim, int* __restrict__ parent,
+                            int* __restrict__ cbeg, int* __restrict__ cend) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int m = blevel[b];
+    uint64_t p = bpre[b];
+    parent[b] = m > 0 ? find_box(bpre, loff, nlev, m - 1, p >> dim) : -1;
+    if (m + 1 < nlev) {
+        int lo = loff[m + 1], hi = loff[m + 2];
+        cbeg[b] = lower_box(bpre, lo, hi, p << dim);
+        cend[b] = lower_box(bpre, lo, hi, (p + 1) << dim);
+    } else {
+        cbeg[b] = cend[b] = 0;
+    }
+}
+
+// per leaf box: sum / min / max of Im x per axis (one warp per box)
+__global__ void k_leaf_stats(int nb, const int* __restrict__ bleaf, const int* __restrict__ bst,
+                             const int* __restrict__ ben, const double* __restrict__ xi, int64_t n, int dim,
+                             double* __restrict__ sum, double* __restrict__ mn, double* __restrict__ mx) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= nb || !bleaf[warp]) return;
+    int b = warp;
+    for (int d = 0; d < dim; ++d) {
+        double s = 0.0, lo = INFINITY, hi = -INFINITY;
+        for (int i = bst[b] + lane; i < ben[b]; i += 32) {
+            double v = xi[d * n + i];
+            s += v;
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            sum[b * dim + d] = s;
+            mn[b * dim + d] = lo;
+            mx[b * dim + d] = hi;
+        }
+    }
+}
+
+__global__ void k_parent_stats(int lo, int hi, const int* __restrict__ bleaf, const int* __restrict__ cbeg,
+                               const int* __restrict__ cend, int dim, double* __restrict__ sum,
+                               double* __restrict__ mn, double* __restrict__ mx) {
+    int b = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= hi || bleaf[b]) return;
+    for (int d = 0; d < dim; ++d) {
+        double s = 0.0, a = INFINITY, z = -INFINITY;
+        for (int c = cbeg[b]; c < cend[b]; ++c) {
+            s += sum[c * dim + d];
+            a = fmin(a, mn[c * dim + d]);
+            z = fmax(z, mx[c * dim + d]);
+        }
+        sum[b * dim + d] = s;
+        mn[b * dim + d] = a;
+        mx[b * dim + d] = z;
+    }
+}
+
+__global__ void k_centers(int nb, const int* __restrict__ blevel, const uint64_t* __restrict__ bpre,
+                          const int* __restrict__ bst, const int* __restrict__ ben, int dim, double lo0,
+                          double lo1, double lo2, double W, const double* __restrict__ sum,
+                          double* __restrict__ cre, double* __restrict__ cim) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double lo[3] = {lo0, lo1, lo2};
+    int m = blevel[b];
+    int64_t I[3];
+    decode(bpre[b], m, dim, I);
+    double w = ldexp(W, -m);
+    double cnt = (double)(ben[b] - bst[b]);
+    for (int d = 0; d < dim; ++d) {
+        cre[b * dim + d] = lo[d] + ((double)I[d] + 0.5) * w;
+        cim[b * dim + d] = sum[b * dim + d] / cnt;
+    }
+}
+
+// g[m] = max spread over boxes at level m and leaves above m (as uint64 of a non-negative double)
+__global__ void k_level_spread(int nb, const int* __restrict__ blevel, const int* __restrict__ bleaf, int nlev,
+                               int dim, const double* __restrict__ mn, const double* __restrict__ mx,
+                               unsigned long long* __restrict__ g) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double s = 0.0;
+    for (int d = 0; d < dim; ++d) s = fmax(s, mx[b * dim + d] - mn[b * dim + d]);
+    unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+    int m = blevel[b];
+    atomicMax(&g[m], bits);
+    if (bleaf[b])
+        for (int mm = m + 1; mm < nlev; ++mm) atomicMax(&g[mm], bits);
+}
+
+// ---------------------------------------------------------------------------
+// Lists 1-4 (count, then fill, then sort each box's entries)
+// ---------------------------------------------------------------------------
+struct ListCtx {
+    int nb, nlev, dim, k, l0, B;
+    const int* level;
+    const int* leaf;
+    const int* parent;
+    const uint64_t* pre;
+    const int* loff;
+};
+
+template <class Emit>
+__device__ void enumerate_window(const ListCtx& C, int m, const int64_t* lo, const int64_t* hi, Emit emit) {
+    if (m < 0 || m >= C.nlev) return;
+    int64_t J[3] = {lo[0], lo[1], C.dim > 2 ? lo[2] : 0};
+    for (int d = 0; d < C.dim; ++d)
+        if (lo[d] > hi[d]) return;
+    for (;;) {
+        emit(J);
+        int d = 0;
+        for (; d < C.dim; ++d) {
+            if (J[d] < hi[d]) { ++J[d]; break; }
+            J[d] = lo[d];
+        }
+        if (d == C.dim) break;
+    }
+}
+
+// which: 0..3 = List 1..4. out == nullptr: count only.
+__device__ int list_entries(const ListCtx& C, int which, int b, int* out) {
+    int m0 = C.level[b];
+    if (m0 < C.l0) return 0;
+    int dim = C.dim, k = C.k;
+    int64_t I[3];
+    decode(C.pre[b], m0, dim, I);
+    int cnt = 0;
+    if (which == 0) {
+        if (!C.leaf[b]) return 0;
+        for (int m = m0 - 1; m <= m0 + 1; ++m) {
+            if (m < 0 || m >= C.nlev) continue;
+            int64_t lo[3], hi[3];
+            for (int d = 0; d < dim; ++d) near_range(m0, I[d], m, k, &lo[d], &hi[d]);
+            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
+                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
+                if (c >= 0 && C.leaf[c]) {
+                    if (out) out[cnt] = c;
+                    ++cnt;
+                }
+            });
+        }
+    } else if (which == 1) {
+        if (m0 == C.l0) {
+            for (int c = C.loff[m0]; c < C.loff[m0 + 1]; ++c) {
+                int64_t J[3];
+                decode(C.pre[c], m0, dim, J);
+                if (!near_boxes(m0, I, m0, J, dim, k)) {
+                    if (out) out[cnt] = c;
+                    ++cnt;
+                }
+            }
+        } else {
+            int64_t lo[3], hi[3];
+            for (int d = 0; d < dim; ++d) {
+                int64_t ip = I[d] >> 1;
+                lo[d] = 2 * (ip - k);
+                hi[d] = 2 * (ip + k) + 1;
+                int64_t top = (1ll << m0) - 1;
+                lo[d] = lo[d] < 0 ? 0 : lo[d];
+                hi[d] = hi[d] > top ? top : hi[d];
+            }
+            enumerate_window(C, m0, lo, hi, [&](const int64_t* J) {
+                if (near_boxes(m0, I, m0, J, dim, k)) return;
+                int c = find_box(C.pre, C.loff, C.nlev, m0, encode(J, m0, dim));
+                if (c >= 0) {
+                    if (out) out[cnt] = c;
+                    ++cnt;
+                }
+            });
+        }
+    } else if (which == 2) {
+        if (!C.leaf[b]) return 0;
+        for (int m = m0 + 1; m <= m0 + 2; ++m) {
+            if (m >= C.nlev) continue;
+            int64_t lo[3], hi[3];
+            for (int d = 0; d < dim; ++d) {
+                int64_t plo, phi;
+                near_range(m0, I[d], m - 1, k, &plo, &phi);
+                lo[d] = 2 * plo;
+                hi[d] = 2 * phi + 1;
+            }
+            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
+                if (near_boxes(m0, I, m, J, dim, k)) return;
+                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
+                if (c >= 0) {
+                    if (out) out[cnt] = c;
+                    ++cnt;
+                }
+            });
+        }
+    } else {
+        if (m0 < 1) return 0;
+        int64_t Ip[3];
+        for (int d = 0; d < dim; ++d) Ip[d] = I[d] >> 1;
+        for (int m = m0 - 2; m <= m0 - 1; ++m) {
+            if (m < C.l0) continue;
+            int64_t lo[3], hi[3];
+            for (int d = 0; d < dim; ++d) near_range(m0 - 1, Ip[d], m, k, &lo[d], &hi[d]);
+            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
+                if (near_boxes(m0, I, m, J, dim, k)) return;
+                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
+                if (c >= 0 && C.leaf[c]) {
+                    if (out) out[cnt] = c;
+                    ++cnt;
+                }
+            });
+        }
+    }
+    return cnt;
+}
+
+__global__ void k_list_count(ListCtx C, int which, int* __restrict__ cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= C.nb) return;
+    cnt[b] = C.nb == 1 ? (which == 0 ? 1 : 0) : list_entries(C, which, b, nullptr);
+}
+
+__global__ void k_list_fill(ListCtx C, int which, const int* __restrict__ off, int* __restrict__ ent) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= C.nb) return;
+    int* out = ent + off[b];
+    if (C.nb == 1) {
+        if (which == 0) out[0] = 0;
+        return;
+    }
+    int c = list_entries(C, which, b, out);
+    // insertion sort by box index (windows are enumerated in coordinate order)
+    for (int i = 1; i < c; ++i) {
+        int v = out[i], j = i - 1;
+        while (j >= 0 && out[j] > v) {
+            out[j + 1] = out[j];
+            --j;
+        }
+        out[j + 1] = v;
+    }
+}
+
+// P2P work: sum over leaves of n_t * sum_{List 1} n_s
+__global__ void k_p2p_work(int nb, const int* __restrict__ off, const int* __restrict__ ent,
+                           const int* __restrict__ bst, const int* __restrict__ ben,
+                           unsigned long long* __restrict__ acc) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    unsigned long long s = 0;
+    for (int j = off[b]; j < off[b + 1]; ++j) s += (unsigned long long)(ben[ent[j]] - bst[ent[j]]);
+    s *= (unsigned long long)(ben[b] - bst[b]);
+    if (s) atomicAdd(acc, s);
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
+    TreeDev& T = P->tree;
+    int dim = P->dim;
+    int maxl = leaf_maxlevel(L, st);
+    int nl = L.n;
+    DevBuf<int> head, idx, leaf_box;
+    head.alloc(nl);
+    idx.alloc(nl);
+    leaf_box.alloc(nl);
+    std::vector<int> counts(maxl + 1);
+    // pass 1: counts per level
+    for (int m = 0; m <= maxl; ++m) {
+        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), dim, m, head.get());
+        CFMM_LAUNCHED();
+        counts[m] = (int)scan_exclusive(head.get(), idx.get(), nl, st);
+    }
+    T.nlevels = maxl + 1;
+    T.level_off.assign(T.nlevels + 1, 0);
+    for (int m = 0; m <= maxl; ++m) T.level_off[m + 1] = T.level_off[m] + counts[m];
+    T.nboxes = T.level_off[T.nlevels];
+    T.nleaves = nl;
+    int nb = T.nboxes;
+    T.level.alloc(nb);
+    T.prefix.alloc(nb);
+    T.start.alloc(nb);
+    T.end.alloc(nb);
+    T.leaf.alloc(nb);
+    T.parent.alloc(nb);
+    T.cbeg.alloc(nb);
+    T.cend.alloc(nb);
+    for (int m = 0; m <= maxl; ++m) {
+        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), dim, m, head.get());
+        CFMM_LAUNCHED();
+        scan_exclusive(head.get(), idx.get(), nl, st);
+        k_box_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(), dim,
+                                                       m, T.level_off[m], head.get(), idx.get(), T.level.get(),
+                                                       T.prefix.get(), T.start.get(), T.end.get(), T.leaf.get(),
+                                                       leaf_box.get());
+        CFMM_LAUNCHED();
+    }
+    T.d_level_off.alloc(T.nlevels + 1);
+    CFMM_CUDA(cudaMemcpyAsync(T.d_level_off.get(), T.level_off.data(), sizeof(int) * (T.nlevels + 1),
+                              cudaMemcpyHostToDevice, st));
+    k_box_links<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.prefix.get(), T.d_level_off.get(),
+                                                    T.nlevels, dim, T.parent.get(), T.cbeg.get(), T.cend.get());
+    CFMM_LAUNCHED();
+    T.leaf_boxes.resize(nl);
+    CFMM_CUDA(cudaMemcpyAsync(T.leaf_boxes.data(), leaf_box.get(), sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
+    T.d_leaf_boxes.alloc(nl);
+    CFMM_CUDA(cudaMemcpyAsync(T.d_leaf_boxes.get(), leaf_box.get(), sizeof(int) * nl, cudaMemcpyDeviceToDevice, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+}
+
+// per-box Im statistics; fills centres and (optionally) the per-level spread
+static void box_stats(cfmm_plan_s* P, cudaStream_t st, std::vector<double>* spread) {
+    TreeDev& T = P->tree;
+    int dim = P->dim, nb = T.nboxes;
+    DevBuf<double> sum, mn, mx;
+    sum.alloc((size_t)nb * dim);
+    mn.alloc((size_t)nb * dim);
+    mx.alloc((size_t)nb * dim);
+    k_leaf_stats<<<blocks_for((int64_t)nb * 32, 256), 256, 0, st>>>(nb, T.leaf.get(), T.start.get(), T.end.get(),
+                                                                   P->xi.get(), P->n, dim, sum.get(), mn.get(),
+                                                                   mx.get());
+    CFMM_LAUNCHED();
+    for (int m = T.nlevels - 2; m >= 0; --m) {
+        int lo = T.level_off[m], hi = T.level_off[m + 1];
+        k_parent_stats<<<blocks_for(hi - lo, 128), 128, 0, st>>>(lo, hi, T.leaf.get(), T.cbeg.get(), T.cend.get(),
+                                                                dim, sum.get(), mn.get(), mx.get());
+        CFMM_LAUNCHED();
+    }
+    T.cen_re.alloc((size_t)nb * dim);
+    T.cen_im.alloc((size_t)nb * dim);
+    k_centers<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.prefix.get(), T.start.get(), T.end.get(), dim,
+                                                  P->lo[0], P->lo[1], P->lo[2], P->W, sum.get(), T.cen_re.get(),
+                                                  T.cen_im.get());
+    CFMM_LAUNCHED();
+    if (spread) {
+        DevBuf<unsigned long long> g;
+        g.alloc(T.nlevels);
+        CFMM_CUDA(cudaMemsetAsync(g.get(), 0, sizeof(unsigned long long) * T.nlevels, st));
+        k_level_spread<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.leaf.get(), T.nlevels, dim,
+                                                           mn.get(), mx.get(), g.get());
+        CFMM_LAUNCHED();
+        std::vector<unsigned long long> h(T.nlevels);
+        CFMM_CUDA(cudaMemcpyAsync(h.data(), g.get(), sizeof(unsigned long long) * T.nlevels,
+                                  cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        spread->resize(T.nlevels);
+        for (int m = 0; m < T.nlevels; ++m) {
+            double v;
+            memcpy(&v, &h[m], sizeof(double));
+            (*spread)[m] = v;
+        }
+    }
+    CFMM_CUDA(cudaStreamSynchronize(st));
+}
+
+static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
+    TreeDev& T = P->tree;
+    int nb = T.nboxes;
+    ListCtx C{nb, T.nlevels, P->dim, P->sep, T.l0, P->B, T.level.get(), T.leaf.get(), T.parent.get(),
+              T.prefix.get(), T.d_level_off.get()};
+    DevBuf<int> cnt;
+    cnt.alloc(nb);
+    for (int w = 0; w < 4; ++w) {
+        k_list_count<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, cnt.get());
+        CFMM_LAUNCHED();
+        T.loff[w].alloc(nb + 1);
+        int64_t tot = scan_exclusive(cnt.get(), T.loff[w].get(), nb, st);
+        CFMM_REQUIRE(tot < (int64_t)1 << 31, CFMM_EUNSUPPORTED, "interaction list longer than 2^31 entries");
+        int t32 = (int)tot;
+        CFMM_CUDA(cudaMemcpyAsync(T.loff[w].get() + nb, &t32, sizeof(int), cudaMemcpyHostToDevice, st));
+        T.llen[w] = tot;
+        T.lent[w].alloc(tot > 0 ? tot : 1);
+        k_list_fill<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, T.loff[w].get(), T.lent[w].get());
+        CFMM_LAUNCHED();
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    }
+    // work counters
+    DevBuf<unsigned long long> acc;
+    acc.alloc(1);
+    CFMM_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(unsigned long long), st));
+    k_p2p_work<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.loff[0].get(), T.lent[0].get(), T.start.get(),
+                                                   T.end.get(), acc.get());
+    CFMM_LAUNCHED();
+    unsigned long long h = 0;
+    CFMM_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    P->p2p_pairs = (int64_t)h;
+    P->m2l_pairs = T.llen[1];
+}
+
+// Builds the sorted geometry and the tree of a plan. re/im (and nre/nim when
+// not null) are device copies of the caller's [n][dim] arrays.
+void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,
+                int top_level_opt) {
+    cudaStream_t st = P->stream;
+    int dim = P->dim;
+    int64_t n = P->n;
+    // finite check
+    {
+        DevBuf<int> flag;
+        flag.alloc(1);
+        CFMM_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), st));
+        int g = blocks_for(n * dim, 256);
+        g = g > 4096 ? 4096 : g;
+        k_nonfinite<<<g, 256, 0, st>>>(re, n * dim, flag.get());
+        k_nonfinite<<<g, 256, 0, st>>>(im, n * dim, flag.get());
+        ::cfmm::count_launch(2);
+        if (nre) {
+            k_nonfinite<<<g, 256, 0, st>>>(nre, n * dim, flag.get());
+            k_nonfinite<<<g, 256, 0, st>>>(nim, n * dim, flag.get());
+            ::cfmm::count_launch(2);
+        }
+        CFMM_CUDA(cudaGetLastError());
+        int h = 0;
+        CFMM_CUDA(cudaMemcpyAsync(&h, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        CFMM_REQUIRE(h == 0, CFMM_ENONFINITE, "points or normals contain NaN or Inf");
+    }
+    // a1: bounding square (Sec. 6.1)
+    {
+        int nblk = blocks_for(n, 256);
+        nblk = nblk > 1024 ? 1024 : nblk;
+        DevBuf<double> part;
+        part.alloc((size_t)nblk * 2 * dim);
+        k_bbox<<<nblk, 256, 0, st>>>(re, n, dim, part.get());
+        CFMM_LAUNCHED();
+        std::vector<double> h((size_t)nblk * 2 * dim);
+        CFMM_CUDA(cudaMemcpyAsync(h.data(), part.get(), sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        double mn[3], mx[3];
+        for (int d = 0; d < dim; ++d) {
+            mn[d] = INFINITY;
+            mx[d] = -INFINITY;
+        }
+        for (int b = 0; b < nblk; ++b)
+            for (int d = 0; d < dim; ++d) {
+                mn[d] = std::min(mn[d], h[b * 2 * dim + d]);
+                mx[d] = std::max(mx[d], h[b * 2 * dim + dim + d]);
+            }
+        double ext = 0.0;
+        for (int d = 0; d < dim; ++d) ext = std::max(ext, mx[d] - mn[d]);
+        double W = ext * (1.0 + std::ldexp(1.0, -20));
+        if (W == 0.0) W = 1.0;
+        P->W = W;
+        for (int d = 0; d < 3; ++d) P->lo[d] = 0.0;
+        for (int d = 0; d < dim; ++d) {
+            double c = (mn[d] + mx[d]) * 0.5;
+            P->lo[d] = c - W * 0.5;
+        }
+    }
+    // a2: keys, stable radix sort, gather
+    P->B = dim == 2 ? 31 : 21;
+    int B = P->B;
+    P->keys.alloc(n);
+    P->perm.alloc(n);
+    k_keys<<<blocks_for(n, 256), 256, 0, st>>>(re, n, dim, B, P->lo[0], P->lo[1], P->lo[2], P->W, P->keys.get(),
+                                              P->perm.get());
+    CFMM_LAUNCHED();
+    radix_sort(P->keys, P->perm, (int)n, dim * B, st);
+    P->xr.alloc((size_t)n * dim);
+    P->xi.alloc((size_t)n * dim);
+    k_gather_soa<<<blocks_for(n, 256), 256, 0, st>>>(re, P->perm.get(), n, dim, P->xr.get());
+    k_gather_soa<<<blocks_for(n, 256), 256, 0, st>>>(im, P->perm.get(), n, dim, P->xi.get());
+    ::cfmm::count_launch(2);
+    if (nre) {
+        P->nr.alloc((size_t)n * dim);
+        P->ni.alloc((size_t)n * dim);
+        k_gather_soa<<<blocks_for(n, 256), 256, 0, st>>>(nre, P->perm.get(), n, dim, P->nr.get());
+        k_gather_soa<<<blocks_for(n, 256), 256, 0, st>>>(nim, P->perm.get(), n, dim, P->ni.get());
+        ::cfmm::count_launch(2);
+    }
+    CFMM_CUDA(cudaGetLastError());
+    // a3: leaves, level restriction
+    LeafArrays L;
+    L.n = 1;
+    L.lev.alloc(1);
+    L.pre.alloc(1);
+    L.st.alloc(1);
+    L.en.alloc(1);
+    {
+        int z = 0, nn = (int)n;
+        uint64_t zp = 0;
+        CFMM_CUDA(cudaMemcpyAsync(L.lev.get(), &z, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.pre.get(), &zp, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.st.get(), &z, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.en.get(), &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    }
+    int Ns = P->leaf_size;
+    refine(L, P->keys.get(), dim, B, Ns, 0, st);
+    balance(L, P->keys.get(), dim, B, P->sep, st);
+    build_boxes(P, L, st);
+    // a4 + top expansion level
+    std::vector<double> spread;
+    bool helm = P->kernel == CFMM_HELMHOLTZ;
+    box_stats(P, st, (helm && n > Ns && top_level_opt <= 0) ? &spread : nullptr);
+    int l0 = 1;
+    if (n > Ns) {
+        if (top_level_opt > 0) {
+            l0 = top_level_opt;
+        } else if (helm) {
+            double tau = 0.25 * std::log(P->eps / std::ldexp(1.0, -52));
+            int maxl = P->tree.nlevels - 1;
+            l0 = maxl < 1 ? 1 : maxl;
+            for (int m = 1; m <= maxl; ++m) {
+                if (P->kappa * std::sqrt((double)dim) * spread[m] <= tau) {
+                    l0 = m;
+                    break;
+                }
+            }
+        }
+        if (l0 > 1) {
+            refine(L, P->keys.get(), dim, B, Ns, l0, st);
+            balance(L, P->keys.get(), dim, B, P->sep, st);
+            build_boxes(P, L, st);
+            box_stats(P, st, nullptr);
+        }
+    }
+    P->tree.l0 = l0;
+    // a5: lists
+    build_lists(P, st);
+}
+
+}  // namespace cfmm
