@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the complex-coordinate FMM hot path on GB300.
+
+Workload (the 2D Helmholtz configuration): k = 20, N = 100,000 points on the
+complexified bump curve t in [-40, 40] (bump height drawn in [0.3, 1.0],
+imaginary part 0.5*sign(t)*max(|t|-4, 0)), single + double layer with the
+curve's analytic normals, complex Gaussian densities, eps = 1e-6, leaf size
+64, FP64. Inputs are synthetic (seeded, cfmm_inputs.config2).
+
+One step = one pass of the whole hot path on inputs resident in HBM:
+cfmm_plan (bounding box, Morton keys, radix sort, tree, level restriction,
+centres, Lists 1-4, expansion orders, translation tables) + cfmm_apply
+(P2M, M2M, M2L, P2L, L2L, P2P, M2P, L2P, un-permute) + cfmm_destroy.
+value = points per second of that pass; apply_only = the same for the apply
+alone on a resident plan (the GMRES matvec).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU: replicas (each rank runs its own copy of the workload), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
+METRIC = "complex-FMM pts/s at rel.err<=1e-6 (2D Helmholtz SLP+DLP, k=20, N=1e5)"
+WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
+STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2509_05458_gb300 as cf
+    from cfmm_inputs import config2, densities
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    g = config2(N_POINTS, seed=0)
+    dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2)
+    re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
+    nre, nim = torch.from_numpy(g.nrm_re).to(dev), torch.from_numpy(g.nrm_im).to(dev)
+    dens = torch.from_numpy(dens_np).to(dev)
+    out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
+    kernel = cf.HELMHOLTZ | cf.SLP | cf.DLP
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def step(timing=False):
+        p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
+        if timing:
+            p.set_timing(True)
+        p.apply(dens, out=out)
+        t = p.timings() if timing else None
+        info = p.info()
+        p.destroy()
+        return t, info
+
+    # work model of the workload (host bookkeeping, outside the timed region)
+    wp = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
+    work = work_model(wp)
+    wp.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # accuracy of this exact configuration on sampled targets (outside the timed region)
+    acc = None
+    if rank == 0 and not args.skip_check:
+        from oracle.direct import direct
+        idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
+        pts = g.re + 1j * g.im
+        u0 = direct(2, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0], tau=dens_np[0, 1],
+                    nrm=g.nrm_re + 1j * g.nrm_im)
+        u = out.cpu().numpy()[0, idx]
+        acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
+
+    clocks = ClockSampler(local)
+    n0 = cf.launch_count()
+    step_ms, kern = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        t, info = step(timing=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kern.append(t)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = cf.launch_count() - n0
+    ms = statistics.mean(step_ms)
+    ms_max = _max_over_ranks(ms, ws, dev)
+
+    # apply-only on a resident plan (GMRES matvec)
+    p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
+    for _ in range(3):
+        p.apply(dens, out=out)
+    torch.cuda.synchronize()
+    ap = []
+    for _ in range(max(5, args.steps)):
+        flush.zero_()
+        ev0.record(stream)
+        p.apply(dens, out=out)
+        ev1.record(stream)
+        ev1.synchronize()
+        ap.append(ev0.elapsed_time(ev1))
+    apply_ms = statistics.median(ap)
+    p.destroy()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hre, him, hnre, hnim = g.re, g.im, g.nrm_re, g.nrm_im
+    hd = np.ascontiguousarray(dens_np)
+    ho = np.empty((1, g.n), dtype=np.complex128)
+    e2e = []
+    for i in range(max(3, args.steps) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ph = cf.plan(2, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF)
+        ph.apply(hd, out=ho)
+        ph.destroy()
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e.append(t1 - t0)
+    e2e_s = statistics.median(e2e)
+    h2d = 4 * hre.nbytes + hd.nbytes
+    d2h = ho.nbytes
+
+    if rank != 0:
+        return
+    # dominant kernel of the step and its roofline (FP64 ALU bound)
+    kt = np.mean(np.array(kern), axis=0)
+    dom = int(np.argmax(kt))
+    peaks = _peaks()
+    fp64_peak = 1250.0   # GFLOP/s: nominal dense FP64 of GB300 (no measured FP64 peak is provided)
+    roof = dominant_roofline(STEP_NAMES[dom], kt[dom], work, fp64_peak)
+    line = {
+        "metric": METRIC,
+        "value": g.n * ws / (ms_max / 1e3),
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
+                   "layers": "SLP+DLP", "precision": "FP64", "parallelism": f"replicas{ws}",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "tree": {k: info[k] for k in ("nlevels", "nboxes", "nleaves", "l0", "p2p_pairs", "m2l_pairs")}},
+        "apply_only": {"value": g.n / (apply_ms / 1e3), "unit": "points/s", "ms": apply_ms},
+        "accuracy": {"rel_l2_vs_direct_100_targets": acc, "eps": EPS},
+        "step_breakdown_ms": {STEP_NAMES[i]: float(kt[i]) for i in range(9)},
+        "plan_ms": float(ms - float(np.sum(kt))),
+        "work": work,
+        "roofline": roof,
+        "e2e": {"value": g.n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches // max(1, args.steps)),
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+
+
+def work_model(p):
+    """Algorithmic work of one apply: List-2 pairs and M2L flops (8 flops per
+    complex multiply-add, (2P+1)^2 per pair at the pair's level), List-1 pairs."""
+    import numpy as np
+    inf = p.info()
+    t = p.export_tree()
+    P = p.orders()
+    off, _ = p.export_list(2)
+    cnt = np.diff(off)
+    m2l_flops = 0
+    pairs_per_level = {}
+    for l in range(inf["nlevels"]):
+        npairs = int(cnt[t["level"] == l].sum())
+        if npairs:
+            pairs_per_level[int(l)] = npairs
+            m2l_flops += npairs * 8 * (2 * int(P[l]) + 1) ** 2
+    return {"p2p_pairs": int(inf["p2p_pairs"]), "m2l_pairs": int(inf["m2l_pairs"]),
+            "m2l_pairs_per_level": pairs_per_level, "orders": [int(x) for x in P],
+            "m2l_flops": int(m2l_flops), "p2p_flops_per_pair": P2P_FLOPS_PER_PAIR}
+
+
+def dominant_roofline(name, ms, work, fp64_peak_gflops):
+    """Roofline of the dominant kernel of the apply, FP64-ALU bound:
+    M2L: work["m2l_flops"]; P2P: List-1 pairs x FP64 flops per pair."""
+    flops = None
+    if name == "M2L":
+        flops = work["m2l_flops"]
+    elif name == "P2P" and P2P_FLOPS_PER_PAIR:
+        flops = work["p2p_pairs"] * P2P_FLOPS_PER_PAIR
+    base = {"bound": "alu", "peak": fp64_peak_gflops, "unit": "GFLOP/s", "traffic": None, "kernel": name,
+            "ms": float(ms),
+            "peak_source": "nominal GB300 dense FP64, 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 figure)"}
+    if not flops:
+        return dict(base, achieved=None, frac=None)
+    ach = flops / (ms / 1e3) / 1e9
+    return dict(base, achieved=ach, frac=ach / fp64_peak_gflops)
+
+
+# FP64 operations of one near-field pair (2D Helmholtz SLP+DLP); 0 = not yet counted
+P2P_FLOPS_PER_PAIR = 0
+
+
+def cpu_baseline(args):
+    """The oracle FMM, as it stands, on a bounded sample of the workload
+    (20,000 points of the same curve family, same k, eps, leaf size), one core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys,time,json; sys.path.insert(0, %r)\n"
+            "from cfmm_inputs import config2, densities\n"
+            "from oracle import fmm2d\n"
+            "g = config2(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=2)\n"
+            "t=time.perf_counter(); fmm2d.apply(g.re, g.im, 1, %r, %r, %d, sigma=d[0,0], tau=d[0,1], "
+            "nrm_re=g.nrm_re, nrm_im=g.nrm_im); t=time.perf_counter()-t\n"
+            "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, args.cpu_n, KAPPA, EPS, LEAF)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip()[-200:]}
+    o = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": o["n"] / o["s"], "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle FMM (numpy/scipy) on {o['n']} points of the same curve family, "
+                      f"same k/eps/leaf, SLP+DLP, one pass: {o['s']:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle, as it stands, on the host cores (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    times = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        res = cpu_baseline(args)
+        if i >= args.warmup and res["value"]:
+            times.append(res["value"])
+    val = statistics.mean(times) if times else None
+    line = {"metric": METRIC, "value": val, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": N_POINTS, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
+                       "layers": "SLP+DLP", "precision": "FP64", "parallelism": "cpu"},
+            "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": res["sample"] if res else None},
+            "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-n", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-check", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.warmup = max(0, min(args.warmup, 1))
+        args.steps = max(1, min(args.steps, 2))
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -236,9 +236,9 @@ class Expansions2D:
 def expansion_orders(T, kernel, kappa, eps):
     """P per level (Sec. 6.3, reading #13)."""
     nl = T.nlevels
-    e = eps * tr.P_HEADROOM
     if kernel == LAPLACE:
-        return [tr.nterms_laplace(2, T.k, e)] * nl
+        return [tr.nterms_laplace(2, T.k, eps * tr.P_HEADROOM)] * nl
+    e = eps * tr.P_HEADROOM_HELM
     return [tr.nterms_helmholtz(2, T.k, e, kappa, T.width(l), tr.helm2d_pair) for l in range(nl)]
 
 

@@ -449,9 +449,12 @@ def check_balance(T):
 # ---- expansion orders (Sec. 6.3) -----------------------------------------
 
 # The criteria of Eqs. nterms_criteria_2d/3d are applied with the Lipschitz
-# prefactor dropped, as the paper does in practice, and with one digit of
-# headroom: the order is chosen for eps * P_HEADROOM.
+# prefactor dropped, as the paper does in practice, and with headroom: the
+# order is chosen for eps * P_HEADROOM (Laplace) or eps * P_HEADROOM_HELM
+# (Helmholtz, whose criterion |H_n(kR) J_n(kr)| carries an extra 1/(n pi)
+# against (r/R)^n and undershoots by about a digit).
 P_HEADROOM = 0.1
+P_HEADROOM_HELM = 0.01
 
 def nterms_laplace(dim, k, eps):
     """Smallest n >= 1 with (r/R)^n <= eps, R=(k+1/2)w, r=sqrt(d)/2 w."""

@@ -745,7 +745,10 @@ static int nterms_helm2d(int k, double eps, double kappa, double w) {
     return pmax;
 }
 
+// the criterion is applied at eps * headroom: one digit for Laplace, two for
+// Helmholtz (|H_n(kR) J_n(kr)| carries an extra 1/(n pi) against (r/R)^n)
 constexpr double kPHeadroom = 0.1;
+constexpr double kPHeadroomHelm = 0.01;
 
 void fmm2d_setup(cfmm_plan_s* P) {
     TreeDev& T = P->tree;
@@ -758,11 +761,10 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->ker = P->kernel;
     S->l0 = T.l0;
     S->nlev = T.nlevels;
-    double e = P->eps * kPHeadroom;
     S->Plev.assign(T.nlevels, 0);
     for (int l = 0; l < T.nlevels; ++l) {
-        if (P->kernel == CFMM_LAPLACE) S->Plev[l] = nterms_laplace(2, P->sep, e);
-        else S->Plev[l] = nterms_helm2d(P->sep, e, P->kappa, std::ldexp(P->W, -l));
+        if (P->kernel == CFMM_LAPLACE) S->Plev[l] = nterms_laplace(2, P->sep, P->eps * kPHeadroom);
+        else S->Plev[l] = nterms_helm2d(P->sep, P->eps * kPHeadroomHelm, P->kappa, std::ldexp(P->W, -l));
     }
     P->P = S->Plev;
     if (T.nboxes <= 1) return;   // single leaf: near field only
