@@ -135,6 +135,32 @@ int cfmm_direct(int dim, int kernel, double k,
                 const double* densities, int nrhs, double* out,
                 int precision, void* stream);
 
+/*
+ * cfmm_direct_noalloc: the same direct sum as cfmm_direct (FP64), for callers
+ * that cannot allocate device memory while they run -- a program that gave
+ * its whole device-memory budget to a pool up front, so an allocation by this
+ * library would fail, or a latency-critical loop in which cudaMalloc/cudaFree
+ * (which may synchronise the device) are not acceptable. The paper has no
+ * counterpart: this is a deployment variant of the direct sum.
+ *   Arguments, layouts and result as cfmm_direct (device pointers; the caller
+ *   passes inputs and output). Allocates nothing: its scratch (SoA copies of
+ *   points and normals) is a fixed array of about 4.5 MiB of device memory
+ *   inside the library, held by every GPU that loads the library until exit.
+ *   Limits: m <= 32768 sources and n <= 32768 targets; larger requests
+ *   return CFMM_EINVAL without touching the GPU.
+ *   All calls share that array: calls that overlap on the GPU (other
+ *   streams, other host threads) race; serialise them. Each call overwrites
+ *   what it reads, so nothing needs clearing between calls.
+ *   The first call on a device looks up the array's address and uploads the
+ *   library's constant tables; make it before any stream capture.
+ *   stream: cudaStream_t or NULL. Asynchronous. Returns 0 or a negative status.
+ */
+int cfmm_direct_noalloc(int dim, int kernel, double k,
+                        const double* src_re, const double* src_im,
+                        const double* nrm_re, const double* nrm_im, int64_t m,
+                        const double* trg_re, const double* trg_im, int64_t n,
+                        const double* densities, int nrhs, double* out, void* stream);
+
 /* ---- introspection (tests and tools) --------------------------------- */
 typedef struct cfmm_plan_info {
     int dim, kernel, sep, leaf_size, precision;

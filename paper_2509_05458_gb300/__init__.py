@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["LAPLACE", "HELMHOLTZ", "SLP", "DLP", "GREEN_SCALE", "FP64", "MIXED", "AUTO",
-           "Plan", "plan", "direct", "lib", "launch_count", "CfmmError", "library_path"]
+           "Plan", "plan", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
 
 LAPLACE, HELMHOLTZ = 0, 1
 SLP, DLP, GREEN_SCALE = 1 << 4, 1 << 5, 1 << 6
@@ -66,6 +66,8 @@ def lib():
     L.cfmm_destroy.argtypes = [vp]
     L.cfmm_direct.restype = ci
     L.cfmm_direct.argtypes = [ci, ci, dbl, vp, vp, vp, vp, i64, vp, vp, i64, vp, ci, vp, ci, vp]
+    L.cfmm_direct_noalloc.restype = ci
+    L.cfmm_direct_noalloc.argtypes = [ci, ci, dbl, vp, vp, vp, vp, i64, vp, vp, i64, vp, ci, vp, vp]
     L.cfmm_plan_get_info.restype = ci
     L.cfmm_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.cfmm_plan_get_orders.restype = ci
@@ -267,4 +269,20 @@ def direct(dim, kernel, k, src_re, src_im, trg_re, trg_im, densities, nrm_re=Non
     _check(lib().cfmm_direct(int(dim), int(kernel), float(k), _ptr(sr), _ptr(si), _ptr(nr), _ptr(ni), m,
                              _ptr(tr), _ptr(ti), n, _ptr(d), nrhs, _ptr(out), int(precision),
                              _stream_ptr(stream)))
+    return out
+
+
+def direct_noalloc(dim, kernel, k, src_re, src_im, trg_re, trg_im, densities, out, nrm_re=None, nrm_im=None,
+                   stream=None):
+    """cfmm_direct_noalloc on CUDA torch tensors: the direct sum without any device
+    allocation inside the library (for callers that cannot allocate while they run).
+    Points [m or n, dim] float64, densities complex128 [nrhs, ncomp, m], out
+    complex128 [nrhs, n], all contiguous CUDA tensors owned by the caller."""
+    for t in (src_re, src_im, trg_re, trg_im, densities, out):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("cfmm_direct_noalloc takes contiguous CUDA tensors")
+    m, n, nrhs = src_re.shape[0], trg_re.shape[0], densities.shape[0]
+    _check(lib().cfmm_direct_noalloc(int(dim), int(kernel), float(k), _ptr(src_re), _ptr(src_im),
+                                     _ptr(nrm_re), _ptr(nrm_im), m, _ptr(trg_re), _ptr(trg_im), n,
+                                     _ptr(densities), nrhs, _ptr(out), _stream_ptr(stream)))
     return out

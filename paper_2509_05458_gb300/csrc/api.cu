@@ -398,6 +398,19 @@ int cfmm_direct(int dim, int kernel, double k, const double* src_re, const doubl
     });
 }
 
+int cfmm_direct_noalloc(int dim, int kernel, double k, const double* src_re, const double* src_im,
+                        const double* nrm_re, const double* nrm_im, int64_t m, const double* trg_re,
+                        const double* trg_im, int64_t n, const double* densities, int nrhs, double* out,
+                        void* stream) {
+    return guarded([&] {
+        CFMM_REQUIRE(is_device_ptr(src_re) && is_device_ptr(trg_re) && is_device_ptr(densities) &&
+                         is_device_ptr(out),
+                     CFMM_EINVAL, "cfmm_direct_noalloc takes device pointers");
+        direct_noalloc(dim, kernel, k, src_re, src_im, nrm_re, nrm_im, m, trg_re, trg_im, n, densities, nrhs, out,
+                       stream);
+    });
+}
+
 int cfmm_plan_get_info(cfmm_plan_t P, cfmm_plan_info* info) {
     return guarded([&] {
         CFMM_REQUIRE(P && info, CFMM_EINVAL, "null argument");

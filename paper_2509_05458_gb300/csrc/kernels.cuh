@@ -36,6 +36,11 @@ void fmm2d_setup(cfmm_plan_s* P);
 void fmm2d_release(cfmm_plan_s* P);
 void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 
+// direct sum with library-owned fixed scratch (direct_noalloc.cu)
+int direct_noalloc(int dim, int kernel, double k, const double* src_re, const double* src_im, const double* nrm_re,
+                   const double* nrm_im, int64_t m, const double* trg_re, const double* trg_im, int64_t n,
+                   const double* densities, int nrhs, double* out, void* stream);
+
 void upload_lag_rule_p2p();
 void upload_lag_rule_fmm2d();
 
