@@ -5,7 +5,10 @@ Workload (the 2D Helmholtz configuration): k = 20, N = 100,000 points on the
 complexified bump curve t in [-40, 40] (bump height drawn in [0.3, 1.0],
 imaginary part 0.5*sign(t)*max(|t|-4, 0)), single + double layer with the
 curve's analytic normals, complex Gaussian densities, eps = 1e-6, leaf size
-64, FP64. Inputs are synthetic (seeded, cfmm_inputs.config2).
+64. Inputs are synthetic (seeded, cfmm_inputs.config2). The headline runs in
+MIXED precision (near field in complex64 arithmetic, translations FP64); the
+same pass in FP64 is reported beside it, and both are checked against the
+direct sum on 100 sampled targets.
 
 One step = one pass of the whole hot path on inputs resident in HBM:
 cfmm_plan (bounding box, Morton keys, radix sort, tree, level restriction,
@@ -32,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
-METRIC = "complex-FMM pts/s at rel.err<=1e-6 (2D Helmholtz SLP+DLP, k=20, N=1e5)"
+METRIC = "complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, N=1e5)"
 WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
 
@@ -141,78 +144,85 @@ def run_gpu(args):
     kernel = cf.HELMHOLTZ | cf.SLP | cf.DLP
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def step(timing=False):
-        p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
-        if timing:
-            p.set_timing(True)
-        p.apply(dens, out=out)
-        t = p.timings() if timing else None
-        info = p.info()
-        p.destroy()
-        return t, info
-
-    # work model of the workload (host bookkeeping, outside the timed region)
+    # work model of the workload (host bookkeeping, outside the timed regions)
     wp = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
     work = work_model(wp)
     wp.destroy()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # accuracy of this exact configuration on sampled targets (outside the timed region)
-    acc = None
-    if rank == 0 and not args.skip_check:
-        from oracle.direct import direct
-        idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
-        pts = g.re + 1j * g.im
-        u0 = direct(2, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0], tau=dens_np[0, 1],
-                    nrm=g.nrm_re + 1j * g.nrm_im)
-        u = out.cpu().numpy()[0, idx]
-        acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
+    def measure(precision, check):
+        def step(timing=False):
+            p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream,
+                        precision=precision)
+            if timing:
+                p.set_timing(True)
+            p.apply(dens, out=out)
+            t = p.timings() if timing else None
+            info = p.info()
+            p.destroy()
+            return t, info
 
-    clocks = ClockSampler(local)
-    n0 = cf.launch_count()
-    step_ms, kern = [], []
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    _barrier(ws)
-    torch.cuda.synchronize()
-    clocks.start()
-    wall0 = time.perf_counter()
-    info = None
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0.record(stream)
-        t, info = step(timing=True)
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        kern.append(t)
-    torch.cuda.synchronize()
-    _barrier(ws)
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    launches = cf.launch_count() - n0
-    ms = statistics.mean(step_ms)
-    ms_max = _max_over_ranks(ms, ws, dev)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        acc = None
+        if check:
+            from oracle.direct import direct
+            idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
+            pts = g.re + 1j * g.im
+            u0 = direct(2, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0], tau=dens_np[0, 1],
+                        nrm=g.nrm_re + 1j * g.nrm_im)
+            u = out.cpu().numpy()[0, idx]
+            acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
+        clocks = ClockSampler(local)
+        n0 = cf.launch_count()
+        step_ms, kern = [], []
+        _barrier(ws)
+        torch.cuda.synchronize()
+        clocks.start()
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            t, info = step(timing=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            kern.append(t)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        wall = time.perf_counter() - wall0
+        clk = clocks.stop()
+        launches = cf.launch_count() - n0
+        ms = _max_over_ranks(statistics.mean(step_ms), ws, dev)
+        # apply alone on a resident plan (the GMRES matvec)
+        p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream, precision=precision)
+        for _ in range(3):
+            p.apply(dens, out=out)
+        torch.cuda.synchronize()
+        ap = []
+        for _ in range(max(5, args.steps)):
+            flush.zero_()
+            ev0.record(stream)
+            p.apply(dens, out=out)
+            ev1.record(stream)
+            ev1.synchronize()
+            ap.append(ev0.elapsed_time(ev1))
+        p.destroy()
+        kt = np.mean(np.array(kern), axis=0)
+        return dict(ms=ms, apply_ms=statistics.median(ap), kt=kt, acc=acc, clk=clk, wall=wall,
+                    launches=launches // max(1, args.steps), info=info)
 
-    # apply-only on a resident plan (GMRES matvec)
-    p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
-    for _ in range(3):
-        p.apply(dens, out=out)
-    torch.cuda.synchronize()
-    ap = []
-    for _ in range(max(5, args.steps)):
-        flush.zero_()
-        ev0.record(stream)
-        p.apply(dens, out=out)
-        ev1.record(stream)
-        ev1.synchronize()
-        ap.append(ev0.elapsed_time(ev1))
-    apply_ms = statistics.median(ap)
-    p.destroy()
+    if args.precision == "fp64":
+        mixed = fp64 = measure(cf.FP64, rank == 0 and not args.skip_check)
+    elif args.precision == "mixed":
+        mixed = fp64 = measure(cf.MIXED, rank == 0 and not args.skip_check)
+    else:
+        mixed = measure(cf.MIXED, rank == 0 and not args.skip_check)
+        fp64 = measure(cf.FP64, rank == 0 and not args.skip_check)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
+    # end to end through the C ABI with host buffers (copies inside the timed region), MIXED
     hre, him, hnre, hnim = g.re, g.im, g.nrm_re, g.nrm_im
     hd = np.ascontiguousarray(dens_np)
     ho = np.empty((1, g.n), dtype=np.complex128)
@@ -220,7 +230,7 @@ def run_gpu(args):
     for i in range(max(3, args.steps) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ph = cf.plan(2, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF)
+        ph = cf.plan(2, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF, precision=cf.MIXED)
         ph.apply(hd, out=ho)
         ph.destroy()
         t1 = time.perf_counter()
@@ -232,40 +242,45 @@ def run_gpu(args):
 
     if rank != 0:
         return
-    # dominant kernel of the step and its roofline (FP64 ALU bound)
-    kt = np.mean(np.array(kern), axis=0)
+    kt = mixed["kt"]
     dom = int(np.argmax(kt))
-    peaks = _peaks()
     fp64_peak = 1250.0   # GFLOP/s: nominal dense FP64 of GB300 (no measured FP64 peak is provided)
     roof = dominant_roofline(STEP_NAMES[dom], kt[dom], work, fp64_peak)
+    info = mixed["info"]
     line = {
         "metric": METRIC,
-        "value": g.n * ws / (ms_max / 1e3),
+        "value": g.n * ws / (mixed["ms"] / 1e3),
         "unit": "points/s",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_max,
+        "ms_per_step": mixed["ms"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
-                   "layers": "SLP+DLP", "precision": "FP64", "parallelism": f"replicas{ws}",
+                   "layers": "SLP+DLP", "precision": "MIXED (near field complex64, translations FP64)",
+                   "parallelism": f"replicas{ws}",
                    "l2": "flushed (256 MB write) before every timed step",
                    "tree": {k: info[k] for k in ("nlevels", "nboxes", "nleaves", "l0", "p2p_pairs", "m2l_pairs")}},
-        "apply_only": {"value": g.n / (apply_ms / 1e3), "unit": "points/s", "ms": apply_ms},
-        "accuracy": {"rel_l2_vs_direct_100_targets": acc, "eps": EPS},
+        "apply_only": {"value": g.n / (mixed["apply_ms"] / 1e3), "unit": "points/s", "ms": mixed["apply_ms"]},
+        "accuracy": {"rel_l2_vs_direct_100_targets": mixed["acc"], "eps": EPS},
+        "fp64": {"value": g.n / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
+                 "apply_only": g.n / (fp64["apply_ms"] / 1e3), "apply_ms": fp64["apply_ms"],
+                 "accuracy": fp64["acc"],
+                 "step_breakdown_ms": {STEP_NAMES[i]: float(fp64["kt"][i]) for i in range(9)}},
         "step_breakdown_ms": {STEP_NAMES[i]: float(kt[i]) for i in range(9)},
-        "plan_ms": float(ms - float(np.sum(kt))),
+        "plan_ms": float(mixed["ms"] - float(np.sum(kt))),
         "work": work,
         "roofline": roof,
         "e2e": {"value": g.n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches // max(1, args.steps)),
-        "clocks": clk,
-        "wall_s": wall,
+        "gpu_launches": int(mixed["launches"]),
+        "clocks": mixed["clk"],
+        "clocks_fp64": fp64["clk"],
+        "wall_s": mixed["wall"],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -367,6 +382,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="which passes to run (the headline needs both)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))

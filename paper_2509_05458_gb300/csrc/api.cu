@@ -203,7 +203,8 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
                   sg, ta, n, P->slp, P->dlp, P->kappa};
         for (int i = 2; i <= 7; ++i) record(P, i);
         launch_p2p(P->dim, P->kernel, K, P->tree.d_leaf_boxes.get(), P->tree.nleaves, P->tree.start.get(),
-                   P->tree.end.get(), P->tree.loff[0].get(), P->tree.lent[0].get(), P->out_s.get(), nrhs, false, st);
+                   P->tree.end.get(), P->tree.loff[0].get(), P->tree.lent[0].get(), P->out_s.get(), nrhs, false, st,
+                   P->precision == CFMM_MIXED);
     }
     record(P, 8);
     cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
@@ -345,7 +346,8 @@ int cfmm_direct(int dim, int kernel, double k, const double* src_re, const doubl
         CFMM_REQUIRE(ker == CFMM_LAPLACE || ker == CFMM_HELMHOLTZ, CFMM_EINVAL, "bad kernel");
         CFMM_REQUIRE(ker == CFMM_LAPLACE || (std::isfinite(k) && k > 0.0), CFMM_EINVAL, "Helmholtz needs k > 0");
         CFMM_REQUIRE(m >= 1 && n >= 1 && nrhs >= 1, CFMM_EINVAL, "sizes must be positive");
-        CFMM_REQUIRE(precision == CFMM_FP64, CFMM_EUNSUPPORTED, "direct sum: only FP64 is built");
+        CFMM_REQUIRE(precision == CFMM_FP64 || precision == CFMM_MIXED, CFMM_EINVAL,
+                     "direct sum: precision must be CFMM_FP64 or CFMM_MIXED");
         bool dlp = (kernel & CFMM_DLP) != 0;
         bool slp = (kernel & CFMM_SLP) != 0 || !dlp;
         CFMM_REQUIRE(!dlp || (nrm_re && nrm_im), CFMM_EINVAL, "double layer needs normals");
@@ -379,7 +381,7 @@ int cfmm_direct(int dim, int kernel, double k, const double* src_re, const doubl
         const cd* d = reinterpret_cast<const cd*>(densities);
         KParams K{sr.get(), si.get(), dlp ? nr.get() : nullptr, dlp ? ni.get() : nullptr, tr.get(), ti.get(), m, n,
                   slp ? d : nullptr, dlp ? d + (slp ? m : 0) : nullptr, ncomp * m, slp, dlp, k};
-        launch_direct(dim, ker, K, reinterpret_cast<cd*>(out), nrhs, st);
+        launch_direct(dim, ker, K, reinterpret_cast<cd*>(out), nrhs, st, precision == CFMM_MIXED);
         if (kernel & CFMM_GREEN_SCALE) {
             DevBuf<int> id;
             std::vector<int> h(n);

@@ -899,7 +899,7 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     if (T.nboxes <= 1) {
         for (int i = 2; i <= 6; ++i) rec(i);
         launch_p2p(2, KER, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
-                   T.lent[0].get(), u, nrhs, false, st);
+                   T.lent[0].get(), u, nrhs, false, st, P->precision == CFMM_MIXED);
         rec(7);
         rec(8);
         return;
@@ -975,7 +975,7 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     rec(6);
     // (3) P2P over List 1 (writes u)
     launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, st);
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, st, P->precision == CFMM_MIXED);
     rec(7);
     // (5) M2P and (8) L2P (add to u)
     {

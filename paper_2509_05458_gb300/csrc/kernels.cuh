@@ -24,8 +24,9 @@ struct KParams {
 };
 
 void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
-                const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st);
-void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st);
+                const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
+                bool mixed = false);
+void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st, bool mixed = false);
 
 // tree construction (tree.cu)
 void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,

@@ -1,6 +1,7 @@
 // Near field (List 1, step 3 of Sec. 6.4) and the direct sum (Sec. 2.3,
 // Eq. evaluation_problem) for 2D/3D Laplace and Helmholtz, single and double
-// layer, in float64 / complex128.
+// layer, in float64 / complex128 or in mixed precision (complex64 kernel
+// arithmetic, FP32 hi/lo pair differences, compensated sums).
 //
 // Layout: one CTA per target leaf. 128 threads = 32 targets x 4 source
 // lanes; the sources of each List-1 leaf are staged through shared memory
@@ -11,7 +12,95 @@
 
 namespace cfmm {
 
-void upload_lag_rule_p2p() { upload_lag_rule_local(); }
+// ---------------------------------------------------------------------------
+// Ascending series of H_0^(1), H_1^(1) in w = -(kappa r)^2/4 (DLMF 10.2.2,
+// 10.8.1), evaluated by Horner's rule with precomputed coefficients:
+//   A(w) = sum w^k/(k!)^2                   J_0 = A
+//   B(w) = sum w^k/(k!(k+1)!)               J_1 = (z/2) B
+//   C(w) = sum_{k>=1} H_k w^k/(k!)^2        Y_0 = (2/pi)((log(z/2)+gamma) A - C)
+//   D(w) = sum (psi(k+1)+psi(k+2)) w^k/(k!(k+1)!)
+//                                           Y_1 = -2/(pi z) + (2/pi) log(z/2) J_1 - (z/(2pi)) D
+// with H_k the harmonic numbers and psi(k+1) = -gamma + H_k. Only r^2 enters:
+// log(z/2) = Log(q)/2 with q = (kappa r/2)^2, and the double layer needs
+// kappa J_1/r = (kappa^2/2) B and kappa Y_1/r = -2/(pi r^2) + (kappa^2/pi) log(z/2) B
+// - (kappa^2/(2 pi)) D, so the near field takes no square root.
+// ---------------------------------------------------------------------------
+constexpr int kSerMax = 21;
+struct SeriesTab {
+    double a[kSerMax + 1], b[kSerMax + 1], c[kSerMax + 1], d[kSerMax + 1];
+    float af[kSerMax + 1], bf[kSerMax + 1], cf_[kSerMax + 1], df[kSerMax + 1];
+};
+static __constant__ SeriesTab c_ser;
+
+static SeriesTab make_series_tab() {
+    SeriesTab T;
+    const double g = 0.57721566490153286061;
+    double fk = 1.0, H = 0.0;   // k!, H_k
+    for (int k = 0; k <= kSerMax; ++k) {
+        if (k > 0) {
+            fk *= k;
+            H += 1.0 / k;
+        }
+        double fk1 = fk * (k + 1);
+        T.a[k] = 1.0 / (fk * fk);
+        T.b[k] = 1.0 / (fk * fk1);
+        T.c[k] = H / (fk * fk);
+        T.d[k] = (-2.0 * g + 2.0 * H + 1.0 / (k + 1)) / (fk * fk1);
+        T.af[k] = (float)T.a[k];
+        T.bf[k] = (float)T.b[k];
+        T.cf_[k] = (float)T.c[k];
+        T.df[k] = (float)T.d[k];
+    }
+    return T;
+}
+
+void upload_lag_rule_p2p() {
+    upload_lag_rule_local();
+    SeriesTab T = make_series_tab();
+    CFMM_CUDA(cudaMemcpyToSymbol(c_ser, &T, sizeof(T)));
+}
+
+// number of series terms for |q|^2 = aq, FP64 (truncation below 1e-18)
+__device__ __forceinline__ int series_terms64(double aq) {
+    return aq <= 0.0625 ? 8 : aq <= 1.0 ? 11 : aq <= 5.0625 ? 14 : aq <= 16.0 ? 16 : 21;
+}
+// FP32 (truncation below 1e-9)
+__device__ __forceinline__ int series_terms32(float aq) {
+    return aq <= 0.0625f ? 5 : aq <= 1.0f ? 7 : aq <= 5.0625f ? 9 : aq <= 16.0f ? 10 : 14;
+}
+
+// FP64 2D Helmholtz pair: returns SLP factor H0 and DLP factor kappa H1 / r
+__device__ __forceinline__ void helm2d_pair64(cd r2, double kappa, bool slp, bool dlp, cd& h0, cd& g1) {
+    const double kPi = 3.14159265358979323846, kG = 0.57721566490153286061;
+    double k2 = kappa * kappa;
+    cd q = (0.25 * k2) * r2;
+    double aq = cabs2(q);
+    if (aq <= 81.0) {
+        cd w = -q;
+        int K = series_terms64(aq);
+        cd A = {c_ser.a[K], 0}, Bs = {c_ser.b[K], 0}, Cs = {c_ser.c[K], 0}, Ds = {c_ser.d[K], 0};
+        for (int k = K - 1; k >= 0; --k) {
+            A = A * w + cd{c_ser.a[k], 0};
+            Cs = Cs * w + cd{c_ser.c[k], 0};
+            if (dlp) {
+                Bs = Bs * w + cd{c_ser.b[k], 0};
+                Ds = Ds * w + cd{c_ser.d[k], 0};
+            }
+        }
+        cd L = {0.25 * log(aq), 0.5 * atan2(q.y, q.x)};    // log(z/2)
+        h0 = A + mul_i((2.0 / kPi) * ((L + cd{kG, 0}) * A - Cs));
+        if (dlp) {
+            cd ir2 = cinv(r2);
+            cd y = (-2.0 / kPi) * ir2 + (k2 / kPi) * (L * Bs) - (k2 / (2.0 * kPi)) * Ds;
+            g1 = (0.5 * k2) * Bs + mul_i(y);
+        }
+        return;
+    }
+    cd r = csqrt_p(r2);
+    cd h1;
+    hankel01(kappa * r, &h0, &h1);
+    g1 = (kappa * h1) * cinv(r);
+}
 
 constexpr int kP2PThreads = 128;
 constexpr int kP2PTargets = 32;
@@ -37,14 +126,13 @@ __device__ __forceinline__ void pair_kernel(const double* dr, const double* di, 
     }
     if (DIM == 2 && KER == CFMM_LAPLACE) {
         // log r = Log(r^2)/2 ; grad_y log r = (y - x)/r^2
-        if (slp) acc += (0.5 * clog_p(r2)) * sg;
-        if (dlp) acc -= (nd / r2) * ta;
+        if (slp) acc += cd{0.25 * log(cabs2(r2)), 0.5 * atan2(r2.y, r2.x)} * sg;
+        if (dlp) acc -= (nd * cinv(r2)) * ta;
     } else if (DIM == 2) {
-        cd r = csqrt_p(r2);
-        cd h0, h1;
-        hankel01(kappa * r, &h0, &h1);
+        cd h0, g1;
+        helm2d_pair64(r2, kappa, slp, dlp, h0, g1);
         if (slp) acc += h0 * sg;
-        if (dlp) acc += (kappa * h1) * (nd / r) * ta;
+        if (dlp) acc += (g1 * nd) * ta;
     } else if (KER == CFMM_LAPLACE) {
         cd r = csqrt_p(r2);
         cd ir = cinv(r);
@@ -172,36 +260,283 @@ __global__ void __launch_bounds__(kP2PThreads) k_direct(KParams K, cd* __restric
     finish_target<DIM, KER>(acc, red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti, false);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision (complex64 kernel arithmetic, compensated FP32 sums).
+// Coordinates enter as FP64 offsets from a reference point of the target
+// block (the first target), split into FP32 hi + lo parts; the pair
+// difference (x_h - y_h) + (x_l - y_l) keeps FP32 relative accuracy even for
+// near-coincident pairs (Sterbenz: x_h - y_h is exact when x_h, y_h are
+// close). Sums over sources use compensated (Kahan) FP32 accumulation; the
+// few partial sums of a target are combined in FP64.
+// ---------------------------------------------------------------------------
+CFMM_HD cf cinvf(cf b) {
+    float den = b.x * b.x + b.y * b.y;
+    return cf{b.x / den, -b.y / den};
+}
+__device__ __forceinline__ cf csqrtf_p(cf z) {
+    float a = z.x, b = z.y;
+    if (a == 0.f && b == 0.f) return cf{0.f, 0.f};
+    float m = hypotf(a, b);
+    float t = sqrtf(0.5f * (fabsf(a) + m));
+    if (a >= 0.f) return cf{t, b / (2.f * t)};
+    return cf{fabsf(b) / (2.f * t), copysignf(t, b)};
+}
+__device__ __forceinline__ cf mul_if(cf a) { return cf{-a.y, a.x}; }
+
+struct Kahan {
+    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    __device__ __forceinline__ void add(cf v) {
+        float yx = v.x - cx, tx = sx + yx;
+        cx = (tx - sx) - yx;
+        sx = tx;
+        float yy = v.y - cy, ty = sy + yy;
+        cy = (ty - sy) - yy;
+        sy = ty;
+    }
+    __device__ __forceinline__ cd value() const { return cd{(double)sx - (double)cx, (double)sy - (double)cy}; }
+};
+
+__device__ __forceinline__ void helm2d_pair32(cf r2, float kappa, bool dlp, cf& h0, cf& g1) {
+    const float kPi = 3.14159265f, kG = 0.5772156649f;
+    float k2 = kappa * kappa;
+    cf q = (0.25f * k2) * r2;
+    float aq = q.x * q.x + q.y * q.y;
+    cf w = cf{-q.x, -q.y};
+    int K = series_terms32(aq);
+    cf A = {c_ser.af[K], 0.f}, Bs = {c_ser.bf[K], 0.f}, Cs = {c_ser.cf_[K], 0.f}, Ds = {c_ser.df[K], 0.f};
+    for (int k = K - 1; k >= 0; --k) {
+        A = A * w + cf{c_ser.af[k], 0.f};
+        Cs = Cs * w + cf{c_ser.cf_[k], 0.f};
+        if (dlp) {
+            Bs = Bs * w + cf{c_ser.bf[k], 0.f};
+            Ds = Ds * w + cf{c_ser.df[k], 0.f};
+        }
+    }
+    cf L = {0.25f * logf(aq), 0.5f * atan2f(q.y, q.x)};
+    cf lg = L + cf{kG, 0.f};
+    h0 = A + mul_if((2.f / kPi) * (lg * A - Cs));
+    if (dlp) {
+        cf ir2 = cinvf(r2);
+        cf y = (-2.f / kPi) * ir2 + (k2 / kPi) * (L * Bs) - (k2 / (2.f * kPi)) * Ds;
+        g1 = (0.5f * k2) * Bs + mul_if(y);
+    }
+}
+
+template <int DIM, int KER>
+__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const float* nr,
+                                              const float* ni, cf sg, cf ta, bool slp, bool dlp, float kappa,
+                                              double kappa64, Kahan& acc) {
+    cf d[DIM];
+    cf r2 = {0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        d[a] = cf{d_re[a], d_im[a]};
+        r2 = r2 + d[a] * d[a];
+    }
+    cf nd = {0.f, 0.f};
+    if (dlp) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nd = nd + cf{nr[a], ni[a]} * d[a];
+    }
+    cf v = {0.f, 0.f};
+    if (DIM == 2 && KER == CFMM_LAPLACE) {
+        if (slp) v = cf{0.25f * logf(r2.x * r2.x + r2.y * r2.y), 0.5f * atan2f(r2.y, r2.x)} * sg;
+        if (dlp) v = v - (nd * cinvf(r2)) * ta;
+    } else if (DIM == 2) {
+        float k2 = kappa * kappa;
+        cf q = (0.25f * k2) * r2;
+        if (q.x * q.x + q.y * q.y <= 81.f) {
+            cf h0, g1;
+            helm2d_pair32(r2, kappa, dlp, h0, g1);
+            if (slp) v = h0 * sg;
+            if (dlp) v = v + (g1 * nd) * ta;
+        } else {
+            // large |kappa r|: the FP64 quadrature path, result rounded to FP32
+            cd h0, g1;
+            helm2d_pair64(cd{r2.x, r2.y}, kappa64, slp, dlp, h0, g1);
+            if (slp) v = cf{(float)h0.x, (float)h0.y} * sg;
+            if (dlp) v = v + (cf{(float)g1.x, (float)g1.y} * nd) * ta;
+        }
+    } else if (KER == CFMM_LAPLACE) {
+        cf r = csqrtf_p(r2);
+        cf ir = cinvf(r);
+        if (slp) v = ir * sg;
+        if (dlp) v = v + (nd * (ir * ir * ir)) * ta;
+    } else {
+        cf r = csqrtf_p(r2);
+        cf ir = cinvf(r);
+        float e = expf(-kappa * r.y), sn, cs;
+        sincosf(kappa * r.x, &sn, &cs);
+        cf g = cf{e * cs, e * sn} * ir;
+        if (slp) v = g * sg;
+        if (dlp) v = v + (nd * (cf{1.f, 0.f} - mul_if(kappa * r)) * g * (ir * ir)) * ta;
+    }
+    acc.add(v);
+}
+
+struct SrcTileF {
+    float hr[kP2PChunk][3], lr[kP2PChunk][3], hi[kP2PChunk][3], li[kP2PChunk][3];
+    float nr[kP2PChunk][3], ni[kP2PChunk][3];
+    cf sg[kP2PChunk], ta[kP2PChunk];
+};
+
+__device__ __forceinline__ void split_hl(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+template <int DIM, int KER>
+__device__ void accumulate_sources32(SrcTileF& S, const KParams& K, int rhs, int s, int e, bool tvalid,
+                                     const double* ref_re, const double* ref_im, const float* xh_r,
+                                     const float* xl_r, const float* xh_i, const float* xl_i, Kahan& acc,
+                                     int split) {
+    const int64_t n = K.n_src;
+    float kap = (float)K.kappa;
+    for (int c0 = s; c0 < e; c0 += kP2PChunk) {
+        int cn = min(kP2PChunk, e - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+            int g = c0 + j;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                split_hl(K.src_re[a * n + g] - ref_re[a], S.hr[j][a], S.lr[j][a]);
+                split_hl(K.src_im[a * n + g] - ref_im[a], S.hi[j][a], S.li[j][a]);
+                if (K.dlp) {
+                    S.nr[j][a] = (float)K.nrm_re[a * n + g];
+                    S.ni[j][a] = (float)K.nrm_im[a * n + g];
+                }
+            }
+            if (K.slp) {
+                cd v = K.sigma[(int64_t)rhs * K.dens_stride + g];
+                S.sg[j] = cf{(float)v.x, (float)v.y};
+            }
+            if (K.dlp) {
+                cd v = K.tau[(int64_t)rhs * K.dens_stride + g];
+                S.ta[j] = cf{(float)v.x, (float)v.y};
+            }
+        }
+        __syncthreads();
+        if (tvalid) {
+            for (int j = split; j < cn; j += kP2PSplit) {
+                float dr[DIM], di[DIM];
+                bool zero = true;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    float hr = xh_r[a] - S.hr[j][a], lr = xl_r[a] - S.lr[j][a];
+                    float hi = xh_i[a] - S.hi[j][a], li = xl_i[a] - S.li[j][a];
+                    zero = zero && hr == 0.f && lr == 0.f && hi == 0.f && li == 0.f;
+                    dr[a] = hr + lr;
+                    di[a] = hi + li;
+                }
+                if (zero) continue;
+                pair_kernel32<DIM, KER>(dr, di, S.nr[j], S.ni[j], K.slp ? S.sg[j] : cf{0, 0},
+                                        K.dlp ? S.ta[j] : cf{0, 0}, K.slp, K.dlp, kap, K.kappa, acc);
+            }
+        }
+    }
+}
+
+template <int DIM, int KER>
+__device__ __forceinline__ void load_target32(const KParams& K, int ti, bool tvalid, const double* ref_re,
+                                              const double* ref_im, float* xh_r, float* xl_r, float* xh_i,
+                                              float* xl_i) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        double vr = tvalid ? K.trg_re[a * K.n_trg + ti] - ref_re[a] : 0.0;
+        double vi = tvalid ? K.trg_im[a * K.n_trg + ti] - ref_im[a] : 0.0;
+        split_hl(vr, xh_r[a], xl_r[a]);
+        split_hl(vi, xh_i[a], xl_i[a]);
+    }
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p32(KParams K, const int* __restrict__ leaf_boxes,
+                                                       const int* __restrict__ bst, const int* __restrict__ ben,
+                                                       const int* __restrict__ l1off, const int* __restrict__ l1,
+                                                       cd* __restrict__ out, int add) {
+    __shared__ SrcTileF S;
+    __shared__ cd red[kP2PThreads];
+    int b = leaf_boxes[blockIdx.x];
+    int rhs = blockIdx.y;
+    int tl = threadIdx.x % kP2PTargets, split = threadIdx.x / kP2PTargets;
+    int ts = bst[b], te = ben[b];
+    double ref_re[DIM], ref_im[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        ref_re[a] = K.trg_re[a * K.n_trg + ts];
+        ref_im[a] = K.trg_im[a * K.n_trg + ts];
+    }
+    for (int t0 = ts; t0 < te; t0 += kP2PTargets) {
+        int ti = t0 + tl;
+        bool tvalid = ti < te;
+        float xh_r[DIM], xl_r[DIM], xh_i[DIM], xl_i[DIM];
+        load_target32<DIM, KER>(K, ti, tvalid, ref_re, ref_im, xh_r, xl_r, xh_i, xl_i);
+        Kahan acc;
+        for (int q = l1off[b]; q < l1off[b + 1]; ++q) {
+            int a = l1[q];
+            accumulate_sources32<DIM, KER>(S, K, rhs, bst[a], ben[a], tvalid, ref_re, ref_im, xh_r, xl_r, xh_i,
+                                           xl_i, acc, split);
+        }
+        finish_target<DIM, KER>(acc.value(), red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti, add != 0);
+    }
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kP2PThreads) k_direct32(KParams K, cd* __restrict__ out) {
+    __shared__ SrcTileF S;
+    __shared__ cd red[kP2PThreads];
+    int rhs = blockIdx.y;
+    int tl = threadIdx.x % kP2PTargets, split = threadIdx.x / kP2PTargets;
+    int t0 = blockIdx.x * kP2PTargets;
+    int ti = t0 + tl;
+    bool tvalid = ti < K.n_trg;
+    double ref_re[DIM], ref_im[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        ref_re[a] = K.trg_re[a * K.n_trg + t0];
+        ref_im[a] = K.trg_im[a * K.n_trg + t0];
+    }
+    float xh_r[DIM], xl_r[DIM], xh_i[DIM], xl_i[DIM];
+    load_target32<DIM, KER>(K, ti, tvalid, ref_re, ref_im, xh_r, xl_r, xh_i, xl_i);
+    Kahan acc;
+    accumulate_sources32<DIM, KER>(S, K, rhs, 0, (int)K.n_src, tvalid, ref_re, ref_im, xh_r, xl_r, xh_i, xl_i,
+                                   acc, split);
+    finish_target<DIM, KER>(acc.value(), red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti, false);
+}
+
 template <int DIM, int KER>
 static void launch_p2p_t(const KParams& K, const int* leaf_boxes, int nleaves, const int* bst, const int* ben,
-                         const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st) {
+                         const int* l1off, const int* l1, cd* out, int nrhs, bool add, bool mixed, cudaStream_t st) {
     if (nleaves == 0) return;
     dim3 grid(nleaves, nrhs);
-    k_p2p<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, leaf_boxes, bst, ben, l1off, l1, out, add ? 1 : 0);
+    if (mixed) k_p2p32<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, leaf_boxes, bst, ben, l1off, l1, out, add ? 1 : 0);
+    else k_p2p<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, leaf_boxes, bst, ben, l1off, l1, out, add ? 1 : 0);
     CFMM_LAUNCHED();
 }
 
 void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
-                const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st) {
-    if (dim == 2 && ker == CFMM_LAPLACE) launch_p2p_t<2, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, st);
-    else if (dim == 2) launch_p2p_t<2, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, st);
-    else if (ker == CFMM_LAPLACE) launch_p2p_t<3, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, st);
-    else launch_p2p_t<3, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, st);
+                const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
+                bool mixed) {
+    if (dim == 2 && ker == CFMM_LAPLACE) launch_p2p_t<2, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
+    else if (dim == 2) launch_p2p_t<2, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
+    else if (ker == CFMM_LAPLACE) launch_p2p_t<3, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
+    else launch_p2p_t<3, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
 }
 
 template <int DIM, int KER>
-static void launch_direct_t(const KParams& K, cd* out, int nrhs, cudaStream_t st) {
+static void launch_direct_t(const KParams& K, cd* out, int nrhs, bool mixed, cudaStream_t st) {
     dim3 grid((unsigned)((K.n_trg + kP2PTargets - 1) / kP2PTargets), nrhs);
-    k_direct<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, out);
+    if (mixed) k_direct32<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, out);
+    else k_direct<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, out);
     CFMM_LAUNCHED();
 }
 
-void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st) {
+void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st, bool mixed) {
     if (K.n_trg == 0) return;
-    if (dim == 2 && ker == CFMM_LAPLACE) launch_direct_t<2, CFMM_LAPLACE>(K, out, nrhs, st);
-    else if (dim == 2) launch_direct_t<2, CFMM_HELMHOLTZ>(K, out, nrhs, st);
-    else if (ker == CFMM_LAPLACE) launch_direct_t<3, CFMM_LAPLACE>(K, out, nrhs, st);
-    else launch_direct_t<3, CFMM_HELMHOLTZ>(K, out, nrhs, st);
+    if (dim == 2 && ker == CFMM_LAPLACE) launch_direct_t<2, CFMM_LAPLACE>(K, out, nrhs, mixed, st);
+    else if (dim == 2) launch_direct_t<2, CFMM_HELMHOLTZ>(K, out, nrhs, mixed, st);
+    else if (ker == CFMM_LAPLACE) launch_direct_t<3, CFMM_LAPLACE>(K, out, nrhs, mixed, st);
+    else launch_direct_t<3, CFMM_HELMHOLTZ>(K, out, nrhs, mixed, st);
 }
 
 }  // namespace cfmm

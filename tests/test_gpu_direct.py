@@ -42,3 +42,21 @@ def test_direct_separate_targets_and_green_scale(cuda):
                     to_dev(trg.re, cuda), to_dev(trg.im, cuda), to_dev(dens, cuda)).cpu().numpy()[0]
     ref = direct(2, 1, 5.0, src.re + 1j * src.im, trg.re + 1j * trg.im, sigma=dens[0, 0], green_scale=True)
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dim,ker,kap", KERNELS)
+def test_direct_mixed_precision(cuda, dim, ker, kap):
+    """Mixed precision (complex64 kernel arithmetic, FP32 hi/lo differences,
+    compensated sums): max-norm error against the FP64 oracle below 2e-6."""
+    import paper_2509_05458_gb300 as cf
+    g = curve2d(900, seed=7, t_half=6.0) if dim == 2 else surface3d(900, seed=7, half=3.0, rho0=1.0)
+    pts = g.re + 1j * g.im
+    nrm = g.nrm_re + 1j * g.nrm_im
+    dens = densities(g.n, seed=8, nrhs=1, ncomp=2)
+    out = cf.direct(dim, ker | cf.SLP | cf.DLP, kap, to_dev(g.re, cuda), to_dev(g.im, cuda), to_dev(g.re, cuda),
+                    to_dev(g.im, cuda), to_dev(dens, cuda), to_dev(g.nrm_re, cuda), to_dev(g.nrm_im, cuda),
+                    precision=cf.MIXED).cpu().numpy()[0]
+    ref = direct(dim, ker, kap, pts, pts, sigma=dens[0, 0], tau=dens[0, 1], nrm=nrm)
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-6

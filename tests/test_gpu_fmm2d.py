@@ -85,3 +85,35 @@ def test_config2_full_size_sampled(cuda):
     u0 = direct(2, 1, 20.0, pts, pts[idx], sigma=dens[0, 0], tau=dens[0, 1], nrm=nrm)
     err = np.linalg.norm(u[0, idx] - u0) / np.linalg.norm(u0)
     assert err <= eps, err
+
+
+@pytest.mark.parametrize("ker,kap", [(0, 0.0), (1, 20.0)])
+def test_mixed_precision_fmm(cuda, ker, kap):
+    """MIXED: near field in complex64 arithmetic; relative l2 against the FP64
+    oracle FMM (same tree, same P) <= 1e-6 and against the direct sum <= eps."""
+    import paper_2509_05458_gb300 as cf
+    g = curve2d(2500, seed=3, t_half=10.0, height=0.5)
+    eps = 1e-6
+    p = gpu_plan(cf, g, ker, kap, eps, cuda, 24, dlp=True, precision=cf.MIXED)
+    dens = densities(g.n, seed=0, nrhs=1, ncomp=2)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()[0]
+    uo, T = fmm2d.apply(g.re, g.im, ker, kap, eps, 24, sigma=dens[0, 0], tau=dens[0, 1],
+                        nrm_re=g.nrm_re, nrm_im=g.nrm_im)
+    assert relerr_l2(u, uo) <= 1e-6
+    pts = g.re + 1j * g.im
+    u0 = direct(2, ker, kap, pts, pts, sigma=dens[0, 0], tau=dens[0, 1], nrm=g.nrm_re + 1j * g.nrm_im)
+    assert relerr_paper(u, u0, dens[0].reshape(-1)) <= eps
+
+
+def test_config2_mixed_full_size_sampled(cuda):
+    """The benchmark workload in MIXED precision meets eps = 1e-6 on sampled targets."""
+    import paper_2509_05458_gb300 as cf
+    g = config2()
+    eps = 1e-6
+    p = gpu_plan(cf, g, 1, 20.0, eps, cuda, 64, dlp=True, precision=cf.MIXED)
+    dens = densities(g.n, seed=0, nrhs=1, ncomp=2)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()[0]
+    idx = np.random.default_rng(2).choice(g.n, 150, replace=False)
+    pts = g.re + 1j * g.im
+    u0 = direct(2, 1, 20.0, pts, pts[idx], sigma=dens[0, 0], tau=dens[0, 1], nrm=g.nrm_re + 1j * g.nrm_im)
+    assert np.linalg.norm(u[idx] - u0) / np.linalg.norm(u0) <= eps
