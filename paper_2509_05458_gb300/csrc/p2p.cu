@@ -322,21 +322,52 @@ __device__ __forceinline__ void helm2d_pair32(cf r2, float kappa, bool dlp, cf& 
     }
 }
 
+// Error-free transformations (Dekker, Knuth): the product and sum of two
+// floats as an unevaluated hi + lo pair.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (h1 + l1) * (h2 + l2) added to the double-float accumulator (S, E)
+__device__ __forceinline__ void df_fma(float h1, float l1, float h2, float l2, float sgn, float& S, float& E) {
+    float p, e, t;
+    two_prod(h1, h2, p, e);
+    e = fmaf(h1, l2, fmaf(l1, h2, e));
+    two_sum(S, sgn * p, S, t);
+    E += t + sgn * e;
+}
+
+// n . d with the normal and the difference each as FP32 hi + lo: on a smooth
+// curve or surface n is nearly orthogonal to d for close pairs, so n . d
+// cancels; the double-float evaluation keeps its FP32 relative accuracy.
+template <int DIM>
+__device__ __forceinline__ cf dot_nd(const float* dh_r, const float* dl_r, const float* dh_i, const float* dl_i,
+                                     const float* nh_r, const float* nl_r, const float* nh_i, const float* nl_i) {
+    float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        df_fma(nh_r[a], nl_r[a], dh_r[a], dl_r[a], 1.f, Sr, Er);
+        df_fma(nh_i[a], nl_i[a], dh_i[a], dl_i[a], -1.f, Sr, Er);
+        df_fma(nh_r[a], nl_r[a], dh_i[a], dl_i[a], 1.f, Si, Ei);
+        df_fma(nh_i[a], nl_i[a], dh_r[a], dl_r[a], 1.f, Si, Ei);
+    }
+    return cf{Sr + Er, Si + Ei};
+}
+
 template <int DIM, int KER>
-__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const float* nr,
-                                              const float* ni, cf sg, cf ta, bool slp, bool dlp, float kappa,
-                                              double kappa64, Kahan& acc) {
+__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, cf nd, cf sg, cf ta,
+                                              bool slp, bool dlp, float kappa, double kappa64, Kahan& acc) {
     cf d[DIM];
     cf r2 = {0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         d[a] = cf{d_re[a], d_im[a]};
         r2 = r2 + d[a] * d[a];
-    }
-    cf nd = {0.f, 0.f};
-    if (dlp) {
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) nd = nd + cf{nr[a], ni[a]} * d[a];
     }
     cf v = {0.f, 0.f};
     if (DIM == 2 && KER == CFMM_LAPLACE) {
@@ -376,7 +407,7 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
 
 struct SrcTileF {
     float hr[kP2PChunk][3], lr[kP2PChunk][3], hi[kP2PChunk][3], li[kP2PChunk][3];
-    float nr[kP2PChunk][3], ni[kP2PChunk][3];
+    float nhr[kP2PChunk][3], nlr[kP2PChunk][3], nhi[kP2PChunk][3], nli[kP2PChunk][3];
     cf sg[kP2PChunk], ta[kP2PChunk];
 };
 
@@ -402,8 +433,8 @@ __device__ void accumulate_sources32(SrcTileF& S, const KParams& K, int rhs, int
                 split_hl(K.src_re[a * n + g] - ref_re[a], S.hr[j][a], S.lr[j][a]);
                 split_hl(K.src_im[a * n + g] - ref_im[a], S.hi[j][a], S.li[j][a]);
                 if (K.dlp) {
-                    S.nr[j][a] = (float)K.nrm_re[a * n + g];
-                    S.ni[j][a] = (float)K.nrm_im[a * n + g];
+                    split_hl(K.nrm_re[a * n + g], S.nhr[j][a], S.nlr[j][a]);
+                    split_hl(K.nrm_im[a * n + g], S.nhi[j][a], S.nli[j][a]);
                 }
             }
             if (K.slp) {
@@ -418,19 +449,23 @@ __device__ void accumulate_sources32(SrcTileF& S, const KParams& K, int rhs, int
         __syncthreads();
         if (tvalid) {
             for (int j = split; j < cn; j += kP2PSplit) {
-                float dr[DIM], di[DIM];
+                float dr[DIM], di[DIM], hr[DIM], lr[DIM], hi[DIM], li[DIM];
                 bool zero = true;
 #pragma unroll
                 for (int a = 0; a < DIM; ++a) {
-                    float hr = xh_r[a] - S.hr[j][a], lr = xl_r[a] - S.lr[j][a];
-                    float hi = xh_i[a] - S.hi[j][a], li = xl_i[a] - S.li[j][a];
-                    zero = zero && hr == 0.f && lr == 0.f && hi == 0.f && li == 0.f;
-                    dr[a] = hr + lr;
-                    di[a] = hi + li;
+                    hr[a] = xh_r[a] - S.hr[j][a];
+                    lr[a] = xl_r[a] - S.lr[j][a];
+                    hi[a] = xh_i[a] - S.hi[j][a];
+                    li[a] = xl_i[a] - S.li[j][a];
+                    zero = zero && hr[a] == 0.f && lr[a] == 0.f && hi[a] == 0.f && li[a] == 0.f;
+                    dr[a] = hr[a] + lr[a];
+                    di[a] = hi[a] + li[a];
                 }
                 if (zero) continue;
-                pair_kernel32<DIM, KER>(dr, di, S.nr[j], S.ni[j], K.slp ? S.sg[j] : cf{0, 0},
-                                        K.dlp ? S.ta[j] : cf{0, 0}, K.slp, K.dlp, kap, K.kappa, acc);
+                cf nd = {0.f, 0.f};
+                if (K.dlp) nd = dot_nd<DIM>(hr, lr, hi, li, S.nhr[j], S.nlr[j], S.nhi[j], S.nli[j]);
+                pair_kernel32<DIM, KER>(dr, di, nd, K.slp ? S.sg[j] : cf{0, 0}, K.dlp ? S.ta[j] : cf{0, 0},
+                                        K.slp, K.dlp, kap, K.kappa, acc);
             }
         }
     }
