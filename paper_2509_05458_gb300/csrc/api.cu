@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "cfmm_special.cuh"
@@ -22,6 +23,39 @@ void set_error(int status, const std::string& msg) {
 std::atomic<int64_t>& launch_counter() {
     static std::atomic<int64_t> c{0};
     return c;
+}
+
+void* Scratch::take(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (cur_ < chunks_.size()) {
+        if (off_ + bytes <= chunks_[cur_].size) {
+            void* p = chunks_[cur_].p + off_;
+            off_ += bytes;
+            return p;
+        }
+        ++cur_;
+        off_ = 0;
+    }
+    size_t sz = std::max(bytes, (size_t)64 << 20);
+    char* p = nullptr;
+    CFMM_CUDA(cudaMalloc((void**)&p, sz));
+    chunks_.push_back(Chunk{p, sz});
+    cur_ = chunks_.size() - 1;
+    off_ = bytes;
+    return p;
+}
+
+Scratch::~Scratch() {
+    for (auto& c : chunks_) cudaFree(c.p);
+}
+
+Scratch& plan_scratch() {
+    thread_local std::vector<std::unique_ptr<Scratch>> per_dev;
+    int dev = 0;
+    CFMM_CUDA(cudaGetDevice(&dev));
+    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+    if (!per_dev[dev]) per_dev[dev].reset(new Scratch());
+    return *per_dev[dev];
 }
 
 // ---- Gauss-Laguerre rules (generalized, alpha = -1/2 and +1/2) ----------
@@ -120,11 +154,13 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// copy a caller array (host or device) of `count` doubles into a device buffer
-static void stage_in(DevBuf<double>& dst, const double* src, size_t count, cudaStream_t st) {
-    dst.alloc(count);
-    CFMM_CUDA(cudaMemcpyAsync(dst.get(), src, count * sizeof(double),
-                              is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+// a device view of a caller array (host or device) of `count` doubles: device
+// pointers are used in place, host arrays are copied into plan scratch
+static const double* stage_in(const double* src, size_t count, cudaStream_t st) {
+    if (is_device_ptr(src)) return src;
+    double* dst = plan_scratch().take_n<double>(count);
+    CFMM_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    return dst;
 }
 
 template <class F>
@@ -279,17 +315,17 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         CFMM_CUDA(cudaGetDevice(&P->device));
         ensure_device_tables();
         for (auto& e : P->ev) CFMM_CUDA(cudaEventCreate(&e));
-        DevBuf<double> re, im, nre, nim;
+        Scratch& scr = plan_scratch();
+        scr.rewind();
         size_t cnt = (size_t)n * dim;
-        stage_in(re, pts_re, cnt, P->stream);
-        stage_in(im, pts_im, cnt, P->stream);
-        if (dlp) {
-            stage_in(nre, nrm_re, cnt, P->stream);
-            stage_in(nim, nrm_im, cnt, P->stream);
-        }
-        build_tree(P, re.get(), im.get(), dlp ? nre.get() : nullptr, dlp ? nim.get() : nullptr, o.top_level);
+        const double* re = stage_in(pts_re, cnt, P->stream);
+        const double* im = stage_in(pts_im, cnt, P->stream);
+        const double* nre = dlp ? stage_in(nrm_re, cnt, P->stream) : nullptr;
+        const double* nim = dlp ? stage_in(nrm_im, cnt, P->stream) : nullptr;
+        build_tree(P, re, im, nre, nim, o.top_level);
         if (dim == 2) fmm2d_setup(P);
         CFMM_CUDA(cudaStreamSynchronize(P->stream));
+        scr.rewind();
     });
     if (rc != 0) {
         destroy_plan(P);

@@ -117,6 +117,32 @@ struct DevBuf {
     T* get() const { return p; }
 };
 
+// Bump allocator over cached device chunks for the temporaries of plan
+// construction (one per host thread and device). take() never frees; rewind()
+// makes the memory reusable once the work that used it has completed.
+class Scratch {
+   public:
+    void* take(size_t bytes);
+    template <class T>
+    T* take_n(size_t n) {
+        return static_cast<T*>(take((n ? n : 1) * sizeof(T)));
+    }
+    void rewind() {
+        cur_ = 0;
+        off_ = 0;
+    }
+    ~Scratch();
+
+   private:
+    struct Chunk {
+        char* p;
+        size_t size;
+    };
+    std::vector<Chunk> chunks_;
+    size_t cur_ = 0, off_ = 0;
+};
+Scratch& plan_scratch();
+
 // ---------------------------------------------------------------------------
 // constants shared by host and device code of this library
 // ---------------------------------------------------------------------------

@@ -511,6 +511,63 @@ __global__ void k_m2l(M2LArgs A, int first_box, const cd* __restrict__ mp, cd* _
     for (int c = threadIdx.x; c < nc; c += blockDim.x) o[c] = acc[c];
 }
 
+// Helmholtz M2L, warp-parallel over sources: each of the 4 warps of a CTA
+// takes every 4th List-2 source of the box; a lane owns outputs
+// j = lane + 32 o (o < kM2LOut) and accumulates the Toeplitz sums
+// L_j += sum_n T_{n-j} M_n in registers; the four warps' partial sums are
+// combined in a fixed order at the end (bitwise reproducible).
+constexpr int kM2LWarps = 4;
+
+template <int kM2LOut>   // outputs per lane: 2P+1 <= 32 kM2LOut
+__global__ void __launch_bounds__(kM2LWarps * 32) k_m2l_helm(M2LArgs A, int first_box, const cd* __restrict__ mp,
+                                                               cd* __restrict__ loc) {
+    extern __shared__ cd sm[];
+    int b = first_box + blockIdx.x;
+    int rhs = blockIdx.y;
+    int l = A.blevel[b];
+    int P = A.Plev[l];
+    int nc = 2 * P + 1, nt = 4 * P + 1;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cd* my_src = sm + (size_t)w * (nc + nt);
+    cd* my_tab = my_src + nc;
+    cd acc[kM2LOut];
+#pragma unroll
+    for (int o = 0; o < kM2LOut; ++o) acc[o] = cd{0, 0};
+    int q0 = A.loff[b], q1 = A.loff[b + 1];
+    for (int q = q0 + w; q < q1; q += kM2LWarps) {
+        int s = A.lent[q];
+        const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
+        const cd* t = A.tab + A.tbase[l] + (int64_t)(q - A.tq0[l]) * nt;
+        __syncwarp();
+        for (int c = lane; c < nc; c += 32) my_src[c] = m[c];
+        for (int c = lane; c < nt; c += 32) my_tab[c] = t[c];
+        __syncwarp();
+        // L_j += sum_n T[n - j + 2P] M[n + P],  j = lane + 32 o - P
+        for (int nn = 0; nn < nc; ++nn) {
+            cd mv = my_src[nn];
+#pragma unroll
+            for (int o = 0; o < kM2LOut; ++o) {
+                int c = lane + 32 * o;
+                if (c < nc) acc[o] += my_tab[nn - c + nc - 1] * mv;
+            }
+        }
+    }
+    __syncthreads();
+    cd* red = sm;                    // reuse: [warp][nc]
+#pragma unroll
+    for (int o = 0; o < kM2LOut; ++o) {
+        int c = lane + 32 * o;
+        if (c < nc) red[(size_t)w * nc + c] = acc[o];
+    }
+    __syncthreads();
+    cd* out = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        cd v = red[c];
+        for (int ww = 1; ww < kM2LWarps; ++ww) v += red[(size_t)ww * nc + c];
+        out[c] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // M2P (step 5, List 3) and L2P (step 8): one CTA per leaf, one thread per target
 // ---------------------------------------------------------------------------
@@ -849,11 +906,10 @@ void fmm2d_setup(cfmm_plan_s* P) {
             std::vector<int> qbox(ql - qf);
             for (int b = T.level_off[S->l0]; b < T.nboxes; ++b)
                 for (int q = loff[b]; q < loff[b + 1]; ++q) qbox[q - qf] = b;
-            DevBuf<int> dq;
-            dq.alloc(qbox.size());
-            CFMM_CUDA(cudaMemcpyAsync(dq.get(), qbox.data(), sizeof(int) * qbox.size(), cudaMemcpyHostToDevice, st));
+            int* dq = plan_scratch().take_n<int>(qbox.size());
+            CFMM_CUDA(cudaMemcpyAsync(dq, qbox.data(), sizeof(int) * qbox.size(), cudaMemcpyHostToDevice, st));
             int nq = ql - qf;
-            k_tab_m2l<<<(nq + 127) / 128, 128, 0, st>>>(nq, dq.get(), T.lent[1].get(), T.level.get(), S->dPlev.get(),
+            k_tab_m2l<<<(nq + 127) / 128, 128, 0, st>>>(nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
                                                        S->d_m2l_base.get(), S->d_m2l_q0.get(), T.cen_re.get(),
                                                        T.cen_im.get(), P->kappa, S->t_m2l.get(), qf);
             CFMM_LAUNCHED();
@@ -883,6 +939,8 @@ void fmm2d_setup(cfmm_plan_s* P) {
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l<CFMM_LAPLACE>, (const void*)k_m2l<CFMM_HELMHOLTZ>,
+                   (const void*)k_m2l_helm<1>, (const void*)k_m2l_helm<2>, (const void*)k_m2l_helm<4>,
+                   (const void*)k_m2l_helm<8>,
                    (const void*)k_eval<CFMM_LAPLACE>, (const void*)k_eval<CFMM_HELMHOLTZ>})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
 }
@@ -944,10 +1002,26 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
                    T.loff[1].get(), T.lent[1].get(), S->binom.get(), S->NB, S->t_m2l.get(), S->d_m2l_base.get(),
                    S->d_m2l_q0.get()};
         int first = T.level_off[S->l0], nb = T.nboxes - first;
-        size_t smem = sizeof(cd) * (2 * (2 * maxP + 1) + 4 * maxP + 3);
-        dim3 g(nb, nrhs);
-        k_m2l<KER><<<g, 128, smem, st>>>(MA, first, mp, lc);
-        CFMM_LAUNCHED();
+        if (KER == CFMM_HELMHOLTZ && maxP <= 127) {
+            // one launch per level, outputs per lane sized to that level's order
+            for (int l = S->l0; l < T.nlevels; ++l) {
+                int lo = T.level_off[l], nbl = T.level_off[l + 1] - lo;
+                if (nbl == 0) continue;
+                int Pl = S->Plev[l], ncl = 2 * Pl + 1;
+                size_t smem = sizeof(cd) * (size_t)kM2LWarps * ((2 * Pl + 1) + (4 * Pl + 1));
+                dim3 gl(nbl, nrhs);
+                if (ncl <= 32) k_m2l_helm<1><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
+                else if (ncl <= 64) k_m2l_helm<2><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
+                else if (ncl <= 128) k_m2l_helm<4><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
+                else k_m2l_helm<8><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
+                CFMM_LAUNCHED();
+            }
+        } else {
+            dim3 g(nb, nrhs);
+            size_t smem = sizeof(cd) * (2 * (2 * maxP + 1) + 4 * maxP + 3);
+            k_m2l<KER><<<g, 128, smem, st>>>(MA, first, mp, lc);
+            CFMM_LAUNCHED();
+        }
     }
     rec(4);
     // (6) P2L over List 4

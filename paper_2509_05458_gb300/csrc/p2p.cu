@@ -376,7 +376,9 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
     } else if (DIM == 2) {
         float k2 = kappa * kappa;
         cf q = (0.25f * k2) * r2;
-        if (q.x * q.x + q.y * q.y <= 81.f) {
+        // complex64 series only for |kappa r| <= 3 (|q| <= 2.25), where its
+        // terms stay below ~1.3x the result; beyond, the FP64 evaluation
+        if (q.x * q.x + q.y * q.y <= 5.0625f) {
             cf h0, g1;
             helm2d_pair32(r2, kappa, dlp, h0, g1);
             if (slp) v = h0 * sg;

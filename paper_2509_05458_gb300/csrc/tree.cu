@@ -79,20 +79,25 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
         if (idx < n) out[idx] += add;
 }
 
-// exclusive scan in -> out (must not alias); returns the total (synchronises the stream)
-static int64_t scan_exclusive(const int* in, int* out, int n, cudaStream_t st) {
-    if (n <= 0) return 0;
+// exclusive scan in -> out (must not alias), asynchronous
+static void scan_exclusive_async(const int* in, int* out, int n, cudaStream_t st) {
+    if (n <= 0) return;
     int nb = (n + kScanTile - 1) / kScanTile;
-    DevBuf<int> sums, sums_x;
-    sums.alloc(nb);
-    k_scan_tile<<<nb, kScanThreads, 0, st>>>(in, out, n, sums.get());
+    int* sums = plan_scratch().take_n<int>(nb);
+    k_scan_tile<<<nb, kScanThreads, 0, st>>>(in, out, n, sums);
     CFMM_LAUNCHED();
     if (nb > 1) {
-        sums_x.alloc(nb);
-        scan_exclusive(sums.get(), sums_x.get(), nb, st);
-        k_scan_add<<<nb, kScanThreads, 0, st>>>(out, n, sums_x.get());
+        int* sums_x = plan_scratch().take_n<int>(nb);
+        scan_exclusive_async(sums, sums_x, nb, st);
+        k_scan_add<<<nb, kScanThreads, 0, st>>>(out, n, sums_x);
         CFMM_LAUNCHED();
     }
+}
+
+// exclusive scan; returns the total (synchronises the stream)
+static int64_t scan_exclusive(const int* in, int* out, int n, cudaStream_t st) {
+    if (n <= 0) return 0;
+    scan_exclusive_async(in, out, n, st);
     // total = last exclusive value + last input
     int last_out = 0, last_in = 0;
     CFMM_CUDA(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -169,22 +174,21 @@ __global__ void k_iota(int* v, int n) {
 // sorts keys (in place, via ping-pong) with payload; nbits = significant bits
 static void radix_sort(DevBuf<uint64_t>& keys, DevBuf<int>& vals, int n, int nbits, cudaStream_t st) {
     if (n <= 1) return;
-    DevBuf<uint64_t> k2;
-    DevBuf<int> v2, hist, offs;
-    k2.alloc(n);
-    v2.alloc(n);
+    Scratch& scr = plan_scratch();
     int ntiles = (n + kSortTile - 1) / kSortTile;
-    hist.alloc(16 * ntiles);
-    offs.alloc(16 * ntiles);
-    uint64_t *ka = keys.get(), *kb = k2.get();
-    int *va = vals.get(), *vb = v2.get();
+    uint64_t* k2 = scr.take_n<uint64_t>(n);
+    int* v2 = scr.take_n<int>(n);
+    int* hist = scr.take_n<int>(16 * ntiles);
+    int* offs = scr.take_n<int>(16 * ntiles);
+    uint64_t *ka = keys.get(), *kb = k2;
+    int *va = vals.get(), *vb = v2;
     int passes = (nbits + 3) / 4;
     for (int p = 0; p < passes; ++p) {
         int shift = 4 * p;
-        k_sort_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist.get(), ntiles);
+        k_sort_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles);
         CFMM_LAUNCHED();
-        scan_exclusive(hist.get(), offs.get(), 16 * ntiles, st);
-        k_sort_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs.get(), ntiles);
+        scan_exclusive_async(hist, offs, 16 * ntiles, st);
+        k_sort_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs, ntiles);
         CFMM_LAUNCHED();
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -316,10 +320,20 @@ __device__ __forceinline__ bool near_boxes(int la, const int64_t* Ia, int lb, co
 // ---------------------------------------------------------------------------
 // leaves: split passes and level restriction
 // ---------------------------------------------------------------------------
-struct LeafArrays {
-    DevBuf<int> lev, st, en;
-    DevBuf<uint64_t> pre;
+struct LeafArrays {   // device arrays in plan scratch
+    int* lev = nullptr;
+    int* st = nullptr;
+    int* en = nullptr;
+    uint64_t* pre = nullptr;
     int n = 0;
+    void take(int count) {
+        Scratch& s = plan_scratch();
+        lev = s.take_n<int>(count);
+        st = s.take_n<int>(count);
+        en = s.take_n<int>(count);
+        pre = s.take_n<uint64_t>(count);
+        n = count;
+    }
 };
 
 __device__ __forceinline__ void child_bounds(const uint64_t* __restrict__ keys, int s, int e, uint64_t p,
@@ -453,50 +467,35 @@ static inline int blocks_for(int64_t n, int t) { return (int)((n + t - 1) / t); 
 static bool split_pass(LeafArrays& L, const uint64_t* keys, int dim, int B, int Ns, int force,
                        const int* flag, cudaStream_t st) {
     int nl = L.n;
-    DevBuf<int> cnt, off, any;
-    cnt.alloc(nl);
-    off.alloc(nl);
-    any.alloc(1);
-    CFMM_CUDA(cudaMemsetAsync(any.get(), 0, sizeof(int), st));
-    k_leaf_count<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(),
-                                                     keys, dim, B, Ns, force, flag, cnt.get(), any.get());
+    Scratch& scr = plan_scratch();
+    int* cnt = scr.take_n<int>(nl);
+    int* off = scr.take_n<int>(nl);
+    int* any = scr.take_n<int>(1);
+    CFMM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
+    k_leaf_count<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, L.st, L.en, keys, dim, B, Ns, force, flag,
+                                                     cnt, any);
     CFMM_LAUNCHED();
-    int64_t total = scan_exclusive(cnt.get(), off.get(), nl, st);
+    int64_t total = scan_exclusive(cnt, off, nl, st);
     int h = 0;
-    CFMM_CUDA(cudaMemcpyAsync(&h, any.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(&h, any, sizeof(int), cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     if (!h) return false;
     LeafArrays N;
-    N.n = (int)total;
-    N.lev.alloc(N.n);
-    N.pre.alloc(N.n);
-    N.st.alloc(N.n);
-    N.en.alloc(N.n);
-    k_leaf_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(), keys,
-                                                    dim, B, Ns, force, flag, off.get(), N.lev.get(), N.pre.get(),
-                                                    N.st.get(), N.en.get());
+    N.take((int)total);
+    k_leaf_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, L.st, L.en, keys, dim, B, Ns, force, flag,
+                                                    off, N.lev, N.pre, N.st, N.en);
     CFMM_LAUNCHED();
-    CFMM_CUDA(cudaStreamSynchronize(st));
-    std::swap(L.lev.p, N.lev.p);
-    std::swap(L.lev.n, N.lev.n);
-    std::swap(L.pre.p, N.pre.p);
-    std::swap(L.pre.n, N.pre.n);
-    std::swap(L.st.p, N.st.p);
-    std::swap(L.st.n, N.st.n);
-    std::swap(L.en.p, N.en.p);
-    std::swap(L.en.n, N.en.n);
-    L.n = N.n;
+    L = N;
     return true;
 }
 
 static int leaf_maxlevel(LeafArrays& L, cudaStream_t st) {
-    DevBuf<int> m;
-    m.alloc(1);
-    CFMM_CUDA(cudaMemsetAsync(m.get(), 0, sizeof(int), st));
-    k_leaf_maxlevel<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.lev.get(), m.get());
+    int* m = plan_scratch().take_n<int>(1);
+    CFMM_CUDA(cudaMemsetAsync(m, 0, sizeof(int), st));
+    k_leaf_maxlevel<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.lev, m);
     CFMM_LAUNCHED();
     int h = 0;
-    CFMM_CUDA(cudaMemcpyAsync(&h, m.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(&h, m, sizeof(int), cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     return h;
 }
@@ -507,20 +506,18 @@ static void refine(LeafArrays& L, const uint64_t* keys, int dim, int B, int Ns, 
 }
 
 static void balance(LeafArrays& L, const uint64_t* keys, int dim, int B, int k, cudaStream_t st) {
-    DevBuf<int> flag, any;
-    any.alloc(1);
+    int* any = plan_scratch().take_n<int>(1);
     for (;;) {
         int maxl = leaf_maxlevel(L, st);
-        flag.alloc(L.n);
-        CFMM_CUDA(cudaMemsetAsync(any.get(), 0, sizeof(int), st));
-        k_balance_flags<<<blocks_for(L.n, 128), 128, 0, st>>>(L.n, L.lev.get(), L.pre.get(), dim, B, k, maxl,
-                                                             flag.get(), any.get());
+        int* flag = plan_scratch().take_n<int>(L.n);
+        CFMM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
+        k_balance_flags<<<blocks_for(L.n, 128), 128, 0, st>>>(L.n, L.lev, L.pre, dim, B, k, maxl, flag, any);
         CFMM_LAUNCHED();
         int h = 0;
-        CFMM_CUDA(cudaMemcpyAsync(&h, any.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaMemcpyAsync(&h, any, sizeof(int), cudaMemcpyDeviceToHost, st));
         CFMM_CUDA(cudaStreamSynchronize(st));
         if (!h) return;
-        split_pass(L, keys, dim, B, 0, 0, flag.get(), st);
+        split_pass(L, keys, dim, B, 0, 0, flag, st);
     }
 }
 
@@ -853,23 +850,35 @@ __global__ void k_p2p_work(int nb, const int* __restrict__ off, const int* __res
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
+__global__ void k_level_totals(int nlev, int nl, const int* __restrict__ head, const int* __restrict__ idx,
+                               int* __restrict__ tot) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < nlev) tot[m] = idx[(int64_t)m * nl + nl - 1] + head[(int64_t)m * nl + nl - 1];
+}
+
 static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
     TreeDev& T = P->tree;
     int dim = P->dim;
     int maxl = leaf_maxlevel(L, st);
     int nl = L.n;
-    DevBuf<int> head, idx, leaf_box;
-    head.alloc(nl);
-    idx.alloc(nl);
-    leaf_box.alloc(nl);
-    std::vector<int> counts(maxl + 1);
-    // pass 1: counts per level
+    int nlev = maxl + 1;
+    Scratch& scr = plan_scratch();
+    int* head = scr.take_n<int>((size_t)nlev * nl);
+    int* idx = scr.take_n<int>((size_t)nlev * nl);
+    int* leaf_box = scr.take_n<int>(nl);
+    int* tot = scr.take_n<int>(nlev);
+    // head flags and their scans for every level, then all totals in one read
     for (int m = 0; m <= maxl; ++m) {
-        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), dim, m, head.get());
+        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, dim, m, head + (size_t)m * nl);
         CFMM_LAUNCHED();
-        counts[m] = (int)scan_exclusive(head.get(), idx.get(), nl, st);
+        scan_exclusive_async(head + (size_t)m * nl, idx + (size_t)m * nl, nl, st);
     }
-    T.nlevels = maxl + 1;
+    k_level_totals<<<blocks_for(nlev, 64), 64, 0, st>>>(nlev, nl, head, idx, tot);
+    CFMM_LAUNCHED();
+    std::vector<int> counts(nlev);
+    CFMM_CUDA(cudaMemcpyAsync(counts.data(), tot, sizeof(int) * nlev, cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    T.nlevels = nlev;
     T.level_off.assign(T.nlevels + 1, 0);
     for (int m = 0; m <= maxl; ++m) T.level_off[m + 1] = T.level_off[m] + counts[m];
     T.nboxes = T.level_off[T.nlevels];
@@ -884,13 +893,10 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
     T.cbeg.alloc(nb);
     T.cend.alloc(nb);
     for (int m = 0; m <= maxl; ++m) {
-        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), dim, m, head.get());
-        CFMM_LAUNCHED();
-        scan_exclusive(head.get(), idx.get(), nl, st);
-        k_box_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev.get(), L.pre.get(), L.st.get(), L.en.get(), dim,
-                                                       m, T.level_off[m], head.get(), idx.get(), T.level.get(),
+        k_box_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, L.st, L.en, dim, m, T.level_off[m],
+                                                       head + (size_t)m * nl, idx + (size_t)m * nl, T.level.get(),
                                                        T.prefix.get(), T.start.get(), T.end.get(), T.leaf.get(),
-                                                       leaf_box.get());
+                                                       leaf_box);
         CFMM_LAUNCHED();
     }
     T.d_level_off.alloc(T.nlevels + 1);
@@ -900,9 +906,9 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
                                                     T.nlevels, dim, T.parent.get(), T.cbeg.get(), T.cend.get());
     CFMM_LAUNCHED();
     T.leaf_boxes.resize(nl);
-    CFMM_CUDA(cudaMemcpyAsync(T.leaf_boxes.data(), leaf_box.get(), sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(T.leaf_boxes.data(), leaf_box, sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
     T.d_leaf_boxes.alloc(nl);
-    CFMM_CUDA(cudaMemcpyAsync(T.d_leaf_boxes.get(), leaf_box.get(), sizeof(int) * nl, cudaMemcpyDeviceToDevice, st));
+    CFMM_CUDA(cudaMemcpyAsync(T.d_leaf_boxes.get(), leaf_box, sizeof(int) * nl, cudaMemcpyDeviceToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -910,35 +916,33 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
 static void box_stats(cfmm_plan_s* P, cudaStream_t st, std::vector<double>* spread) {
     TreeDev& T = P->tree;
     int dim = P->dim, nb = T.nboxes;
-    DevBuf<double> sum, mn, mx;
-    sum.alloc((size_t)nb * dim);
-    mn.alloc((size_t)nb * dim);
-    mx.alloc((size_t)nb * dim);
+    Scratch& scr = plan_scratch();
+    double* sum = scr.take_n<double>((size_t)nb * dim);
+    double* mn = scr.take_n<double>((size_t)nb * dim);
+    double* mx = scr.take_n<double>((size_t)nb * dim);
     k_leaf_stats<<<blocks_for((int64_t)nb * 32, 256), 256, 0, st>>>(nb, T.leaf.get(), T.start.get(), T.end.get(),
-                                                                   P->xi.get(), P->n, dim, sum.get(), mn.get(),
-                                                                   mx.get());
+                                                                   P->xi.get(), P->n, dim, sum, mn, mx);
     CFMM_LAUNCHED();
     for (int m = T.nlevels - 2; m >= 0; --m) {
         int lo = T.level_off[m], hi = T.level_off[m + 1];
         k_parent_stats<<<blocks_for(hi - lo, 128), 128, 0, st>>>(lo, hi, T.leaf.get(), T.cbeg.get(), T.cend.get(),
-                                                                dim, sum.get(), mn.get(), mx.get());
+                                                                dim, sum, mn, mx);
         CFMM_LAUNCHED();
     }
     T.cen_re.alloc((size_t)nb * dim);
     T.cen_im.alloc((size_t)nb * dim);
     k_centers<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.prefix.get(), T.start.get(), T.end.get(), dim,
-                                                  P->lo[0], P->lo[1], P->lo[2], P->W, sum.get(), T.cen_re.get(),
+                                                  P->lo[0], P->lo[1], P->lo[2], P->W, sum, T.cen_re.get(),
                                                   T.cen_im.get());
     CFMM_LAUNCHED();
     if (spread) {
-        DevBuf<unsigned long long> g;
-        g.alloc(T.nlevels);
-        CFMM_CUDA(cudaMemsetAsync(g.get(), 0, sizeof(unsigned long long) * T.nlevels, st));
+        unsigned long long* g = scr.take_n<unsigned long long>(T.nlevels);
+        CFMM_CUDA(cudaMemsetAsync(g, 0, sizeof(unsigned long long) * T.nlevels, st));
         k_level_spread<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.leaf.get(), T.nlevels, dim,
-                                                           mn.get(), mx.get(), g.get());
+                                                           mn, mx, g);
         CFMM_LAUNCHED();
         std::vector<unsigned long long> h(T.nlevels);
-        CFMM_CUDA(cudaMemcpyAsync(h.data(), g.get(), sizeof(unsigned long long) * T.nlevels,
+        CFMM_CUDA(cudaMemcpyAsync(h.data(), g, sizeof(unsigned long long) * T.nlevels,
                                   cudaMemcpyDeviceToHost, st));
         CFMM_CUDA(cudaStreamSynchronize(st));
         spread->resize(T.nlevels);
@@ -956,13 +960,12 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
     int nb = T.nboxes;
     ListCtx C{nb, T.nlevels, P->dim, P->sep, T.l0, P->B, T.level.get(), T.leaf.get(), T.parent.get(),
               T.prefix.get(), T.d_level_off.get()};
-    DevBuf<int> cnt;
-    cnt.alloc(nb);
+    int* cnt = plan_scratch().take_n<int>(nb);
     for (int w = 0; w < 4; ++w) {
-        k_list_count<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, cnt.get());
+        k_list_count<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, cnt);
         CFMM_LAUNCHED();
         T.loff[w].alloc(nb + 1);
-        int64_t tot = scan_exclusive(cnt.get(), T.loff[w].get(), nb, st);
+        int64_t tot = scan_exclusive(cnt, T.loff[w].get(), nb, st);
         CFMM_REQUIRE(tot < (int64_t)1 << 31, CFMM_EUNSUPPORTED, "interaction list longer than 2^31 entries");
         int t32 = (int)tot;
         CFMM_CUDA(cudaMemcpyAsync(T.loff[w].get() + nb, &t32, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -973,14 +976,13 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
         CFMM_CUDA(cudaStreamSynchronize(st));
     }
     // work counters
-    DevBuf<unsigned long long> acc;
-    acc.alloc(1);
-    CFMM_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(unsigned long long), st));
+    unsigned long long* acc = plan_scratch().take_n<unsigned long long>(1);
+    CFMM_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), st));
     k_p2p_work<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.loff[0].get(), T.lent[0].get(), T.start.get(),
-                                                   T.end.get(), acc.get());
+                                                   T.end.get(), acc);
     CFMM_LAUNCHED();
     unsigned long long h = 0;
-    CFMM_CUDA(cudaMemcpyAsync(&h, acc.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     P->p2p_pairs = (int64_t)h;
     P->m2l_pairs = T.llen[1];
@@ -995,22 +997,21 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     int64_t n = P->n;
     // finite check
     {
-        DevBuf<int> flag;
-        flag.alloc(1);
-        CFMM_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), st));
+        int* flag = plan_scratch().take_n<int>(1);
+        CFMM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
         int g = blocks_for(n * dim, 256);
         g = g > 4096 ? 4096 : g;
-        k_nonfinite<<<g, 256, 0, st>>>(re, n * dim, flag.get());
-        k_nonfinite<<<g, 256, 0, st>>>(im, n * dim, flag.get());
+        k_nonfinite<<<g, 256, 0, st>>>(re, n * dim, flag);
+        k_nonfinite<<<g, 256, 0, st>>>(im, n * dim, flag);
         ::cfmm::count_launch(2);
         if (nre) {
-            k_nonfinite<<<g, 256, 0, st>>>(nre, n * dim, flag.get());
-            k_nonfinite<<<g, 256, 0, st>>>(nim, n * dim, flag.get());
+            k_nonfinite<<<g, 256, 0, st>>>(nre, n * dim, flag);
+            k_nonfinite<<<g, 256, 0, st>>>(nim, n * dim, flag);
             ::cfmm::count_launch(2);
         }
         CFMM_CUDA(cudaGetLastError());
         int h = 0;
-        CFMM_CUDA(cudaMemcpyAsync(&h, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
         CFMM_CUDA(cudaStreamSynchronize(st));
         CFMM_REQUIRE(h == 0, CFMM_ENONFINITE, "points or normals contain NaN or Inf");
     }
@@ -1018,12 +1019,11 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     {
         int nblk = blocks_for(n, 256);
         nblk = nblk > 1024 ? 1024 : nblk;
-        DevBuf<double> part;
-        part.alloc((size_t)nblk * 2 * dim);
-        k_bbox<<<nblk, 256, 0, st>>>(re, n, dim, part.get());
+        double* part = plan_scratch().take_n<double>((size_t)nblk * 2 * dim);
+        k_bbox<<<nblk, 256, 0, st>>>(re, n, dim, part);
         CFMM_LAUNCHED();
         std::vector<double> h((size_t)nblk * 2 * dim);
-        CFMM_CUDA(cudaMemcpyAsync(h.data(), part.get(), sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
         CFMM_CUDA(cudaStreamSynchronize(st));
         double mn[3], mx[3];
         for (int d = 0; d < dim; ++d) {
@@ -1070,18 +1070,14 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     CFMM_CUDA(cudaGetLastError());
     // a3: leaves, level restriction
     LeafArrays L;
-    L.n = 1;
-    L.lev.alloc(1);
-    L.pre.alloc(1);
-    L.st.alloc(1);
-    L.en.alloc(1);
+    L.take(1);
     {
         int z = 0, nn = (int)n;
         uint64_t zp = 0;
-        CFMM_CUDA(cudaMemcpyAsync(L.lev.get(), &z, sizeof(int), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.pre.get(), &zp, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.st.get(), &z, sizeof(int), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.en.get(), &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.lev, &z, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.pre, &zp, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.st, &z, sizeof(int), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaMemcpyAsync(L.en, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
         CFMM_CUDA(cudaStreamSynchronize(st));
     }
     int Ns = P->leaf_size;
