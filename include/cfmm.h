@@ -117,6 +117,18 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps,
  */
 int cfmm_apply(cfmm_plan_t plan, const double* densities, int nrhs, double* out);
 
+/*
+ * cfmm_apply_capture: records one cfmm_apply of device buffers (densities,
+ * out: device pointers, which must stay valid while the graph is used) into a
+ * CUDA graph owned by the plan, replacing any earlier one. The plan must have
+ * been created with a non-NULL stream. Nothing runs during capture.
+ * cfmm_apply_replay: launches the captured graph on the plan's stream
+ * (asynchronous); the result overwrites the captured `out`.
+ * Both return 0 or a negative status.
+ */
+int cfmm_apply_capture(cfmm_plan_t plan, const double* densities, int nrhs, double* out);
+int cfmm_apply_replay(cfmm_plan_t plan);
+
 /* cfmm_destroy: frees the plan; NULL is OK. */
 int cfmm_destroy(cfmm_plan_t plan);
 

@@ -62,6 +62,10 @@ def lib():
     L.cfmm_plan_ex.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, C.POINTER(_Opts)]
     L.cfmm_apply.restype = ci
     L.cfmm_apply.argtypes = [vp, vp, ci, vp]
+    L.cfmm_apply_capture.restype = ci
+    L.cfmm_apply_capture.argtypes = [vp, vp, ci, vp]
+    L.cfmm_apply_replay.restype = ci
+    L.cfmm_apply_replay.argtypes = [vp]
     L.cfmm_destroy.restype = ci
     L.cfmm_destroy.argtypes = [vp]
     L.cfmm_direct.restype = ci
@@ -185,6 +189,18 @@ class Plan:
             raise ValueError(f"densities must be [nrhs, {self.ncomp}, {self.n}]")
         _check(lib().cfmm_apply(self._h, _ptr(d), nrhs, _ptr(out)))
         return out
+
+    def capture(self, densities, out):
+        """Record one apply of CUDA tensors (densities [nrhs, ncomp, n] complex128,
+        out [nrhs, n]) into a CUDA graph owned by the plan; replay() reruns it.
+        The tensors must stay alive and in place while the graph is used."""
+        if not (densities.is_cuda and out.is_cuda and densities.is_contiguous() and out.is_contiguous()):
+            raise ValueError("capture takes contiguous CUDA tensors")
+        self._graph_keep = (densities, out)
+        _check(lib().cfmm_apply_capture(self._h, _ptr(densities), densities.shape[0], _ptr(out)))
+
+    def replay(self):
+        _check(lib().cfmm_apply_replay(self._h))
 
     def info(self):
         inf = _Info()

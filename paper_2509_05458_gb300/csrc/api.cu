@@ -259,6 +259,8 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
 
 static void destroy_plan(cfmm_plan_s* P) {
     if (!P) return;
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
     fmm2d_release(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
@@ -366,6 +368,51 @@ int cfmm_apply(cfmm_plan_t P, const double* densities, int nrhs, double* out) {
             CFMM_CUDA(cudaMemcpyAsync(out, d_out, dout * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
             CFMM_CUDA(cudaStreamSynchronize(P->stream));
         }
+    });
+}
+
+int cfmm_apply_capture(cfmm_plan_t P, const double* densities, int nrhs, double* out) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        CFMM_REQUIRE(P->stream != nullptr, CFMM_EINVAL, "capture needs a plan created on a non-NULL stream");
+        CFMM_REQUIRE(nrhs >= 1 && densities && out, CFMM_EINVAL, "bad arguments");
+        CFMM_REQUIRE(is_device_ptr(densities) && is_device_ptr(out), CFMM_EINVAL, "capture takes device pointers");
+        const cd* d_in = reinterpret_cast<const cd*>(densities);
+        cd* d_out = reinterpret_cast<cd*>(out);
+        bool timing = P->timing;
+        P->timing = false;
+        // one eager apply sizes every workspace, so nothing is allocated while capturing
+        apply_device(P, d_in, nrhs, d_out);
+        CFMM_CUDA(cudaStreamSynchronize(P->stream));
+        if (P->graph_exec) {
+            cudaGraphExecDestroy(P->graph_exec);
+            P->graph_exec = nullptr;
+        }
+        if (P->graph) {
+            cudaGraphDestroy(P->graph);
+            P->graph = nullptr;
+        }
+        CFMM_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            apply_device(P, d_in, nrhs, d_out);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(P->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            P->timing = timing;
+            throw;
+        }
+        CFMM_CUDA(cudaStreamEndCapture(P->stream, &P->graph));
+        CFMM_CUDA(cudaGraphInstantiate(&P->graph_exec, P->graph, 0));
+        P->timing = timing;
+    });
+}
+
+int cfmm_apply_replay(cfmm_plan_t P) {
+    return guarded([&] {
+        CFMM_REQUIRE(P && P->graph_exec, CFMM_EINVAL, "no captured apply");
+        CFMM_CUDA(cudaGraphLaunch(P->graph_exec, P->stream));
+        count_launch();
     });
 }
 

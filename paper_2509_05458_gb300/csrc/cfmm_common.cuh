@@ -200,7 +200,7 @@ struct cfmm_plan_s {
     int64_t ncoef = 0;               // complex coefficients per rhs per kind
     int maxP = 0;
     // workspaces (grown on demand)
-    cfmm::DevBuf<cd> mpole, local, dens_s, out_s;
+    cfmm::DevBuf<cd> mpole, local, dens_s, out_s, m2l_part;
     cfmm::DevBuf<double> staging;
     int ws_nrhs = 0;
     // diagnostics
@@ -208,4 +208,7 @@ struct cfmm_plan_s {
     bool timing = false;
     double step_ms[9] = {0};
     cudaEvent_t ev[10] = {};
+    // captured apply
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 };

@@ -62,6 +62,12 @@ struct Fmm2dState {
     DevBuf<int> d_leaves_l0;
     int n_p2l = 0;                         // boxes with a non-empty List 4
     DevBuf<int> d_p2l_boxes;
+    // Helmholtz M2L work split: chunks of at most kM2LChunk List-2 entries
+    std::vector<int> lvl_chunk0;           // per level: first chunk (levels >= l0), size nlev+1
+    std::vector<int64_t> lvl_part0;        // per level: first partial-sum slot (complex units)
+    DevBuf<int> chunk_box, chunk_q0, chunk_q1, box_chunk0;   // box_chunk0: [nboxes+1]
+    int64_t npart = 0;                     // partial-sum slots per rhs
+    DevBuf<cd> part;
 };
 
 
@@ -568,6 +574,77 @@ __global__ void __launch_bounds__(kM2LWarps * 32) k_m2l_helm(M2LArgs A, int firs
     }
 }
 
+// Helmholtz M2L split into chunks of List-2 entries: one CTA per chunk, thread
+// (c, s) owns output c for source lane s; the S lanes' sums are combined in a
+// fixed order into one partial sum per chunk, and k_m2l_reduce adds the chunks
+// of a box in chunk order (bitwise reproducible, and the long all-pairs lists
+// of the top level are spread over many CTAs).
+constexpr int kM2LChunk = 32;
+
+__global__ void k_m2l_chunk(M2LArgs A, int ch0, const int* __restrict__ chunk_box, const int* __restrict__ cq0,
+                            const int* __restrict__ cq1, int P, int S, cd* __restrict__ part, int64_t part_stride,
+                            const cd* __restrict__ mp) {
+    extern __shared__ cd sm[];
+    int ch = ch0 + blockIdx.x;
+    int rhs = blockIdx.y;
+    int b = chunk_box[ch];
+    int l = A.blevel[b];
+    int nc = 2 * P + 1, nt = 4 * P + 1;
+    int t = threadIdx.x;
+    int c = t % nc, sl = t / nc;
+    bool act = sl < S;
+    cd* msrc = sm;                         // [S][nc]
+    cd* mtab = sm + (size_t)S * nc;        // [S][nt]
+    cd acc = {0, 0};
+    int q0 = cq0[ch], q1 = cq1[ch];
+    for (int qb = q0; qb < q1; qb += S) {
+        __syncthreads();
+        int nsrc = min(S, q1 - qb);
+        for (int i = t; i < nsrc * nc; i += blockDim.x) {
+            int ss = i / nc, cc = i - ss * nc;
+            int src = A.lent[qb + ss];
+            msrc[(size_t)ss * nc + cc] = mp[(int64_t)rhs * A.ncoef + A.eoff[src] + cc];
+        }
+        for (int i = t; i < nsrc * nt; i += blockDim.x) {
+            int ss = i / nt, cc = i - ss * nt;
+            int q = qb + ss;
+            mtab[(size_t)ss * nt + cc] = A.tab[A.tbase[l] + (int64_t)(q - A.tq0[l]) * nt + cc];
+        }
+        __syncthreads();
+        if (act && sl < nsrc) {
+            const cd* ms = msrc + (size_t)sl * nc;
+            const cd* tb = mtab + (size_t)sl * nt + (nc - 1 - c);   // T[n - c + 2P] = tb[n]
+            cd a = acc;
+            for (int nn = 0; nn < nc; ++nn) a += tb[nn] * ms[nn];
+            acc = a;
+        }
+    }
+    __syncthreads();
+    cd* red = sm;                          // [S][nc]
+    if (act) red[(size_t)sl * nc + c] = acc;
+    __syncthreads();
+    if (t < nc) {
+        cd v = red[t];
+        for (int ss = 1; ss < S; ++ss) v += red[(size_t)ss * nc + t];
+        part[(int64_t)rhs * part_stride + (int64_t)(ch - ch0) * nc + t] = v;
+    }
+}
+
+__global__ void k_m2l_reduce(int lo, int nbl, const int* __restrict__ box_chunk0, int ch0, int nc,
+                             const cd* __restrict__ part, int64_t part_stride, const int64_t* __restrict__ eoff,
+                             int64_t ncoef, cd* __restrict__ loc) {
+    int b = lo + blockIdx.x;
+    int rhs = blockIdx.y;
+    int c0 = box_chunk0[b], c1 = box_chunk0[b + 1];
+    cd* out = loc + (int64_t)rhs * ncoef + eoff[b];
+    const cd* pp = part + (int64_t)rhs * part_stride;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        cd v = {0, 0};
+        for (int k = c0; k < c1; ++k) v += pp[(int64_t)(k - ch0) * nc + c];
+        out[c] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // M2P (step 5, List 3) and L2P (step 8): one CTA per leaf, one thread per target
 // ---------------------------------------------------------------------------
@@ -915,6 +992,42 @@ void fmm2d_setup(cfmm_plan_s* P) {
             CFMM_LAUNCHED();
             CFMM_CUDA(cudaStreamSynchronize(st));
         }
+        // List-2 chunks per box (levels >= l0)
+        {
+            std::vector<int> cb, c0v, c1v, bc0(T.nboxes + 1, 0);
+            S->lvl_chunk0.assign(T.nlevels + 1, 0);
+            S->lvl_part0.assign(T.nlevels + 1, 0);
+            int64_t pslot = 0;
+            for (int l = 0; l < T.nlevels; ++l) {
+                S->lvl_chunk0[l] = (int)cb.size();
+                S->lvl_part0[l] = pslot;
+                for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) {
+                    bc0[b] = (int)cb.size();
+                    if (l < S->l0) continue;
+                    for (int q = loff[b]; q < loff[b + 1]; q += kM2LChunk) {
+                        cb.push_back(b);
+                        c0v.push_back(q);
+                        c1v.push_back(std::min(q + kM2LChunk, loff[b + 1]));
+                    }
+                }
+                if (l >= S->l0) pslot += (int64_t)((int)cb.size() - S->lvl_chunk0[l]) * (2 * S->Plev[l] + 1);
+            }
+            S->lvl_chunk0[T.nlevels] = (int)cb.size();
+            S->lvl_part0[T.nlevels] = pslot;
+            bc0[T.nboxes] = (int)cb.size();
+            S->npart = pslot;
+            S->chunk_box.alloc(cb.size());
+            S->chunk_q0.alloc(cb.size());
+            S->chunk_q1.alloc(cb.size());
+            S->box_chunk0.alloc(T.nboxes + 1);
+            if (!cb.empty()) {
+                CFMM_CUDA(cudaMemcpyAsync(S->chunk_box.get(), cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
+                CFMM_CUDA(cudaMemcpyAsync(S->chunk_q0.get(), c0v.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
+                CFMM_CUDA(cudaMemcpyAsync(S->chunk_q1.get(), c1v.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
+            }
+            CFMM_CUDA(cudaMemcpyAsync(S->box_chunk0.get(), bc0.data(), sizeof(int) * (T.nboxes + 1), cudaMemcpyHostToDevice, st));
+            CFMM_CUDA(cudaStreamSynchronize(st));
+        }
         // shift tables for boxes at levels > l0
         std::vector<int64_t> so(T.nboxes, -1);
         int64_t sb = 0;
@@ -940,7 +1053,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l<CFMM_LAPLACE>, (const void*)k_m2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l_helm<1>, (const void*)k_m2l_helm<2>, (const void*)k_m2l_helm<4>,
-                   (const void*)k_m2l_helm<8>,
+                   (const void*)k_m2l_helm<8>, (const void*)k_m2l_chunk,
                    (const void*)k_eval<CFMM_LAPLACE>, (const void*)k_eval<CFMM_HELMHOLTZ>})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
 }
@@ -1002,18 +1115,29 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
                    T.loff[1].get(), T.lent[1].get(), S->binom.get(), S->NB, S->t_m2l.get(), S->d_m2l_base.get(),
                    S->d_m2l_q0.get()};
         int first = T.level_off[S->l0], nb = T.nboxes - first;
-        if (KER == CFMM_HELMHOLTZ && maxP <= 127) {
-            // one launch per level, outputs per lane sized to that level's order
+        if (KER == CFMM_HELMHOLTZ && maxP <= 255) {
+            // chunks of List-2 entries, one launch per level (P fixed per level), then
+            // the per-box reduction of the chunk sums
+            P->m2l_part.alloc((size_t)S->npart * nrhs + 1);
+            cd* part = P->m2l_part.get();
             for (int l = S->l0; l < T.nlevels; ++l) {
                 int lo = T.level_off[l], nbl = T.level_off[l + 1] - lo;
+                int ch0 = S->lvl_chunk0[l], nch = S->lvl_chunk0[l + 1] - ch0;
                 if (nbl == 0) continue;
                 int Pl = S->Plev[l], ncl = 2 * Pl + 1;
-                size_t smem = sizeof(cd) * (size_t)kM2LWarps * ((2 * Pl + 1) + (4 * Pl + 1));
-                dim3 gl(nbl, nrhs);
-                if (ncl <= 32) k_m2l_helm<1><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
-                else if (ncl <= 64) k_m2l_helm<2><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
-                else if (ncl <= 128) k_m2l_helm<4><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
-                else k_m2l_helm<8><<<gl, kM2LWarps * 32, smem, st>>>(MA, lo, mp, lc);
+                cd* pl = part + S->lvl_part0[l];
+                if (nch > 0) {
+                    int Sl = std::max(1, std::min(8, 256 / ncl));
+                    int threads = ((ncl * Sl + 31) / 32) * 32;
+                    size_t smem = sizeof(cd) * (size_t)Sl * (ncl + 4 * Pl + 1);
+                    dim3 gl(nch, nrhs);
+                    k_m2l_chunk<<<gl, threads, smem, st>>>(MA, ch0, S->chunk_box.get(), S->chunk_q0.get(),
+                                                            S->chunk_q1.get(), Pl, Sl, pl, S->npart, mp);
+                    CFMM_LAUNCHED();
+                }
+                dim3 gr(nbl, nrhs);
+                k_m2l_reduce<<<gr, 64, 0, st>>>(lo, nbl, S->box_chunk0.get(), ch0, ncl, pl, S->npart,
+                                                S->exp_off.get(), S->ncoef, lc);
                 CFMM_LAUNCHED();
             }
         } else {

@@ -359,9 +359,23 @@ __device__ __forceinline__ cf dot_nd(const float* dh_r, const float* dl_r, const
     return cf{Sr + Er, Si + Ei};
 }
 
+// r^2 in FP64 from the hi/lo differences (for |kappa r| beyond the complex64
+// range: the phase kappa*r needs more than FP32 relative accuracy there)
+template <int DIM>
+__device__ __forceinline__ cd r2_from_hl(const float* hr, const float* lr, const float* hi, const float* li) {
+    cd r2 = {0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        cd d = {(double)hr[a] + (double)lr[a], (double)hi[a] + (double)li[a]};
+        r2 += d * d;
+    }
+    return r2;
+}
+
 template <int DIM, int KER>
-__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, cf nd, cf sg, cf ta,
-                                              bool slp, bool dlp, float kappa, double kappa64, Kahan& acc) {
+__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const float* hr,
+                                              const float* lr, const float* hi, const float* li, cf nd, cf sg,
+                                              cf ta, bool slp, bool dlp, float kappa, double kappa64, Kahan& acc) {
     cf d[DIM];
     cf r2 = {0.f, 0.f};
 #pragma unroll
@@ -384,9 +398,9 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
             if (slp) v = h0 * sg;
             if (dlp) v = v + (g1 * nd) * ta;
         } else {
-            // large |kappa r|: the FP64 quadrature path, result rounded to FP32
+            // |kappa r| > 3: FP64 r^2 and the FP64 evaluation, result rounded to FP32
             cd h0, g1;
-            helm2d_pair64(cd{r2.x, r2.y}, kappa64, slp, dlp, h0, g1);
+            helm2d_pair64(r2_from_hl<DIM>(hr, lr, hi, li), kappa64, slp, dlp, h0, g1);
             if (slp) v = cf{(float)h0.x, (float)h0.y} * sg;
             if (dlp) v = v + (cf{(float)g1.x, (float)g1.y} * nd) * ta;
         }
@@ -398,9 +412,18 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
     } else {
         cf r = csqrtf_p(r2);
         cf ir = cinvf(r);
-        float e = expf(-kappa * r.y), sn, cs;
-        sincosf(kappa * r.x, &sn, &cs);
-        cf g = cf{e * cs, e * sn} * ir;
+        cf g;
+        float k4 = kappa * kappa * kappa * kappa;
+        if (k4 * (r2.x * r2.x + r2.y * r2.y) <= 81.f) {    // |kappa r| <= 3
+            float e = expf(-kappa * r.y), sn, cs;
+            sincosf(kappa * r.x, &sn, &cs);
+            g = cf{e * cs, e * sn} * ir;
+        } else {
+            // |kappa r| > 3: the phase from an FP64 r
+            cd r64 = csqrt_p(r2_from_hl<DIM>(hr, lr, hi, li));
+            cd e64 = cexp_i(kappa64 * r64);
+            g = cf{(float)e64.x, (float)e64.y} * ir;
+        }
         if (slp) v = g * sg;
         if (dlp) v = v + (nd * (cf{1.f, 0.f} - mul_if(kappa * r)) * g * (ir * ir)) * ta;
     }
@@ -466,8 +489,8 @@ __device__ void accumulate_sources32(SrcTileF& S, const KParams& K, int rhs, int
                 if (zero) continue;
                 cf nd = {0.f, 0.f};
                 if (K.dlp) nd = dot_nd<DIM>(hr, lr, hi, li, S.nhr[j], S.nlr[j], S.nhi[j], S.nli[j]);
-                pair_kernel32<DIM, KER>(dr, di, nd, K.slp ? S.sg[j] : cf{0, 0}, K.dlp ? S.ta[j] : cf{0, 0},
-                                        K.slp, K.dlp, kap, K.kappa, acc);
+                pair_kernel32<DIM, KER>(dr, di, hr, lr, hi, li, nd, K.slp ? S.sg[j] : cf{0, 0},
+                                        K.dlp ? S.ta[j] : cf{0, 0}, K.slp, K.dlp, kap, K.kappa, acc);
             }
         }
     }

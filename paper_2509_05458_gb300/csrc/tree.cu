@@ -700,138 +700,137 @@ struct ListCtx {
     const int* loff;
 };
 
-template <class Emit>
-__device__ void enumerate_window(const ListCtx& C, int m, const int64_t* lo, const int64_t* hi, Emit emit) {
-    if (m < 0 || m >= C.nlev) return;
-    int64_t J[3] = {lo[0], lo[1], C.dim > 2 ? lo[2] : 0};
-    for (int d = 0; d < C.dim; ++d)
-        if (lo[d] > hi[d]) return;
-    for (;;) {
-        emit(J);
-        int d = 0;
-        for (; d < C.dim; ++d) {
-            if (J[d] < hi[d]) { ++J[d]; break; }
-            J[d] = lo[d];
-        }
-        if (d == C.dim) break;
+// One warp per box. Candidates of each enumeration window are split over the
+// lanes; a ballot keeps the window order, so counts and entries are
+// deterministic. Entries are then sorted by box index.
+struct Window {
+    int m;                  // level of the candidates
+    int64_t lo[3], len[3];  // per-axis start and extent
+    int64_t total;
+};
+
+__device__ __forceinline__ void window_J(const Window& W, int dim, int64_t i, int64_t* J) {
+    for (int d = 0; d < dim; ++d) {
+        J[d] = W.lo[d] + i % W.len[d];
+        i /= W.len[d];
     }
 }
 
-// which: 0..3 = List 1..4. out == nullptr: count only.
-__device__ int list_entries(const ListCtx& C, int which, int b, int* out) {
+// which: 0..3 = List 1..4; out == nullptr counts only. Returns the count (all lanes).
+__device__ int list_entries_warp(const ListCtx& C, int which, int b, int* out) {
+    const int lane = threadIdx.x & 31;
     int m0 = C.level[b];
     if (m0 < C.l0) return 0;
     int dim = C.dim, k = C.k;
     int64_t I[3];
     decode(C.pre[b], m0, dim, I);
     int cnt = 0;
-    if (which == 0) {
-        if (!C.leaf[b]) return 0;
-        for (int m = m0 - 1; m <= m0 + 1; ++m) {
-            if (m < 0 || m >= C.nlev) continue;
-            int64_t lo[3], hi[3];
-            for (int d = 0; d < dim; ++d) near_range(m0, I[d], m, k, &lo[d], &hi[d]);
-            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
-                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
-                if (c >= 0 && C.leaf[c]) {
-                    if (out) out[cnt] = c;
-                    ++cnt;
-                }
-            });
-        }
-    } else if (which == 1) {
-        if (m0 == C.l0) {
-            for (int c = C.loff[m0]; c < C.loff[m0 + 1]; ++c) {
+    // emit helper: every lane holds a candidate result (c or -1)
+    auto flush = [&](int c) {
+        unsigned mask = __ballot_sync(0xffffffffu, c >= 0);
+        if (c >= 0 && out) out[cnt + __popc(mask & ((1u << lane) - 1u))] = c;
+        cnt += __popc(mask);
+    };
+    if (which == 1 && m0 == C.l0) {
+        // all boxes of the top level that are not near b
+        for (int base = C.loff[m0]; base < C.loff[m0 + 1]; base += 32) {
+            int c = base + lane;
+            int r = -1;
+            if (c < C.loff[m0 + 1]) {
                 int64_t J[3];
                 decode(C.pre[c], m0, dim, J);
-                if (!near_boxes(m0, I, m0, J, dim, k)) {
-                    if (out) out[cnt] = c;
-                    ++cnt;
-                }
+                if (!near_boxes(m0, I, m0, J, dim, k)) r = c;
             }
-        } else {
-            int64_t lo[3], hi[3];
-            for (int d = 0; d < dim; ++d) {
-                int64_t ip = I[d] >> 1;
-                lo[d] = 2 * (ip - k);
-                hi[d] = 2 * (ip + k) + 1;
-                int64_t top = (1ll << m0) - 1;
-                lo[d] = lo[d] < 0 ? 0 : lo[d];
-                hi[d] = hi[d] > top ? top : hi[d];
-            }
-            enumerate_window(C, m0, lo, hi, [&](const int64_t* J) {
-                if (near_boxes(m0, I, m0, J, dim, k)) return;
-                int c = find_box(C.pre, C.loff, C.nlev, m0, encode(J, m0, dim));
-                if (c >= 0) {
-                    if (out) out[cnt] = c;
-                    ++cnt;
-                }
-            });
+            flush(r);
         }
-    } else if (which == 2) {
-        if (!C.leaf[b]) return 0;
-        for (int m = m0 + 1; m <= m0 + 2; ++m) {
-            if (m >= C.nlev) continue;
-            int64_t lo[3], hi[3];
-            for (int d = 0; d < dim; ++d) {
+        return cnt;
+    }
+    if (which == 0 && !C.leaf[b]) return 0;
+    if (which == 2 && !C.leaf[b]) return 0;
+    if (which == 3 && m0 < 1) return 0;
+    // windows per list
+    int mlo, mhi;
+    if (which == 0) { mlo = m0 - 1; mhi = m0 + 1; }
+    else if (which == 1) { mlo = mhi = m0; }
+    else if (which == 2) { mlo = m0 + 1; mhi = m0 + 2; }
+    else { mlo = m0 - 2; mhi = m0 - 1; }
+    for (int m = mlo; m <= mhi; ++m) {
+        if (m < 0 || m >= C.nlev) continue;
+        if (which == 3 && m < C.l0) continue;
+        Window w;
+        w.m = m;
+        w.total = 1;
+        bool empty = false;
+        for (int d = 0; d < dim; ++d) {
+            int64_t lo, hi;
+            if (which == 0) {
+                near_range(m0, I[d], m, k, &lo, &hi);
+            } else if (which == 1) {
+                int64_t ip = I[d] >> 1, top = (1ll << m0) - 1;
+                lo = 2 * (ip - k);
+                hi = 2 * (ip + k) + 1;
+                lo = lo < 0 ? 0 : lo;
+                hi = hi > top ? top : hi;
+            } else if (which == 2) {
                 int64_t plo, phi;
                 near_range(m0, I[d], m - 1, k, &plo, &phi);
-                lo[d] = 2 * plo;
-                hi[d] = 2 * phi + 1;
+                lo = 2 * plo;
+                hi = 2 * phi + 1;
+            } else {
+                near_range(m0 - 1, I[d] >> 1, m, k, &lo, &hi);
             }
-            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
-                if (near_boxes(m0, I, m, J, dim, k)) return;
-                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
-                if (c >= 0) {
-                    if (out) out[cnt] = c;
-                    ++cnt;
-                }
-            });
+            if (hi < lo) empty = true;
+            w.lo[d] = lo;
+            w.len[d] = hi - lo + 1;
+            w.total *= empty ? 0 : w.len[d];
         }
-    } else {
-        if (m0 < 1) return 0;
-        int64_t Ip[3];
-        for (int d = 0; d < dim; ++d) Ip[d] = I[d] >> 1;
-        for (int m = m0 - 2; m <= m0 - 1; ++m) {
-            if (m < C.l0) continue;
-            int64_t lo[3], hi[3];
-            for (int d = 0; d < dim; ++d) near_range(m0 - 1, Ip[d], m, k, &lo[d], &hi[d]);
-            enumerate_window(C, m, lo, hi, [&](const int64_t* J) {
-                if (near_boxes(m0, I, m, J, dim, k)) return;
-                int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
-                if (c >= 0 && C.leaf[c]) {
-                    if (out) out[cnt] = c;
-                    ++cnt;
+        if (empty) continue;
+        for (int64_t base = 0; base < w.total; base += 32) {
+            int64_t i = base + lane;
+            int r = -1;
+            if (i < w.total) {
+                int64_t J[3];
+                window_J(w, dim, i, J);
+                bool ok = true;
+                if (which == 1 || which == 2 || which == 3) ok = !near_boxes(m0, I, m, J, dim, k);
+                if (ok) {
+                    int c = find_box(C.pre, C.loff, C.nlev, m, encode(J, m, dim));
+                    if (c >= 0 && (which == 0 || which == 3 ? C.leaf[c] != 0 : true)) r = c;
                 }
-            });
+            }
+            flush(r);
         }
     }
     return cnt;
 }
 
 __global__ void k_list_count(ListCtx C, int which, int* __restrict__ cnt) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= C.nb) return;
-    cnt[b] = C.nb == 1 ? (which == 0 ? 1 : 0) : list_entries(C, which, b, nullptr);
+    int c = C.nb == 1 ? (which == 0 ? 1 : 0) : list_entries_warp(C, which, b, nullptr);
+    if ((threadIdx.x & 31) == 0) cnt[b] = c;
 }
 
 __global__ void k_list_fill(ListCtx C, int which, const int* __restrict__ off, int* __restrict__ ent) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= C.nb) return;
     int* out = ent + off[b];
     if (C.nb == 1) {
-        if (which == 0) out[0] = 0;
+        if (which == 0 && (threadIdx.x & 31) == 0) out[0] = 0;
         return;
     }
-    int c = list_entries(C, which, b, out);
-    // insertion sort by box index (windows are enumerated in coordinate order)
-    for (int i = 1; i < c; ++i) {
-        int v = out[i], j = i - 1;
-        while (j >= 0 && out[j] > v) {
-            out[j + 1] = out[j];
-            --j;
+    int c = list_entries_warp(C, which, b, out);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        // insertion sort by box index (windows are enumerated in coordinate order)
+        for (int i = 1; i < c; ++i) {
+            int v = out[i], j = i - 1;
+            while (j >= 0 && out[j] > v) {
+                out[j + 1] = out[j];
+                --j;
+            }
+            out[j + 1] = v;
         }
-        out[j + 1] = v;
     }
 }
 
@@ -962,7 +961,7 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
               T.prefix.get(), T.d_level_off.get()};
     int* cnt = plan_scratch().take_n<int>(nb);
     for (int w = 0; w < 4; ++w) {
-        k_list_count<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, cnt);
+        k_list_count<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(C, w, cnt);
         CFMM_LAUNCHED();
         T.loff[w].alloc(nb + 1);
         int64_t tot = scan_exclusive(cnt, T.loff[w].get(), nb, st);
@@ -971,7 +970,7 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
         CFMM_CUDA(cudaMemcpyAsync(T.loff[w].get() + nb, &t32, sizeof(int), cudaMemcpyHostToDevice, st));
         T.llen[w] = tot;
         T.lent[w].alloc(tot > 0 ? tot : 1);
-        k_list_fill<<<blocks_for(nb, 64), 64, 0, st>>>(C, w, T.loff[w].get(), T.lent[w].get());
+        k_list_fill<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(C, w, T.loff[w].get(), T.lent[w].get());
         CFMM_LAUNCHED();
         CFMM_CUDA(cudaStreamSynchronize(st));
     }

@@ -117,3 +117,15 @@ def test_config2_mixed_full_size_sampled(cuda):
     pts = g.re + 1j * g.im
     u0 = direct(2, 1, 20.0, pts, pts[idx], sigma=dens[0, 0], tau=dens[0, 1], nrm=g.nrm_re + 1j * g.nrm_im)
     assert np.linalg.norm(u[idx] - u0) / np.linalg.norm(u0) <= eps
+
+
+def test_autotuned_leaf_size_runs(cuda):
+    """The leaf-size autotuner times real applies and returns one of its candidates."""
+    import torch
+    from paper_2509_05458_gb300 import autotune, HELMHOLTZ, SLP, MIXED
+    g = curve2d(20000, seed=9, t_half=20.0)
+    t = lambda a: torch.from_numpy(a).to(cuda)
+    best, times = autotune.tune_leaf_size(2, HELMHOLTZ | SLP, 10.0, 1e-6, t(g.re), t(g.im), precision=MIXED,
+                                          candidates=(32, 64, 128), reps=2)
+    assert best in (32, 64, 128) and set(times) == {32, 64, 128}
+    assert all(v > 0 for v in times.values())
