@@ -34,6 +34,8 @@ dz T_n^m = -T_{n+1}^m (finite-difference pinned).
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 from . import tree as tr
@@ -155,52 +157,67 @@ class Laplace3D:
 
     @staticmethod
     def m2m(Pc, Pp, M, a):
-        """a = c_child - c_parent."""
+        """a = c_child - c_parent: M_n^m(c) = sum_{k,l} (-1)^l U_k^l(a) M_{n-k}^{m+l}."""
         U = regular(Pp, a[None, :])[:, 0]
-        out = np.zeros((M.shape[0], (Pp + 1) ** 2), complex)
-        for n in range(Pp + 1):
-            for m in range(-n, n + 1):
-                acc = 0
-                for k in range(0, n + 1):
-                    nk = n - k
-                    if nk > Pc:
-                        continue
-                    for l in range(-k, k + 1):
-                        if abs(m + l) > nk:
-                            continue
-                        acc = acc + (-1) ** l * U[idx(k, l)] * M[:, idx(nk, m + l)]
-                out[:, idx(n, m)] = acc
-        return out
+        I, S, K = _m2m_index(Pc, Pp)
+        mat = np.where(K, S * U[I], 0.0)
+        return M @ mat.T
 
     @staticmethod
     def m2l(P, M, X0):
-        """X0 = c_t - c_s."""
+        """X0 = c_t - c_s: L_k^l = (-1)^{k+l} sum_{n,m} M_n^m T_{n+k}^{m-l}(X0)."""
         T = irregular(2 * P, X0[None, :])[:, 0]
-        out = np.zeros_like(M)
-        for k in range(P + 1):
-            for l in range(-k, k + 1):
-                acc = 0
-                for n in range(P + 1):
-                    for m in range(-n, n + 1):
-                        acc = acc + M[:, idx(n, m)] * T[idx(n + k, m - l)]
-                out[:, idx(k, l)] = (-1) ** (k + l) * acc
-        return out
+        I, S = _m2l_index(P)
+        return M @ (S * T[I]).T
 
     @staticmethod
     def l2l(Pp, Pc, L, a):
-        """a = c_child - c_parent."""
+        """a = c_child - c_parent: L'_k^l = sum_{n,m} L_n^m U_{n-k}^{m-l}(a)."""
         U = regular(Pp, a[None, :])[:, 0]
-        out = np.zeros((L.shape[0], (Pc + 1) ** 2), complex)
-        for k in range(Pc + 1):
-            for l in range(-k, k + 1):
-                acc = 0
-                for n in range(k, Pp + 1):
-                    for m in range(-n, n + 1):
-                        if abs(m - l) > n - k:
-                            continue
-                        acc = acc + L[:, idx(n, m)] * U[idx(n - k, m - l)]
-                out[:, idx(k, l)] = acc
-        return out
+        I, K = _l2l_index(Pp, Pc)
+        mat = np.where(K, U[I], 0.0)
+        return L @ mat.T
+
+
+def _nm(P):
+    return [(n, m) for n in range(P + 1) for m in range(-n, n + 1)]
+
+
+@functools.lru_cache(maxsize=None)
+def _m2m_index(Pc, Pp):
+    rows, cols = _nm(Pp), _nm(Pc)
+    I = np.zeros((len(rows), len(cols)), int)
+    S = np.zeros((len(rows), len(cols)))
+    K = np.zeros((len(rows), len(cols)), bool)
+    for r, (n, m) in enumerate(rows):
+        for c, (n2, m2) in enumerate(cols):
+            k, l = n - n2, m2 - m
+            if 0 <= k and abs(l) <= k:
+                I[r, c], S[r, c], K[r, c] = idx(k, l), (-1) ** l, True
+    return I, S, K
+
+
+@functools.lru_cache(maxsize=None)
+def _m2l_index(P):
+    nm = _nm(P)
+    I = np.zeros((len(nm), len(nm)), int)
+    S = np.zeros((len(nm), len(nm)))
+    for r, (k, l) in enumerate(nm):
+        for c, (n, m) in enumerate(nm):
+            I[r, c], S[r, c] = idx(n + k, m - l), (-1) ** (k + l)
+    return I, S
+
+
+@functools.lru_cache(maxsize=None)
+def _l2l_index(Pp, Pc):
+    rows, cols = _nm(Pc), _nm(Pp)
+    I = np.zeros((len(rows), len(cols)), int)
+    K = np.zeros((len(rows), len(cols)), bool)
+    for r, (k, l) in enumerate(rows):
+        for c, (n, m) in enumerate(cols):
+            if n >= k and abs(m - l) <= n - k:
+                I[r, c], K[r, c] = idx(n - k, m - l), True
+    return I, K
 
 
 def expansion_orders(T, eps):

@@ -230,18 +230,8 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
         CFMM_LAUNCHED();
     }
     record(P, 1);
-    if (P->dim == 2) {
-        fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
-    } else {
-        // 3D: near field over List 1 only when the tree is a single leaf
-        CFMM_REQUIRE(P->tree.nboxes == 1, CFMM_EUNSUPPORTED, "3D FMM translations are not built yet");
-        KParams K{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->xr.get(), P->xi.get(), n, n,
-                  sg, ta, n, P->slp, P->dlp, P->kappa};
-        for (int i = 2; i <= 7; ++i) record(P, i);
-        launch_p2p(P->dim, P->kernel, K, P->tree.d_leaf_boxes.get(), P->tree.nleaves, P->tree.start.get(),
-                   P->tree.end.get(), P->tree.loff[0].get(), P->tree.lent[0].get(), P->out_s.get(), nrhs, false, st,
-                   P->precision == CFMM_MIXED);
-    }
+    if (P->dim == 2) fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
+    else fmm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
     record(P, 8);
     cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
     k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, scale, out);
@@ -262,6 +252,7 @@ static void destroy_plan(cfmm_plan_s* P) {
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     if (P->graph) cudaGraphDestroy(P->graph);
     fmm2d_release(P);
+    fmm3d_release(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     delete P;
@@ -326,6 +317,7 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         const double* nim = dlp ? stage_in(nrm_im, cnt, P->stream) : nullptr;
         build_tree(P, re, im, nre, nim, o.top_level);
         if (dim == 2) fmm2d_setup(P);
+        else fmm3d_setup(P);
         CFMM_CUDA(cudaStreamSynchronize(P->stream));
         scr.rewind();
     });

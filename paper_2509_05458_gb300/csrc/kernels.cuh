@@ -42,6 +42,11 @@ int direct_noalloc(int dim, int kernel, double k, const double* src_re, const do
                    const double* nrm_im, int64_t m, const double* trg_re, const double* trg_im, int64_t n,
                    const double* densities, int nrhs, double* out, void* stream);
 
+// 3D Laplace expansions (fmm3d.cu)
+void fmm3d_setup(cfmm_plan_s* P);
+void fmm3d_release(cfmm_plan_s* P);
+void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+
 void upload_lag_rule_p2p();
 void upload_lag_rule_fmm2d();
 
