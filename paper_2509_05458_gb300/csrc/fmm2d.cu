@@ -24,7 +24,9 @@
 // Helmholtz translation tables depend only on the geometry and are built
 // once per plan (one table per List-2 pair and per child box).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "cfmm_special.cuh"
@@ -887,6 +889,20 @@ constexpr double kPHeadroomHelm = 0.01;
 void fmm2d_setup(cfmm_plan_s* P) {
     TreeDev& T = P->tree;
     cudaStream_t st = P->stream;
+    const char* prof = getenv("CFMM_PLAN_PROFILE");
+    auto t_start = std::chrono::steady_clock::now();
+    struct Done {
+        const char* prof;
+        cudaStream_t st;
+        std::chrono::steady_clock::time_point t0;
+        ~Done() {
+            if (prof && prof[0] == '1') {
+                cudaStreamSynchronize(st);
+                fprintf(stderr, "[cfmm plan] %-14s %8.3f ms\n", "setup2d",
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+            }
+        }
+    } done{prof, st, t_start};
     Fmm2dState* S = new Fmm2dState();
     {
         std::lock_guard<std::mutex> lk(g_ext_mu);

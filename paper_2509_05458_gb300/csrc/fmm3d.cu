@@ -483,8 +483,9 @@ void fmm3d_setup(cfmm_plan_s* P) {
     S->nlev = T.nlevels;
     S->Plev.assign(T.nlevels, nterms_laplace3(P->sep, P->eps * 0.1));
     P->P = S->Plev;
-    if (T.nboxes <= 1) return;
-    CFMM_REQUIRE(P->kernel == CFMM_LAPLACE, CFMM_EUNSUPPORTED, "3D Helmholtz translations are not built yet");
+    // 3D Helmholtz: the tree and lists are built; the apply reports that its
+    // translations are not (unless the tree is a single leaf)
+    if (T.nboxes <= 1 || P->kernel != CFMM_LAPLACE) return;
     int maxP = S->Plev[0];
     CFMM_REQUIRE(maxP <= 40, CFMM_EUNSUPPORTED, "3D Laplace: expansion order above 40 (eps too small)");
     S->maxP = maxP;
@@ -534,6 +535,8 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     KParams K{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->xr.get(), P->xi.get(), P->n, P->n,
               sigma, tau, dstride, P->slp, P->dlp, P->kappa};
     bool mixed = P->precision == CFMM_MIXED;
+    CFMM_REQUIRE(T.nboxes <= 1 || P->kernel == CFMM_LAPLACE, CFMM_EUNSUPPORTED,
+                 "3D Helmholtz translations are not built yet");
     if (T.nboxes <= 1) {
         for (int i = 2; i <= 6; ++i) rec(i);
         launch_p2p(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),

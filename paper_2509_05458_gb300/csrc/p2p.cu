@@ -359,22 +359,30 @@ __device__ __forceinline__ cf dot_nd(const float* dh_r, const float* dl_r, const
     return cf{Sr + Er, Si + Ei};
 }
 
-// r^2 in FP64 from the hi/lo differences (for |kappa r| beyond the complex64
-// range: the phase kappa*r needs more than FP32 relative accuracy there)
+// The hi/lo parts of a target and a source (offsets from the block's
+// reference point), for pairs that need the difference in FP64.
+struct PairHL {
+    const float *xhr, *xlr, *xhi, *xli;   // target
+    const float *yhr, *ylr, *yhi, *yli;   // source
+};
+
+// r^2 in FP64 from the hi/lo parts (for |kappa r| beyond the complex64 range:
+// the phase kappa*r needs more than FP32 relative accuracy there, and the
+// FP32 difference of the hi parts is not exact for distant pairs)
 template <int DIM>
-__device__ __forceinline__ cd r2_from_hl(const float* hr, const float* lr, const float* hi, const float* li) {
+__device__ __forceinline__ cd r2_from_hl(const PairHL& H) {
     cd r2 = {0.0, 0.0};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        cd d = {(double)hr[a] + (double)lr[a], (double)hi[a] + (double)li[a]};
+        cd d = {((double)H.xhr[a] - (double)H.yhr[a]) + ((double)H.xlr[a] - (double)H.ylr[a]),
+                ((double)H.xhi[a] - (double)H.yhi[a]) + ((double)H.xli[a] - (double)H.yli[a])};
         r2 += d * d;
     }
     return r2;
 }
 
 template <int DIM, int KER>
-__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const float* hr,
-                                              const float* lr, const float* hi, const float* li, cf nd, cf sg,
+__device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const PairHL& H, cf nd, cf sg,
                                               cf ta, bool slp, bool dlp, float kappa, double kappa64, Kahan& acc) {
     cf d[DIM];
     cf r2 = {0.f, 0.f};
@@ -400,7 +408,7 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
         } else {
             // |kappa r| > 3: FP64 r^2 and the FP64 evaluation, result rounded to FP32
             cd h0, g1;
-            helm2d_pair64(r2_from_hl<DIM>(hr, lr, hi, li), kappa64, slp, dlp, h0, g1);
+            helm2d_pair64(r2_from_hl<DIM>(H), kappa64, slp, dlp, h0, g1);
             if (slp) v = cf{(float)h0.x, (float)h0.y} * sg;
             if (dlp) v = v + (cf{(float)g1.x, (float)g1.y} * nd) * ta;
         }
@@ -420,7 +428,7 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
             g = cf{e * cs, e * sn} * ir;
         } else {
             // |kappa r| > 3: the phase from an FP64 r
-            cd r64 = csqrt_p(r2_from_hl<DIM>(hr, lr, hi, li));
+            cd r64 = csqrt_p(r2_from_hl<DIM>(H));
             cd e64 = cexp_i(kappa64 * r64);
             g = cf{(float)e64.x, (float)e64.y} * ir;
         }
@@ -489,8 +497,9 @@ __device__ void accumulate_sources32(SrcTileF& S, const KParams& K, int rhs, int
                 if (zero) continue;
                 cf nd = {0.f, 0.f};
                 if (K.dlp) nd = dot_nd<DIM>(hr, lr, hi, li, S.nhr[j], S.nlr[j], S.nhi[j], S.nli[j]);
-                pair_kernel32<DIM, KER>(dr, di, hr, lr, hi, li, nd, K.slp ? S.sg[j] : cf{0, 0},
-                                        K.dlp ? S.ta[j] : cf{0, 0}, K.slp, K.dlp, kap, K.kappa, acc);
+                PairHL H{xh_r, xl_r, xh_i, xl_i, S.hr[j], S.lr[j], S.hi[j], S.li[j]};
+                pair_kernel32<DIM, KER>(dr, di, H, nd, K.slp ? S.sg[j] : cf{0, 0}, K.dlp ? S.ta[j] : cf{0, 0},
+                                        K.slp, K.dlp, kap, K.kappa, acc);
             }
         }
     }

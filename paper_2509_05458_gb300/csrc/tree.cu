@@ -17,11 +17,34 @@
 //   level restriction: no leaf near a box two levels finer;
 //   Lists as in Sec. 6.2 with the top expansion level l0.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 
 #include "cfmm_common.cuh"
 
 namespace cfmm {
+
+// Optional host-side phase timing of plan construction (CFMM_PLAN_PROFILE=1):
+// each phase is synchronised and its wall time printed to stderr.
+struct PhaseTimer {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t;
+    explicit PhaseTimer(cudaStream_t s) : st(s) {
+        const char* e = getenv("CFMM_PLAN_PROFILE");
+        on = e && e[0] == '1';
+        t = std::chrono::steady_clock::now();
+    }
+    void mark(const char* name) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[cfmm plan] %-14s %8.3f ms\n", name,
+                std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 (any length), returns the total
@@ -994,6 +1017,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     cudaStream_t st = P->stream;
     int dim = P->dim;
     int64_t n = P->n;
+    PhaseTimer pt(st);
     // finite check
     {
         int* flag = plan_scratch().take_n<int>(1);
@@ -1045,6 +1069,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
             P->lo[d] = c - W * 0.5;
         }
     }
+    pt.mark("check+bbox");
     // a2: keys, stable radix sort, gather
     P->B = dim == 2 ? 31 : 21;
     int B = P->B;
@@ -1067,6 +1092,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         ::cfmm::count_launch(2);
     }
     CFMM_CUDA(cudaGetLastError());
+    pt.mark("keys+sort");
     // a3: leaves, level restriction
     LeafArrays L;
     L.take(1);
@@ -1081,8 +1107,11 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     }
     int Ns = P->leaf_size;
     refine(L, P->keys.get(), dim, B, Ns, 0, st);
+    pt.mark("refine");
     balance(L, P->keys.get(), dim, B, P->sep, st);
+    pt.mark("balance");
     build_boxes(P, L, st);
+    pt.mark("boxes");
     // a4 + top expansion level
     std::vector<double> spread;
     bool helm = P->kernel == CFMM_HELMHOLTZ;
@@ -1110,8 +1139,10 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         }
     }
     P->tree.l0 = l0;
+    pt.mark("centres+l0");
     // a5: lists
     build_lists(P, st);
+    pt.mark("lists");
 }
 
 }  // namespace cfmm
