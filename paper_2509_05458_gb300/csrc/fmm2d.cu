@@ -861,8 +861,7 @@ static int nterms_laplace(int dim, int k, double eps) {
     }
 }
 
-static int nterms_helm2d(int k, double eps, double kappa, double w) {
-    const int pmax = 2000;
+static int nterms_helm2d_upto(int k, double eps, double kappa, double w, int pmax) {
     double R = (k + 0.5) * w, r = std::sqrt(2.0) * 0.5 * w;
     std::vector<cd> J(pmax + 4), H(pmax + 4);
     bessel_j_seq(cd{kappa * r, 0.0}, pmax + 3, J.data());
@@ -878,7 +877,20 @@ static int nterms_helm2d(int k, double eps, double kappa, double w) {
     }
     for (int n = 1; n < pmax; ++n)
         if (ok[n] && ok[n + 1] && ok[n + 2] && ok[n + 3]) return n;
-    return pmax;
+    return -1;
+}
+
+// smallest n with |H_n(kR) J_n(kr)| <= eps for n..n+3 (search up to 2000; a
+// short search range first, since the answer is near k R for large k R and
+// O(log eps) otherwise)
+static int nterms_helm2d(int k, double eps, double kappa, double w) {
+    int guess = (int)(kappa * (k + 0.5) * w) + 80;
+    if (guess < 2000) {
+        int n = nterms_helm2d_upto(k, eps, kappa, w, guess);
+        if (n > 0) return n;
+    }
+    int n = nterms_helm2d_upto(k, eps, kappa, w, 2000);
+    return n > 0 ? n : 2000;
 }
 
 // the criterion is applied at eps * headroom: one digit for Laplace, two for
