@@ -155,8 +155,11 @@ class Laplace3D:
         U = regular(P, d)
         return L @ U
 
+    kernel = LAPLACE
+    kappa = 0.0
+
     @staticmethod
-    def m2m(Pc, Pp, M, a):
+    def m2m(Pc, Pp, M, a, level=None):
         """a = c_child - c_parent: M_n^m(c) = sum_{k,l} (-1)^l U_k^l(a) M_{n-k}^{m+l}."""
         U = regular(Pp, a[None, :])[:, 0]
         I, S, K = _m2m_index(Pc, Pp)
@@ -164,14 +167,14 @@ class Laplace3D:
         return M @ mat.T
 
     @staticmethod
-    def m2l(P, M, X0):
+    def m2l(P, M, X0, level=None):
         """X0 = c_t - c_s: L_k^l = (-1)^{k+l} sum_{n,m} M_n^m T_{n+k}^{m-l}(X0)."""
         T = irregular(2 * P, X0[None, :])[:, 0]
         I, S = _m2l_index(P)
         return M @ (S * T[I]).T
 
     @staticmethod
-    def l2l(Pp, Pc, L, a):
+    def l2l(Pp, Pc, L, a, level=None):
         """a = c_child - c_parent: L'_k^l = sum_{n,m} L_n^m U_{n-k}^{m-l}(a)."""
         U = regular(Pp, a[None, :])[:, 0]
         I, K = _l2l_index(Pp, Pc)
@@ -224,12 +227,17 @@ def expansion_orders(T, eps):
     return [tr.nterms_laplace(3, T.k, eps * tr.P_HEADROOM)] * T.nlevels
 
 
-def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
-    """3D Laplace FMM on tree T; pts/sigma/tau/nrm in tree (sorted) order."""
+def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
+    """3D FMM on tree T; pts/sigma/tau/nrm in tree (sorted) order.
+
+    ops: the expansion operators (``Laplace3D`` by default, or an instance of
+    ``oracle.helm3d.Helmholtz3D``); translations receive the level of the box
+    their result is centred on.
+    """
     n = pts.shape[0]
     if P_levels is None:
         P_levels = expansion_orders(T, eps)
-    X = Laplace3D
+    X = Laplace3D if ops is None else ops
     nr = (sigma if sigma is not None else tau).shape[0]
     u = np.zeros((nr, n), complex)
     nb = T.nboxes
@@ -251,16 +259,25 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
         if expand and lv[b] >= l0 and T.box_leaf[b]:
             s, e, sg, dp = src(b)
             M[b] = X.p2m(P_levels[lv[b]], pts[s:e] - cen[b][None, :], sg, dp)
+    batched = getattr(X, "batched", False)
     for l in range(T.nlevels - 1, l0 - 1, -1):
+        Pp = P_levels[l]
         for b in range(T.level_offset[l], T.level_offset[l + 1]):
-            if not expand or T.box_leaf[b]:
-                continue
-            Pp = P_levels[l]
-            acc = np.zeros((nr, (Pp + 1) ** 2), complex)
-            for c in range(T.level_offset[l + 1], T.level_offset[l + 2]):
-                if T.box_parent[c] == b:
-                    acc += X.m2m(P_levels[l + 1], Pp, M[c], cen[c] - cen[b])
-            M[b] = acc
+            if expand and not T.box_leaf[b]:
+                M[b] = np.zeros((nr, (Pp + 1) ** 2), complex)
+        if not expand or l + 1 >= T.nlevels:
+            continue
+        kids = [c for c in range(T.level_offset[l + 1], T.level_offset[l + 2])]
+        if batched and kids:
+            par = [T.box_parent[c] for c in kids]
+            out = X.m2m(P_levels[l + 1], Pp, np.stack([M[c] for c in kids]),
+                        np.stack([cen[c] - cen[p] for c, p in zip(kids, par)]), l)
+            for i, p in enumerate(par):
+                M[p] += out[i]
+        else:
+            for c in kids:
+                p = T.box_parent[c]
+                M[p] += X.m2m(P_levels[l + 1], Pp, M[c], cen[c] - cen[p], l)
     for b in range(nb):
         if not T.box_leaf[b]:
             continue
@@ -270,7 +287,7 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
             d = pts[ts:te, None, :] - pts[None, s:e, :]
             zero = np.all(d == 0, axis=-1)
             dd = np.where(zero[..., None], 1.0, d)
-            slp, dlp = kernel_pair(3, LAPLACE, 0.0, dd, None if not dipole else
+            slp, dlp = kernel_pair(3, X.kernel, X.kappa, dd, None if not dipole else
                                    np.broadcast_to(nrm[None, s:e, :], dd.shape))
             if sg is not None:
                 u[:, ts:te] += sg @ np.where(zero, 0, slp).T
@@ -279,13 +296,19 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
     if not expand:
         return u
     for b in range(nb):
-        if lv[b] < l0:
-            continue
-        P = P_levels[lv[b]]
-        acc = np.zeros((nr, (P + 1) ** 2), complex)
-        for a in T.lists["list2"][b]:
-            acc += X.m2l(P, M[a], cen[b] - cen[a])
-        Lc[b] = acc
+        if lv[b] >= l0:
+            Lc[b] = np.zeros((nr, (P_levels[lv[b]] + 1) ** 2), complex)
+    for l in range(l0, T.nlevels):
+        pairs = [(b, a) for b in range(T.level_offset[l], T.level_offset[l + 1])
+                 for a in T.lists["list2"][b]]
+        if batched and pairs:
+            out = X.m2l(P_levels[l], np.stack([M[a] for b, a in pairs]),
+                        np.stack([cen[b] - cen[a] for b, a in pairs]), l)
+            for i, (b, a) in enumerate(pairs):
+                Lc[b] += out[i]
+        else:
+            for b, a in pairs:
+                Lc[b] += X.m2l(P_levels[l], M[a], cen[b] - cen[a], l)
     for b in range(nb):
         if T.box_leaf[b] and lv[b] >= l0:
             ts, te = st[b], en[b]
@@ -298,9 +321,16 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
             s, e, sg, dp = src(a)
             Lc[b] += X.p2l(P_levels[lv[b]], pts[s:e] - cen[b][None, :], sg, dp)
     for l in range(l0 + 1, T.nlevels):
-        for b in range(T.level_offset[l], T.level_offset[l + 1]):
-            p = T.box_parent[b]
-            Lc[b] += X.l2l(P_levels[l - 1], P_levels[l], Lc[p], cen[b] - cen[p])
+        kids = list(range(T.level_offset[l], T.level_offset[l + 1]))
+        if batched and kids:
+            out = X.l2l(P_levels[l - 1], P_levels[l], np.stack([Lc[T.box_parent[b]] for b in kids]),
+                        np.stack([cen[b] - cen[T.box_parent[b]] for b in kids]), l)
+            for i, b in enumerate(kids):
+                Lc[b] += out[i]
+        else:
+            for b in kids:
+                p = T.box_parent[b]
+                Lc[b] += X.l2l(P_levels[l - 1], P_levels[l], Lc[p], cen[b] - cen[p], l)
     for b in range(nb):
         if T.box_leaf[b] and lv[b] >= l0:
             ts, te = st[b], en[b]
@@ -309,8 +339,9 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
 
 
 def apply(geom_re, geom_im, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None, nrm_im=None,
-          P_levels=None, T=None):
-    """User-order 3D Laplace FMM; sigma/tau complex [nrhs, n] or [n]. Returns (u, T)."""
+          P_levels=None, T=None, ops=None):
+    """User-order 3D FMM (Laplace unless ops is given); sigma/tau complex [nrhs, n] or [n].
+    Returns (u, T)."""
     pts = np.asarray(geom_re) + 1j * np.asarray(geom_im)
     if T is None:
         T = tr.build_tree(geom_re, geom_im, N_s, k=k, eps=eps, helmholtz=False)
@@ -329,7 +360,7 @@ def apply(geom_re, geom_im, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None, nr
 
     sg, tu = prep(sigma), prep(tau)
     nrm = None if tau is None else (np.asarray(nrm_re) + 1j * np.asarray(nrm_im))[perm]
-    u_s = fmm3d(T, eps, pts[perm], sg, tu, nrm, P_levels)
+    u_s = fmm3d(T, eps, pts[perm], sg, tu, nrm, P_levels, ops)
     u = np.empty_like(u_s)
     u[:, perm] = u_s
     return (u[0] if single else u), T

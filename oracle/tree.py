@@ -315,8 +315,10 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
     return maxl
 
 
-def build_tree(re, im, N_s, k=1, kappa=0.0, eps=1e-6, helmholtz=False):
-    """Build the complete tree (leaves, boxes, lists) for points re/im [n][dim]."""
+def build_tree(re, im, N_s, k=1, kappa=0.0, eps=1e-6, helmholtz=False, top_level=0):
+    """Build the complete tree (leaves, boxes, lists) for points re/im [n][dim].
+
+    top_level > 0 forces the top expansion level l0 instead of the rule."""
     re = np.asarray(re, dtype=np.float64)
     im = np.asarray(im, dtype=np.float64)
     n, dim = re.shape
@@ -334,7 +336,7 @@ def build_tree(re, im, N_s, k=1, kappa=0.0, eps=1e-6, helmholtz=False):
     im_sorted = im[perm]
     l0 = 1
     if n > N_s:
-        l0 = choose_l0(T, im_sorted, kappa, eps, helmholtz)
+        l0 = top_level if top_level > 0 else choose_l0(T, im_sorted, kappa, eps, helmholtz)
         if l0 > 1:
             T.leaves = _balance(keys, B, dim, _refine(keys, B, dim, T.leaves, N_s, l0), k)
             _build_boxes(T)
