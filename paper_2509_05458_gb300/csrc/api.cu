@@ -231,6 +231,7 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     }
     record(P, 1);
     if (P->dim == 2) fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
+    else if (P->kernel == CFMM_HELMHOLTZ) helm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
     else fmm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
     record(P, 8);
     cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
@@ -253,6 +254,7 @@ static void destroy_plan(cfmm_plan_s* P) {
     if (P->graph) cudaGraphDestroy(P->graph);
     fmm2d_release(P);
     fmm3d_release(P);
+    helm3d_release(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     delete P;
@@ -317,6 +319,7 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         const double* nim = dlp ? stage_in(nrm_im, cnt, P->stream) : nullptr;
         build_tree(P, re, im, nre, nim, o.top_level);
         if (dim == 2) fmm2d_setup(P);
+        else if (P->kernel == CFMM_HELMHOLTZ) helm3d_setup(P);
         else fmm3d_setup(P);
         CFMM_CUDA(cudaStreamSynchronize(P->stream));
         scr.rewind();

@@ -15,7 +15,13 @@
 //     normalised with exp(-/+ i z) = J_0 + 2 sum (-/+ i)^k J_k (generating
 //     function DLMF 10.12.1 at t = -/+ i), the sign chosen so the sum does
 //     not cancel;
-//   * H_n by forward recurrence H_{n+1} = (2n/z) H_n - H_{n-1} (DLMF 10.6.1).
+//   * H_n by forward recurrence H_{n+1} = (2n/z) H_n - H_{n-1} (DLMF 10.6.1);
+//   * spherical h_n^(1)(z) from h_0 = -i e^{iz}/z, h_1 = -e^{iz}(z + i)/z^2
+//     and forward recurrence h_{n+1} = ((2n+1)/z) h_n - h_{n-1} (DLMF 10.49.6,
+//     10.51.1; h_n is the dominant solution);
+//   * spherical j_n(z) by Miller's backward recurrence, normalised with
+//     exp(-/+ i z) = sum (2n+1) (-/+ i)^n j_n(z) (the plane-wave expansion
+//     DLMF 10.60.7 at cos = -/+ 1), the sign chosen so the sum does not cancel.
 #pragma once
 
 #include "cfmm_common.cuh"
@@ -134,6 +140,57 @@ CFMM_HD void bessel_j_seq(cd z, int nmax, cd* out) {
         else    w = (r == 0) ? f : (r == 1) ? cd{-f.y, f.x} : (r == 2) ? -f : cd{f.y, -f.x};
         S += 2.0 * w;
         cd fm = (2.0 * n) * (zi * f) - fp;
+        fp = f;
+        f = fm;
+        if (cabs2(f) > 1e300) {
+            const double sc = 1e-150;
+            f = sc * f;
+            fp = sc * fp;
+            S = sc * S;
+            int top = nmax < N0 ? nmax : N0;
+            for (int m = n; m <= top; ++m) out[m] = sc * out[m];
+        }
+    }
+    out[0] = f;
+    S += f;
+    cd e = up ? cexp_i(-z) : cexp_i(z);
+    cd scale = e / S;
+    for (int n = 0; n <= nmax; ++n) out[n] = out[n] * scale;
+}
+
+// h_n^(1)(z), n = 0..nmax, complex z != 0
+CFMM_HD void sph_h_seq(cd z, int nmax, cd* out) {
+    cd e = cexp_i(z);
+    cd zi = cinv(z);
+    out[0] = -mul_i(e * zi);
+    if (nmax < 1) return;
+    out[1] = -(e * (z + cd{0.0, 1.0})) * (zi * zi);
+    for (int n = 1; n < nmax; ++n) out[n + 1] = (2.0 * n + 1.0) * (zi * out[n]) - out[n - 1];
+}
+
+// j_n(z), n = 0..nmax, complex z
+CFMM_HD void sph_j_seq(cd z, int nmax, cd* out) {
+    double az = hypot(z.x, z.y);
+    if (az == 0.0) {
+        out[0] = cd{1.0, 0.0};
+        for (int n = 1; n <= nmax; ++n) out[n] = cd{0.0, 0.0};
+        return;
+    }
+    double big = az > (double)nmax ? az : (double)nmax;
+    int N0 = (int)big + 24 + (int)sqrt(32.0 * big);
+    bool up = z.y >= 0.0;                  // exp(-iz) = sum (2n+1) (-i)^n j_n
+    cd zi = cinv(z);
+    cd fp = {0.0, 0.0}, f = {1e-200, 0.0};
+    cd S = {0.0, 0.0};
+    for (int n = 0; n <= nmax; ++n) out[n] = cd{0.0, 0.0};
+    for (int n = N0; n >= 1; --n) {
+        if (n <= nmax) out[n] = f;
+        cd w;
+        int r = n & 3;
+        if (up) w = (r == 0) ? f : (r == 1) ? cd{f.y, -f.x} : (r == 2) ? -f : cd{-f.y, f.x};
+        else    w = (r == 0) ? f : (r == 1) ? cd{-f.y, f.x} : (r == 2) ? -f : cd{f.y, -f.x};
+        S += (2.0 * n + 1.0) * w;
+        cd fm = (2.0 * n + 1.0) * (zi * f) - fp;   // j_{n-1} = ((2n+1)/z) j_n - j_{n+1}
         fp = f;
         f = fm;
         if (cabs2(f) > 1e300) {

@@ -1,0 +1,1020 @@
+// 3D complex-coordinate Helmholtz FMM: expansions and translations (Sec. 5.3,
+// Sec. 6.4), FP64.
+//
+// Expansion functions of a complex 3-vector x (x+ = x1 + i x2, x- = x1 - i x2,
+// x3, rho^2 = x.x, rho the principal root; no angle is formed):
+//   Z_n^m(x) = rho^n Y_n^m, Y the Schmidt semi-normalised harmonics of Sec. 3.2,
+//     Z_0^0 = 1,  Z_m^m = -x+ sqrt((2m-1)/(2m)) Z_{m-1}^{m-1},  Z_{m+1}^m = sqrt(2m+1) x3 Z_m^m,
+//     Z_n^m = A_n^m x3 Z_{n-1}^m - B_n^m rho^2 Z_{n-2}^m,
+//     A_n^m = (2n-1)/sqrt((n-m)(n+m)),  B_n^m = sqrt((n-m-1)(n+m-1)/((n-m)(n+m))),
+//     Z_n^{-m} = Z_n^m with x+ and x- exchanged;
+//   R_n^m = j_n(k rho) rho^-n Z_n^m (entire),  S_n^m = h_n(k rho) rho^-n Z_n^m.
+// Gegenbauer's addition theorem with Eq. sphaddition gives, for the
+// constant-free kernel e^{ik r}/r = ik h_0(kr),
+//   e^{ik|x-y|}/|x-y| = ik sum (2n+1) R_n^{-m}(y) S_n^m(x),
+// hence (Thms 5.3.1, 5.3.2)
+//   P2M  M_n^m = ik(2n+1) sum_j s_j R_n^{-m}(y_j - c)     M2P  u = sum M_n^m S_n^m(x - c)
+//   P2L  L_n^m = ik(2n+1) sum_j s_j S_n^{-m}(y_j - c)     L2P  u = sum L_n^m R_n^m(x - c)
+// and the double layer differentiates the source side along the normal:
+//   grad(f_n rho^-n Z) = f_n rho^-n grad Z - k f_{n+1} rho^-(n+1) Z x,
+//   n.grad Z_n^m = n3 c3 Z_{n-1}^m - nu+ s+ c+ Z_{n-1}^{m-1} + nu- s- c- Z_{n-1}^{m+1},
+//   c3 = sqrt((n-m)(n+m)), c+ = sqrt((n+m)(n+m-1))/2, c- = sqrt((n-m)(n-m-1))/2,
+//   s+ = 1 (m >= 1) else -1, s- = 1 (m >= 0) else -1, nu+- = n1 +- i n2.
+//
+// Translations by a complex shift d = c_new - c_old ("point and shoot",
+// Sec. 5.3 translation operators):
+//   1. rotate to the z-axis. e = (d1 + i d2)/s, s = sqrt(d1^2 + d2^2) (e = 1 if
+//      s^2 = 0); t = sqrt(d.d); e_a = (d3 + i s)/t. The complex rotation
+//      x' = R_y(a) R_z(-b) x carries d to (0, 0, t) and maps coefficients by
+//        c' = Phi^-1 D^T E(e_a) D Phi E(e) c,   Phi = diag(i^m), E(e) = diag(e^m),
+//      with D_n the real (2n+1)x(2n+1) matrix of the fixed rotation
+//      x -> R_x(pi/2) x conjugated by Phi: the y-rotation of Eq. mp_y_rot
+//      factored into two fixed rotations around a diagonal z-rotation.
+//      D is built on the host by projecting onto the equator exactly as
+//      Eq. mp_y_rot does (real rotation, so F_n is a trigonometric polynomial
+//      and 2n+1 samples are exact);
+//   2. re-expand along z with the exact coaxial coefficients
+//        W_{n'}^m(x + t e3) = sum_n T^m_{n n'}(t) V_n^m(x)
+//      (W = S, V = R for M2L, f = h; W = V = R or S, f = j for L2L and M2M),
+//      generated per shift by the recurrences that follow from
+//        d3 W_n^m = k(alpha_n^m W_{n-1}^m - beta_n^m W_{n+1}^m),
+//        d- W_n^m = k(mu_n^m W_{n-1}^{m+1} + nu_n^m W_{n+1}^{m+1})  (m >= 0),
+//        alpha = sqrt((n-m)(n+m))/(2n+1), beta = sqrt((n+1-m)(n+1+m))/(2n+1),
+//        mu = sqrt((n-m)(n-m-1))/(2(2n+1)), nu = sqrt((n+m+1)(n+m+2))/(2(2n+1)):
+//        T^0_{n,0} = (2n+1)(-1)^n f_n(kt),
+//        T^m_{n,m} = [mu_{n+1}^{m-1} T^{m-1}_{n+1,m-1} + nu_{n-1}^{m-1} T^{m-1}_{n-1,m-1}] / nu_{m-1}^{m-1},
+//        T_{n,n'+1} = [alpha_{n'} T_{n,n'-1} - alpha_{n+1} T_{n+1,n'} + beta_{n-1} T_{n-1,n'}] / beta_{n'},
+//      the last only for n > n' (the stable direction); the rest from
+//        T_{n',n} = (2n'+1)/(2n+1) (-1)^{n+n'} T_{n,n'},   T^{-m} = T^m.
+//      These are the translations the paper's projection step approximates
+//      (its Gauss-Legendre projection recovers T up to aliasing);
+//   3. rotate back: c = E(1/e) Phi^-1 D^T E(1/e_a) D Phi c'.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+
+#include "cfmm_special.cuh"
+#include "kernels.cuh"
+
+namespace cfmm {
+
+namespace {
+
+__host__ __device__ __forceinline__ int nmi(int n, int m) { return n * n + n + m; }
+
+constexpr int kH3Threads = 256;
+constexpr int kH3MaxP = 63;          // expansion order limit of this path
+constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
+
+// ---------------------------------------------------------------------------
+// Per-device tables shared by all plans: D_n (row-major, n <= Pmax), the Z
+// recurrence coefficients and the coaxial recurrence coefficients.
+// ---------------------------------------------------------------------------
+struct H3Tables {
+    int Pmax = -1;
+    DevBuf<double> D;        // sum_n (2n+1)^2
+    DevBuf<int64_t> Doff;    // [Pmax+2]
+    DevBuf<double> zA, zB;   // [(2Pmax+2)^2] by nmi(n, m), m >= 0
+    DevBuf<double> al, be, ibe;  // alpha, beta, 1/beta by nmi(n, m), n <= 2Pmax+2
+};
+
+// Tables only grow: a larger order builds a new set and the older sets stay
+// alive, since plans that hold them may be running on other streams.
+static std::mutex g_tab_mu;
+static std::map<int, std::vector<H3Tables*>>& tab_map() {
+    static std::map<int, std::vector<H3Tables*>> m;
+    return m;
+}
+
+// Z_n^m at a complex point (host), n <= P, all m
+static void host_ztable(int P, cd x0, cd x1, cd x2, std::vector<cd>& Z) {
+    Z.assign((size_t)(P + 1) * (P + 1), cd{0, 0});
+    cd xp = x0 + mul_i(x1), xm = x0 - mul_i(x1), z = x2;
+    cd r2 = xp * xm + z * z;
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        cd xs = sgn ? xm : xp;
+        cd d = {1, 0};
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) d = (-std::sqrt((2.0 * m - 1.0) / (2.0 * m))) * (xs * d);
+            if (sgn == 1 && m == 0) continue;
+            int mi = sgn ? -m : m;
+            Z[nmi(m, mi)] = d;
+            if (m + 1 > P) continue;
+            cd p2 = d, p1 = std::sqrt(2.0 * m + 1.0) * (z * d);
+            Z[nmi(m + 1, mi)] = p1;
+            for (int n = m + 2; n <= P; ++n) {
+                double A = (2.0 * n - 1.0) / std::sqrt((double)(n - m) * (n + m));
+                double B = std::sqrt((double)(n - m - 1) * (n + m - 1) / ((double)(n - m) * (n + m)));
+                cd cur = A * (z * p1) - B * (r2 * p2);
+                Z[nmi(n, mi)] = cur;
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+}
+
+// D_n for n <= P (real, row-major by (m + n, m' + n)); see the file comment.
+static void host_rotation_tables(int P, std::vector<double>& D, std::vector<int64_t>& off) {
+    const double kPi = 3.14159265358979323846;
+    off.assign(P + 2, 0);
+    for (int n = 0; n <= P; ++n) off[n + 1] = off[n] + (int64_t)(2 * n + 1) * (2 * n + 1);
+    D.assign(off[P + 1], 0.0);
+    std::vector<cd> Z, ab;
+    // a_n^m = Y_n^m(e1), b_n^m = d_theta Y_n^m at (pi/2, 0) = -sqrt((n-m)(n+m)) Z_{n-1}^m(e1)
+    host_ztable(P, cd{1, 0}, cd{0, 0}, cd{0, 0}, ab);
+    std::vector<cd> F, G;
+    for (int n = 0; n <= P; ++n) {
+        int N = 2 * n + 1;
+        // samples of Z_n^{m'} at p_j = X^T-rotated equator points and their
+        // theta-derivative: frame x1 = Q x with Q = R_x(-pi/2)^T, so the
+        // samples are taken at Q^T e_j = (cos phi, 0, -sin phi) along
+        // Q^T (0, 0, -1) = (0, -1, 0) (v+ = -i, v- = i)
+        F.assign((size_t)N * N, cd{0, 0});
+        G.assign((size_t)N * N, cd{0, 0});
+        for (int j = 0; j < N; ++j) {
+            double ph = 2.0 * kPi * j / N;
+            host_ztable(n, cd{std::cos(ph), 0}, cd{0, 0}, cd{-std::sin(ph), 0}, Z);
+            for (int mp = -n; mp <= n; ++mp) {
+                F[(size_t)j * N + (mp + n)] = Z[nmi(n, mp)];
+                // grad Z . v = -i d+ Z + i d- Z
+                cd g = {0, 0};
+                if (n >= 1) {
+                    if (std::abs(mp - 1) <= n - 1) {
+                        double sp = mp >= 1 ? 1.0 : -1.0;
+                        cd dp = (-0.5 * sp * std::sqrt((double)(n + mp) * (n + mp - 1))) * Z[nmi(n - 1, mp - 1)];
+                        g = g - mul_i(dp);
+                    }
+                    if (std::abs(mp + 1) <= n - 1) {
+                        double sm = mp >= 0 ? 1.0 : -1.0;
+                        cd dm = (0.5 * sm * std::sqrt((double)(n - mp) * (n - mp - 1))) * Z[nmi(n - 1, mp + 1)];
+                        g = g + mul_i(dm);
+                    }
+                }
+                G[(size_t)j * N + (mp + n)] = g;
+            }
+        }
+        for (int m = -n; m <= n; ++m) {
+            double a = ab[nmi(n, m)].x;
+            double b = 0.0;
+            if (std::abs(m) <= n - 1) b = -std::sqrt((double)(n - m) * (n + m)) * ab[nmi(n - 1, m)].x;
+            double den = a * a + b * b;
+            for (int mp = -n; mp <= n; ++mp) {
+                cd Fh = {0, 0}, Gh = {0, 0};
+                for (int j = 0; j < N; ++j) {
+                    double ph = 2.0 * kPi * j / N;
+                    cd w = {std::cos(m * ph) / N, -std::sin(m * ph) / N};
+                    Fh = Fh + w * F[(size_t)j * N + (mp + n)];
+                    Gh = Gh + w * G[(size_t)j * N + (mp + n)];
+                }
+                cd da = (a * Fh + b * Gh) * (1.0 / den);
+                // D = Phi DA Phi^-1: multiply by i^m i^-m'
+                int e = ((m - mp) % 4 + 4) % 4;
+                cd ph = e == 0 ? cd{1, 0} : e == 1 ? cd{0, 1} : e == 2 ? cd{-1, 0} : cd{0, -1};
+                cd v = ph * da;
+                CFMM_REQUIRE(std::fabs(v.y) <= 1e-10 * (1.0 + std::fabs(v.x)), CFMM_ECUDA,
+                             "3D Helmholtz rotation table is not real");
+                D[off[n] + (int64_t)(m + n) * N + (mp + n)] = v.x;
+            }
+        }
+    }
+}
+
+static H3Tables* tables(int P) {
+    int dev = 0;
+    CFMM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto& sets = tab_map()[dev];
+    if (!sets.empty() && sets.back()->Pmax >= P) return sets.back();
+    H3Tables* T = new H3Tables();
+    int Pm = std::max(P, 16);
+    std::vector<double> D;
+    std::vector<int64_t> off;
+    host_rotation_tables(Pm, D, off);
+    int NN = 2 * Pm + 3;
+    std::vector<double> zA((size_t)NN * NN, 0.0), zB((size_t)NN * NN, 0.0), al((size_t)NN * NN, 0.0),
+        be((size_t)NN * NN, 0.0), ibe((size_t)NN * NN, 0.0);
+    for (int n = 0; n < NN; ++n)
+        for (int m = 0; m <= n && nmi(n, m) < NN * NN; ++m) {
+            int k = nmi(n, m);
+            if (n >= m + 2) {
+                zA[k] = (2.0 * n - 1.0) / std::sqrt((double)(n - m) * (n + m));
+                zB[k] = std::sqrt((double)(n - m - 1) * (n + m - 1) / ((double)(n - m) * (n + m)));
+            }
+            al[k] = std::sqrt((double)(n - m) * (n + m)) / (2.0 * n + 1.0);
+            be[k] = std::sqrt((double)(n + 1 - m) * (n + 1 + m)) / (2.0 * n + 1.0);
+            ibe[k] = 1.0 / be[k];
+        }
+    T->D.alloc(D.size());
+    T->Doff.alloc(off.size());
+    T->zA.alloc(zA.size());
+    T->zB.alloc(zB.size());
+    T->al.alloc(al.size());
+    T->be.alloc(be.size());
+    T->ibe.alloc(ibe.size());
+    CFMM_CUDA(cudaMemcpy(T->D.get(), D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->Doff.get(), off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->zA.get(), zA.data(), sizeof(double) * zA.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->zB.get(), zB.data(), sizeof(double) * zB.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->al.get(), al.data(), sizeof(double) * al.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->be.get(), be.data(), sizeof(double) * be.size(), cudaMemcpyHostToDevice));
+    CFMM_CUDA(cudaMemcpy(T->ibe.get(), ibe.data(), sizeof(double) * ibe.size(), cudaMemcpyHostToDevice));
+    T->Pmax = Pm;
+    sets.push_back(T);
+    return T;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+struct ZCoef {
+    const double* A;
+    const double* B;
+};
+
+// Z table of (a0, a1, a2) up to order P into tab[nmi(n, m)]; columns split
+// over threads t0, t0 + nthreads, ...
+__device__ void z_table(ZCoef zc, cd a0, cd a1, cd a2, int P, cd* tab, int t0, int nthreads) {
+    cd xp = a0 + mul_i(a1), xm = a0 - mul_i(a1), z = a2;
+    cd r2 = xp * xm + z * z;
+    for (int col = t0; col < 2 * P + 1; col += nthreads) {
+        int m = col <= P ? col : col - P;
+        bool neg = col > P;
+        cd xs = neg ? xm : xp;
+        cd d = {1, 0};
+        for (int j = 1; j <= m; ++j) d = (-sqrt((2.0 * j - 1.0) / (2.0 * j))) * (xs * d);
+        int mi = neg ? -m : m;
+        tab[nmi(m, mi)] = d;
+        if (m + 1 > P) continue;
+        cd p2 = d, p1 = sqrt(2.0 * m + 1.0) * (z * d);
+        tab[nmi(m + 1, mi)] = p1;
+        for (int n = m + 2; n <= P; ++n) {
+            int k = nmi(n, m);
+            cd cur = zc.A[k] * (z * p1) - zc.B[k] * (r2 * p2);
+            tab[nmi(n, mi)] = cur;
+            p2 = p1;
+            p1 = cur;
+        }
+    }
+}
+
+// F[n] = f_n(k rho) / rho^n for n = 0..N (f = j if reg, else h); rho = 0 (reg
+// only) gives the limits k^n / (2n+1)!!
+__device__ void radial_seq(bool reg, double kappa, cd r2, int N, cd* F) {
+    cd rho = csqrt_p(r2);
+    if (rho.x == 0.0 && rho.y == 0.0) {
+        double v = 1.0;
+        for (int n = 0; n <= N; ++n) {
+            F[n] = cd{v, 0};
+            v *= kappa / (2.0 * n + 3.0);
+        }
+        return;
+    }
+    cd z = kappa * rho;
+    if (reg) sph_j_seq(z, N, F);
+    else sph_h_seq(z, N, F);
+    cd ir = cinv(rho), p = {1, 0};
+    for (int n = 0; n <= N; ++n) {
+        F[n] = F[n] * p;
+        p = p * ir;
+    }
+}
+
+__device__ __forceinline__ cd zget(const cd* tab, int n, int m) {
+    if (n < 0 || m > n || -m > n) return cd{0, 0};
+    return tab[nmi(n, m)];
+}
+
+__device__ __forceinline__ void nm_of(int c, int& n, int& m) {
+    n = (int)sqrt((double)c);
+    while (n * n > c) --n;
+    while ((n + 1) * (n + 1) <= c) ++n;
+    m = c - n * n - n;
+}
+
+struct Exp3hArgs {
+    const double* xr;
+    const double* xi;
+    const double* nr;
+    const double* ni;
+    int64_t n;
+    const cd* sigma;
+    const cd* tau;
+    int64_t dstride;
+    bool slp, dlp;
+    const int* blevel;
+    const int* bst;
+    const int* ben;
+    const double* cre;
+    const double* cim;
+    const int* Plev;
+    const int64_t* eoff;
+    int64_t ncoef;
+    double kappa;
+    ZCoef zc;
+};
+
+__device__ __forceinline__ void load3(const double* re, const double* im, int64_t n, int64_t j, cd* x) {
+    for (int a = 0; a < 3; ++a) x[a] = cd{re[a * n + j], im[a * n + j]};
+}
+
+// P2M (sing = 0: R waves, the box's own points) or P2L (sing = 1: S waves,
+// the box's List-4 leaves). Sources are staged chunk by chunk: Z table, radial
+// factors and (sigma, tau, nu+, nu-, n3, y.n) per source; each thread owns
+// coefficients and adds the sources' terms in source order.
+__global__ void k_p2x3h(Exp3hArgs A, const int* __restrict__ boxes, const int* __restrict__ loff,
+                        const int* __restrict__ lent, int sing, cd* __restrict__ out, int chunk) {
+    extern __shared__ cd sm[];
+    int b = boxes[blockIdx.x];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    int nc = (P + 1) * (P + 1);
+    cd* acc = sm;
+    cd* tabs = acc + nc;                           // [chunk][nc]
+    cd* rad = tabs + (size_t)chunk * nc;           // [chunk][P+2]
+    cd* srcv = rad + (size_t)chunk * (P + 2);      // [chunk][6]
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) acc[c] = cd{0, 0};
+    cd cen[3];
+    for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+    int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
+    for (int q = qa; q < qb; ++q) {
+        int src = loff ? lent[q] : b;
+        int s0 = A.bst[src], s1 = A.ben[src];
+        for (int c0 = s0; c0 < s1; c0 += chunk) {
+            int cn = min(chunk, s1 - c0);
+            __syncthreads();
+            int cols = 2 * P + 1;
+            for (int w = threadIdx.x; w < cn * (cols + 1); w += blockDim.x) {
+                int s = w / (cols + 1), col = w - s * (cols + 1);
+                int64_t j = c0 + s;
+                cd y[3];
+                load3(A.xr, A.xi, A.n, j, y);
+                for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
+                if (col < cols) {
+                    z_table(A.zc, y[0], y[1], y[2], P, tabs + (size_t)s * nc, col, cols);
+                } else {
+                    cd r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+                    radial_seq(!sing, A.kappa, r2, P + 1, rad + (size_t)s * (P + 2));
+                    cd* v = srcv + (size_t)s * 6;
+                    v[0] = A.slp ? A.sigma[rhs * A.dstride + j] : cd{0, 0};
+                    v[1] = A.dlp ? A.tau[rhs * A.dstride + j] : cd{0, 0};
+                    if (A.dlp) {
+                        cd nn[3];
+                        load3(A.nr, A.ni, A.n, j, nn);
+                        v[2] = nn[0] + mul_i(nn[1]);
+                        v[3] = nn[0] - mul_i(nn[1]);
+                        v[4] = nn[2];
+                        v[5] = y[0] * nn[0] + y[1] * nn[1] + y[2] * nn[2];
+                    }
+                }
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+                int n, m;
+                nm_of(c, n, m);
+                int mu = -m;
+                cd a = acc[c];
+                for (int s = 0; s < cn; ++s) {
+                    const cd* tb = tabs + (size_t)s * nc;
+                    const cd* F = rad + (size_t)s * (P + 2);
+                    const cd* v = srcv + (size_t)s * 6;
+                    cd Zv = tb[nmi(n, mu)];
+                    cd term = {0, 0};
+                    if (A.slp) term = v[0] * (F[n] * Zv);
+                    if (A.dlp) {
+                        cd g = {0, 0};
+                        if (n >= 1) {
+                            g = (sqrt((double)(n - mu) * (n + mu)) * v[4]) * zget(tb, n - 1, mu);
+                            double sp = mu >= 1 ? 1.0 : -1.0, sn = mu >= 0 ? 1.0 : -1.0;
+                            g = g - (0.5 * sp * sqrt((double)(n + mu) * (n + mu - 1))) * (v[2] * zget(tb, n - 1, mu - 1));
+                            g = g + (0.5 * sn * sqrt((double)(n - mu) * (n - mu - 1))) * (v[3] * zget(tb, n - 1, mu + 1));
+                        }
+                        cd dw = F[n] * g - A.kappa * (F[n + 1] * (Zv * v[5]));
+                        term += v[1] * dw;
+                    }
+                    a += term;
+                }
+                acc[c] = a;
+            }
+        }
+    }
+    __syncthreads();
+    cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int n = (int)sqrt((double)c);
+        while (n * n > c) --n;
+        while ((n + 1) * (n + 1) <= c) ++n;
+        cd v = mul_i(A.kappa * (2.0 * n + 1.0) * acc[c]);
+        if (sing) o[c] += v;
+        else o[c] = v;
+    }
+}
+
+// Sum over n, m of coef_n^m F[n] Z_n^m(x) with Z generated column by column.
+__device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const cd* coef) {
+    cd xp = a0 + mul_i(a1), xm = a0 - mul_i(a1), z = a2;
+    cd r2 = xp * xm + z * z;
+    cd acc = {0, 0};
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        cd xs = sgn ? xm : xp;
+        cd d = {1, 0};
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) d = (-sqrt((2.0 * m - 1.0) / (2.0 * m))) * (xs * d);
+            if (sgn == 1 && m == 0) continue;
+            int mi = sgn ? -m : m;
+            acc += F[m] * (d * coef[nmi(m, mi)]);
+            if (m + 1 > P) continue;
+            cd p2 = d, p1 = sqrt(2.0 * m + 1.0) * (z * d);
+            acc += F[m + 1] * (p1 * coef[nmi(m + 1, mi)]);
+            for (int n = m + 2; n <= P; ++n) {
+                int k = nmi(n, m);
+                cd cur = zc.A[k] * (z * p1) - zc.B[k] * (r2 * p2);
+                acc += F[n] * (cur * coef[nmi(n, mi)]);
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+    return acc;
+}
+
+// M2P over List 3 (S waves) and L2P (R waves); one thread per target.
+__global__ void k_eval3h(Exp3hArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
+                         const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
+                         cd* __restrict__ u) {
+    extern __shared__ cd sm[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    int nc = (P + 1) * (P + 1);
+    cd* coef = sm;
+    int s0 = A.bst[b], s1 = A.ben[b];
+    cd F[kH3MaxP + 2];
+    for (int t0 = s0; t0 < s1; t0 += blockDim.x) {
+        int i = t0 + threadIdx.x;
+        bool valid = i < s1;
+        cd x[3] = {{0, 0}, {0, 0}, {0, 0}};
+        if (valid) load3(A.xr, A.xi, A.n, i, x);
+        cd acc = {0, 0};
+        for (int q = l3off[b]; q < l3off[b + 1]; ++q) {
+            int s = l3[q];
+            int Ps = A.Plev[A.blevel[s]];
+            __syncthreads();
+            const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
+            for (int c = threadIdx.x; c < (Ps + 1) * (Ps + 1); c += blockDim.x) coef[c] = m[c];
+            __syncthreads();
+            if (valid) {
+                cd d[3];
+                for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * s + a], A.cim[3 * s + a]};
+                radial_seq(false, A.kappa, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], Ps, F);
+                acc += eval_wave(A.zc, d[0], d[1], d[2], Ps, F, coef);
+            }
+        }
+        __syncthreads();
+        const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) coef[c] = lc[c];
+        __syncthreads();
+        if (valid) {
+            cd d[3];
+            for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+            radial_seq(true, A.kappa, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], P, F);
+            acc += eval_wave(A.zc, d[0], d[1], d[2], P, F, coef);
+            u[(int64_t)rhs * A.n + i] += acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// translations
+// ---------------------------------------------------------------------------
+struct Tr3hArgs {
+    const double* cre;
+    const double* cim;
+    const int64_t* eoff;
+    int64_t ncoef;
+    const double* D;
+    const int64_t* Doff;
+    const double* al;
+    const double* be;
+    const double* ibe;
+    double kappa;
+    // source enumeration (mode 0: children cbeg..cend; 1: List 2; 2: parent)
+    const int* cbeg;
+    const int* cend;
+    const int* loff;
+    const int* lent;
+    const int* parent;
+    const int* leaf;
+};
+
+// c[nmi(n, m)] *= s^m (s given by its powers pw[m + Pm], m in [-Pm, Pm])
+__device__ __forceinline__ void diag_scale(cd* c, int P, const cd* pw, int Pm) {
+    int K = (P + 1) * (P + 1);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        int n, m;
+        nm_of(k, n, m);
+        c[k] = c[k] * pw[m + Pm];
+    }
+}
+
+// out = D in (trans = 0) or D^T in (trans = 1), order by order, n <= P
+__device__ __forceinline__ void rot_apply(const double* D, const int64_t* Doff, const cd* in, cd* out, int P,
+                                          int trans) {
+    int K = (P + 1) * (P + 1);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        int n, m;
+        nm_of(k, n, m);
+        int N = 2 * n + 1;
+        const double* Dn = D + Doff[n];
+        const cd* v = in + n * n;
+        cd s = {0, 0};
+        if (trans) {
+            for (int j = 0; j < N; ++j) s += Dn[j * N + (m + n)] * v[j];
+        } else {
+            const double* row = Dn + (m + n) * N;
+            for (int j = 0; j < N; ++j) s += row[j] * v[j];
+        }
+        out[k] = s;
+    }
+}
+
+// i^e for integer e
+__device__ __forceinline__ cd ipow(int e) {
+    e = ((e % 4) + 4) % 4;
+    return e == 0 ? cd{1, 0} : e == 1 ? cd{0, 1} : e == 2 ? cd{-1, 0} : cd{0, -1};
+}
+
+// One translation per destination box and source; the destination box's
+// result is accumulated in shared memory and written (mode 0, 1) or added
+// (mode 2) at the end. Shared layout: acc[Ko], a[Km], b[Km], f[Pi+Po+1],
+// pw_e[2Pm+1], pw_a[2Pm+1], sect[(Pmin+1)(Pi+Po+1)], per-warp columns
+// [nwarps][3][Pi+Po+2], then (when it fits) the D tables.
+__global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
+                       cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out) {
+    extern __shared__ cd sm[];
+    int b = lo + blockIdx.x;
+    if (mode == 0 && A.leaf[b]) return;    // a leaf keeps its P2M expansion
+    int rhs = blockIdx.y;
+    int Pm = max(Pi, Po), Pn = min(Pi, Po);
+    int Ki = (Pi + 1) * (Pi + 1), Ko = (Po + 1) * (Po + 1), Km = (Pm + 1) * (Pm + 1);
+    int NR = Pi + Po;                   // rows 0..NR
+    int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    cd* acc = sm;
+    cd* a = acc + Ko;
+    cd* bb = a + Km;
+    cd* f = bb + Km;
+    cd* pwe = f + (NR + 1);
+    cd* pwa = pwe + (2 * Pm + 1);
+    cd* sect = pwa + (2 * Pm + 1);
+    cd* cols = sect + (size_t)(Pn + 1) * (NR + 1);
+    double* Dsm = (double*)(cols + (size_t)nwarp * 3 * (NR + 2));
+    if (gscr) {
+        // large orders: the coaxial work arrays live in this block's slice of
+        // global scratch instead of shared memory
+        size_t per = (size_t)(Pn + 1) * (NR + 1) + (size_t)nwarp * 3 * (NR + 2);
+        sect = gscr + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * per;
+        cols = sect + (size_t)(Pn + 1) * (NR + 1);
+        Dsm = (double*)(pwa + (2 * Pm + 1));
+    }
+    const double* D = A.D;
+    if (d_in_smem) {
+        int64_t nd = 0;
+        for (int n = 0; n <= Pm; ++n) nd += (int64_t)(2 * n + 1) * (2 * n + 1);
+        for (int64_t k = threadIdx.x; k < nd; k += blockDim.x) Dsm[k] = A.D[k];
+        D = Dsm;
+    }
+    for (int k = threadIdx.x; k < Ko; k += blockDim.x) acc[k] = cd{0, 0};
+    int qa, qb;
+    if (mode == 0) {
+        qa = A.cbeg[b];
+        qb = A.cend[b];
+    } else if (mode == 1) {
+        qa = A.loff[b];
+        qb = A.loff[b + 1];
+    } else {
+        qa = 0;
+        qb = 1;
+    }
+    for (int q = qa; q < qb; ++q) {
+        int s = mode == 0 ? q : mode == 1 ? A.lent[q] : A.parent[b];
+        __syncthreads();
+        // shift d = c_new - c_old: M2M new = parent b, old = child s; M2L new =
+        // target b, old = source s; L2L new = child b, old = parent s
+        cd d[3];
+        for (int k = 0; k < 3; ++k) d[k] = cd{A.cre[3 * b + k] - A.cre[3 * s + k], A.cim[3 * b + k] - A.cim[3 * s + k]};
+        cd s2 = d[0] * d[0] + d[1] * d[1];
+        cd t = csqrt_p(s2 + d[2] * d[2]);
+        cd sq = {0, 0}, e = {1, 0};
+        if (!(s2.x == 0.0 && s2.y == 0.0)) {
+            sq = csqrt_p(s2);
+            e = (d[0] + mul_i(d[1])) / sq;
+        }
+        cd it = cinv(t);
+        cd ea = (d[2] + mul_i(sq)) * it;
+        const cd* src = in + (int64_t)rhs * A.ncoef + A.eoff[s];
+        for (int k = threadIdx.x; k < Ki; k += blockDim.x) a[k] = src[k];
+        if (threadIdx.x == 0) {
+            // powers e^m, e_a^m for m in [-Pm, Pm]
+            cd ie = cinv(e), iea = cinv(ea);
+            pwe[Pm] = cd{1, 0};
+            pwa[Pm] = cd{1, 0};
+            for (int m = 1; m <= Pm; ++m) {
+                pwe[Pm + m] = pwe[Pm + m - 1] * e;
+                pwe[Pm - m] = pwe[Pm - m + 1] * ie;
+                pwa[Pm + m] = pwa[Pm + m - 1] * ea;
+                pwa[Pm - m] = pwa[Pm - m + 1] * iea;
+            }
+        } else if (threadIdx.x == 32) {
+            cd z = A.kappa * t;
+            if (use_h) sph_h_seq(z, NR, f);
+            else sph_j_seq(z, NR, f);
+        }
+        __syncthreads();
+        // (1) forward rotation: a <- i^m e^m a; bb = D a; bb <- e_a^m bb; a = D^T bb; a <- i^-m a
+        for (int k = threadIdx.x; k < Ki; k += blockDim.x) {
+            int n, m;
+            nm_of(k, n, m);
+            a[k] = (ipow(m) * pwe[m + Pm]) * a[k];
+        }
+        __syncthreads();
+        rot_apply(D, A.Doff, a, bb, Pi, 0);
+        __syncthreads();
+        diag_scale(bb, Pi, pwa, Pm);
+        __syncthreads();
+        rot_apply(D, A.Doff, bb, a, Pi, 1);
+        __syncthreads();
+        for (int k = threadIdx.x; k < Ki; k += blockDim.x) {
+            int n, m;
+            nm_of(k, n, m);
+            a[k] = ipow(-m) * a[k];
+        }
+        // (2) coaxial: sectorial columns (warp 0), then one warp per m
+        for (int k = threadIdx.x; k < Ko; k += blockDim.x) bb[k] = cd{0, 0};
+        if (wid == 0) {
+            for (int r = lane; r <= NR; r += 32) {
+                double sg = (r & 1) ? -1.0 : 1.0;
+                sect[r] = (sg * (2.0 * r + 1.0)) * f[r];
+            }
+            __syncwarp();
+            for (int m = 1; m <= Pn; ++m) {
+                const cd* pv = sect + (size_t)(m - 1) * (NR + 1);
+                cd* cur = sect + (size_t)m * (NR + 1);
+                int mm = m - 1;
+                double inu = 2.0 * (2.0 * mm + 1.0) / sqrt((double)(2 * mm + 1) * (2 * mm + 2));
+                for (int r = m + lane; r <= NR - m; r += 32) {
+                    double mu1 = sqrt((double)(r + 1 - mm) * (r - mm)) / (2.0 * (2.0 * r + 3.0));
+                    double nu1 = sqrt((double)(r + mm) * (r + mm + 1)) / (2.0 * (2.0 * r - 1.0));
+                    cur[r] = inu * (mu1 * pv[r + 1] + nu1 * pv[r - 1]);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int m = wid; m <= Pn; m += nwarp) {
+            cd* cm1 = cols + (size_t)wid * 3 * (NR + 2);
+            cd* c0 = cm1 + (NR + 2);
+            cd* c1 = c0 + (NR + 2);
+            const cd* sc = sect + (size_t)m * (NR + 1);
+            for (int r = lane; r <= NR; r += 32) {
+                cm1[r] = cd{0, 0};
+                c0[r] = (r >= m && r <= NR - m) ? sc[r] : cd{0, 0};
+            }
+            __syncwarp();
+            for (int c = m; c <= Pn; ++c) {
+                // column c holds T_{r,c} for rows c <= r <= NR - c
+                int rtop = min(Pm, NR - c);
+                for (int r = c + lane; r <= rtop; r += 32) {
+                    cd T = c0[r];
+                    // direct: out_r^{+-m} += T_{r c} in_c^{+-m}   (r <= Po, c <= Pi)
+                    if (r <= Po && c <= Pi) {
+                        bb[nmi(r, m)] += T * a[nmi(c, m)];
+                        if (m > 0) bb[nmi(r, -m)] += T * a[nmi(c, -m)];
+                    }
+                }
+                // symmetric part: out_c^{+-m} += sym(c, r) T_{r c} in_r^{+-m}, c < r <= Pi, c <= Po
+                if (c <= Po) {
+                    cd sp = {0, 0}, sn = {0, 0};
+                    for (int r = c + 1 + lane; r <= min(Pi, rtop); r += 32) {
+                        double sy = (2.0 * c + 1.0) / (2.0 * r + 1.0) * (((r + c) & 1) ? -1.0 : 1.0);
+                        cd T = sy * c0[r];
+                        sp += T * a[nmi(r, m)];
+                        if (m > 0) sn += T * a[nmi(r, -m)];
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sp.x += __shfl_xor_sync(0xffffffffu, sp.x, o);
+                        sp.y += __shfl_xor_sync(0xffffffffu, sp.y, o);
+                        sn.x += __shfl_xor_sync(0xffffffffu, sn.x, o);
+                        sn.y += __shfl_xor_sync(0xffffffffu, sn.y, o);
+                    }
+                    if (lane == 0) {
+                        bb[nmi(c, m)] += sp;
+                        if (m > 0) bb[nmi(c, -m)] += sn;
+                    }
+                }
+                if (c == Pn) break;
+                // next column c + 1, rows c + 1 .. NR - c - 1
+                double ac = A.al[nmi(c, m)], ib = A.ibe[nmi(c, m)];
+                __syncwarp();
+                for (int r = c + 1 + lane; r <= NR - c - 1; r += 32) {
+                    cd v = ac * cm1[r] - A.al[nmi(r + 1, m)] * c0[r + 1];
+                    if (r - 1 >= m) v += A.be[nmi(r - 1, m)] * c0[r - 1];
+                    c1[r] = ib * v;
+                }
+                __syncwarp();
+                cd* tmp = cm1;
+                cm1 = c0;
+                c0 = c1;
+                c1 = tmp;
+                for (int r = lane; r <= c; r += 32) c0[r] = cd{0, 0};
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // (3) back rotation: bb <- i^m bb; a = D bb; a <- e_a^-m a; bb = D^T a; bb <- i^-m e^-m bb
+        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
+            int n, m;
+            nm_of(k, n, m);
+            bb[k] = ipow(m) * bb[k];
+        }
+        __syncthreads();
+        rot_apply(D, A.Doff, bb, a, Po, 0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
+            int n, m;
+            nm_of(k, n, m);
+            a[k] = a[k] * pwa[Pm - m];
+        }
+        __syncthreads();
+        rot_apply(D, A.Doff, a, bb, Po, 1);
+        __syncthreads();
+        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
+            int n, m;
+            nm_of(k, n, m);
+            acc[k] += (ipow(-m) * pwe[Pm - m]) * bb[k];
+        }
+    }
+    __syncthreads();
+    cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
+        if (mode == 2) o[k] += acc[k];
+        else o[k] = acc[k];
+    }
+    (void)nb;
+}
+
+// coaxial work arrays of one block (complex entries)
+size_t tr3h_work(int Pi, int Po) {
+    int Pn = std::min(Pi, Po), NR = Pi + Po;
+    return (size_t)(Pn + 1) * (NR + 1) + (size_t)(kH3Threads / 32) * 3 * (NR + 2);
+}
+
+size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true) {
+    int Pm = std::max(Pi, Po);
+    size_t Km = (size_t)(Pm + 1) * (Pm + 1), Ko = (size_t)(Po + 1) * (Po + 1);
+    int NR = Pi + Po;
+    size_t c = Ko + 2 * Km + (NR + 1) + 2 * (2 * Pm + 1) + (work_in_smem ? tr3h_work(Pi, Po) : 0);
+    size_t bytes = c * sizeof(cd);
+    if (d_in_smem) {
+        size_t nd = 0;
+        for (int n = 0; n <= Pm; ++n) nd += (size_t)(2 * n + 1) * (2 * n + 1);
+        bytes += nd * sizeof(double);
+    }
+    return bytes;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Helm3dState {
+    int l0 = 1, nlev = 0, maxP = 0;
+    std::vector<int> Plev;
+    DevBuf<int> dPlev;
+    DevBuf<int64_t> exp_off;
+    int64_t ncoef = 0;
+    std::vector<int> leaves_l0;
+    DevBuf<int> d_leaves_l0;
+    int n_p2l = 0;
+    DevBuf<int> d_p2l_boxes;
+    H3Tables* tab = nullptr;
+    DevBuf<cd> gscr;             // coaxial work arrays of large-order translations
+};
+
+static std::mutex g_mu;
+static std::vector<std::pair<cfmm_plan_s*, Helm3dState*>>& exts() {
+    static std::vector<std::pair<cfmm_plan_s*, Helm3dState*>> v;
+    return v;
+}
+static Helm3dState* state(cfmm_plan_s* P) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& e : exts())
+        if (e.first == P) return e.second;
+    return nullptr;
+}
+void helm3d_release(cfmm_plan_s* P) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto& v = exts();
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].first == P) {
+            delete v[i].second;
+            v.erase(v.begin() + i);
+            return;
+        }
+}
+
+// smallest n with |h_n(kR) j_n(kr)| <= eps for n..n+3 (Eq. nterms_criteria_3d),
+// R = (k + 1/2) w, r = sqrt(3)/2 w; a short search first, then up to 2000
+static int nterms_helm3d_upto(int k, double eps, double kappa, double w, int pmax) {
+    double R = (k + 0.5) * w, r = std::sqrt(3.0) * 0.5 * w;
+    std::vector<cd> J(pmax + 4), H(pmax + 4);
+    sph_j_seq(cd{kappa * r, 0.0}, pmax + 3, J.data());
+    sph_h_seq(cd{kappa * R, 0.0}, pmax + 3, H.data());
+    std::vector<char> ok(pmax + 4);
+    for (int m = 0; m < pmax + 4; ++m) {
+        double a = std::sqrt(cabs2(H[m] * J[m]));
+        ok[m] = std::isfinite(a) && a <= eps;
+    }
+    for (int n = 1; n < pmax; ++n)
+        if (ok[n] && ok[n + 1] && ok[n + 2] && ok[n + 3]) return n;
+    return -1;
+}
+
+int nterms_helm3d(int k, double eps, double kappa, double w) {
+    int guess = (int)(kappa * (k + 0.5) * w) + 80;
+    if (guess < 2000) {
+        int n = nterms_helm3d_upto(k, eps, kappa, w, guess);
+        if (n > 0) return n;
+    }
+    int n = nterms_helm3d_upto(k, eps, kappa, w, 2000);
+    return n > 0 ? n : 2000;
+}
+
+void helm3d_setup(cfmm_plan_s* P) {
+    TreeDev& T = P->tree;
+    cudaStream_t st = P->stream;
+    Helm3dState* S = new Helm3dState();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        exts().push_back({P, S});
+    }
+    S->l0 = T.l0;
+    S->nlev = T.nlevels;
+    S->Plev.resize(T.nlevels);
+    for (int l = 0; l < T.nlevels; ++l) S->Plev[l] = nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, P->W / (double)(1 << l));
+    P->P = S->Plev;
+    if (T.nboxes <= 1) return;
+    int maxP = 0;
+    for (int l = S->l0; l < T.nlevels; ++l) maxP = std::max(maxP, S->Plev[l]);
+    CFMM_REQUIRE(maxP <= kH3MaxP, CFMM_EUNSUPPORTED,
+                 "3D Helmholtz: expansion order above 63 at the top expansion level (raise top_level or eps)");
+    S->maxP = maxP;
+    S->tab = tables(maxP);
+    S->dPlev.alloc(T.nlevels);
+    CFMM_CUDA(cudaMemcpyAsync(S->dPlev.get(), S->Plev.data(), sizeof(int) * T.nlevels, cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> off(T.nboxes, -1);
+    int64_t tot = 0;
+    for (int l = S->l0; l < T.nlevels; ++l)
+        for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) {
+            off[b] = tot;
+            tot += (int64_t)(S->Plev[l] + 1) * (S->Plev[l] + 1);
+        }
+    S->ncoef = tot;
+    P->ncoef = tot;
+    S->exp_off.alloc(T.nboxes);
+    CFMM_CUDA(cudaMemcpyAsync(S->exp_off.get(), off.data(), sizeof(int64_t) * T.nboxes, cudaMemcpyHostToDevice, st));
+    std::vector<int> lvl(T.nboxes), l4(T.nboxes + 1), boxes;
+    CFMM_CUDA(cudaMemcpyAsync(lvl.data(), T.level.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(l4.data(), T.loff[3].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    for (int b : T.leaf_boxes)
+        if (lvl[b] >= S->l0) S->leaves_l0.push_back(b);
+    S->d_leaves_l0.alloc(S->leaves_l0.size());
+    CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
+                              cudaMemcpyHostToDevice, st));
+    for (int b = T.level_off[S->l0]; b < T.nboxes; ++b)
+        if (l4[b + 1] > l4[b]) boxes.push_back(b);
+    S->n_p2l = (int)boxes.size();
+    S->d_p2l_boxes.alloc(boxes.size());
+    if (!boxes.empty())
+        CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
+                                  cudaMemcpyHostToDevice, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    for (auto f : {(const void*)k_p2x3h, (const void*)k_eval3h, (const void*)k_tr3h})
+        CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
+}
+
+void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
+    Helm3dState* S = state(P);
+    CFMM_REQUIRE(S, CFMM_EINVAL, "plan has no 3D Helmholtz state");
+    TreeDev& T = P->tree;
+    cudaStream_t st = P->stream;
+    auto rec = [&](int i) {
+        if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev[i], st));
+    };
+    KParams K{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->xr.get(), P->xi.get(), P->n, P->n,
+              sigma, tau, dstride, P->slp, P->dlp, P->kappa};
+    bool mixed = P->precision == CFMM_MIXED;
+    if (T.nboxes <= 1) {
+        for (int i = 2; i <= 6; ++i) rec(i);
+        launch_p2p(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
+                   T.lent[0].get(), u, nrhs, false, st, mixed);
+        rec(7);
+        rec(8);
+        return;
+    }
+    size_t need = (size_t)S->ncoef * nrhs;
+    P->mpole.alloc(need);
+    P->local.alloc(need);
+    cd* mp = P->mpole.get();
+    cd* lc = P->local.get();
+    H3Tables* TB = S->tab;
+    ZCoef zc{TB->zA.get(), TB->zB.get()};
+    Exp3hArgs A{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->n, sigma, tau, dstride, P->slp, P->dlp,
+                T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(), S->dPlev.get(),
+                S->exp_off.get(), S->ncoef, P->kappa, zc};
+    int maxP = S->maxP;
+    auto p2x_smem = [&](int& chunk) {
+        size_t nc = (size_t)(maxP + 1) * (maxP + 1);
+        size_t per = nc + (maxP + 2) + 6;
+        chunk = (int)std::max<size_t>(1, std::min<size_t>(16, (150 * 1024 / sizeof(cd) - nc) / per));
+        return sizeof(cd) * (nc + (size_t)chunk * per);
+    };
+    // (1) P2M
+    {
+        int chunk;
+        size_t smem = p2x_smem(chunk);
+        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
+        if (g.x) {
+            k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_leaves_l0.get(), nullptr, nullptr, 0, mp, chunk);
+            CFMM_LAUNCHED();
+        }
+    }
+    rec(2);
+    Tr3hArgs TA{T.cen_re.get(), T.cen_im.get(), S->exp_off.get(), S->ncoef, TB->D.get(), TB->Doff.get(),
+                TB->al.get(), TB->be.get(), TB->ibe.get(), P->kappa, T.cbeg.get(), T.cend.get(),
+                T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get()};
+    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out) {
+        if (nb <= 0) return;
+        size_t smem = tr3h_smem(Pi, Po, true);
+        int dsm = 1;
+        cd* gs = nullptr;
+        if (smem > (size_t)kH3Smem) {
+            smem = tr3h_smem(Pi, Po, false);
+            dsm = 0;
+        }
+        if (smem > (size_t)kH3Smem) {
+            smem = tr3h_smem(Pi, Po, false, false);
+            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)nb * nrhs);
+            gs = S->gscr.get();
+        }
+        CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Helmholtz translation exceeds shared memory");
+        dim3 g(nb, nrhs);
+        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out);
+        CFMM_LAUNCHED();
+    };
+    // (2) M2M: parents at level l from children at l + 1 (leaf parents get zeros
+    // from an empty child range)
+    for (int l = T.nlevels - 2; l >= S->l0; --l) {
+        int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
+        launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp);
+    }
+    rec(3);
+    // (4) M2L per level (overwrites L at levels >= l0)
+    for (int l = S->l0; l < T.nlevels; ++l) {
+        int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
+        launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc);
+    }
+    rec(4);
+    // (6) P2L
+    if (S->n_p2l > 0) {
+        int chunk;
+        size_t smem = p2x_smem(chunk);
+        dim3 g(S->n_p2l, nrhs);
+        k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_p2l_boxes.get(), T.loff[3].get(), T.lent[3].get(), 1, lc,
+                                             chunk);
+        CFMM_LAUNCHED();
+    }
+    rec(5);
+    // (7) L2L
+    for (int l = S->l0 + 1; l < T.nlevels; ++l) {
+        int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
+        launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc);
+    }
+    rec(6);
+    // (3) P2P
+    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, st, mixed);
+    rec(7);
+    // (5) M2P, (8) L2P
+    {
+        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
+        k_eval3h<<<g, 128, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
+            A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, u);
+        CFMM_LAUNCHED();
+    }
+    rec(8);
+}
+
+}  // namespace cfmm

@@ -47,6 +47,12 @@ void fmm3d_setup(cfmm_plan_s* P);
 void fmm3d_release(cfmm_plan_s* P);
 void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 
+// 3D Helmholtz expansions (helm3d.cu)
+void helm3d_setup(cfmm_plan_s* P);
+void helm3d_release(cfmm_plan_s* P);
+void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+int nterms_helm3d(int k, double eps, double kappa, double w);
+
 void upload_lag_rule_p2p();
 void upload_lag_rule_fmm2d();
 
