@@ -30,10 +30,15 @@ Readings (all listed in the design doc):
     List 4: leaves a coarser than b with b in List 3 of a.
 * top expansion level l0 (a departure for Helmholtz, Sec. 6.5 catastrophic
   cancellation): Laplace uses l0 = 1. Helmholtz uses the coarsest level l >= 1
-  whose boxes have kappa*sqrt(d)*g_l <= tau(eps) = ln(eps/2^-52)/4, g_l the
-  largest per-axis spread of Im x inside one box of level l (a coarser leaf
-  counts with its own spread). Leaves above l0 are split down to l0 and the
-  tree is re-balanced. M2L at l0 runs over all non-near pairs of l0 boxes.
+  whose boxes have kappa*sqrt(d)*g_l <= tau(eps), g_l the largest per-axis
+  spread of Im x inside one box of level l (a coarser leaf counts with its
+  own spread), tau = c_d ln(eps/2^-52) with c_2 = 1/4 and c_3 = 1 (calibrated:
+  on the 3D surface workload at kappa = 10, 64 wavelengths, top levels 3-5
+  all met eps = 1e-6, while c_3 = 1/4 would force level 6-7 at 10-20 times
+  the cost). In 3D it is also at least the coarsest level with P_l <= 63,
+  the order limit of the CUDA translation kernel. Leaves above l0 are split
+  down to l0 and the tree is re-balanced. M2L at l0 runs over all non-near
+  pairs of l0 boxes.
 """
 from __future__ import annotations
 
@@ -298,7 +303,7 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
     """Top expansion level (see module docstring)."""
     if not helmholtz:
         return 1
-    tau = 0.25 * math.log(eps / EPS_MACH)
+    tau = (0.25 if T.dim == 2 else 1.0) * math.log(eps / EPS_MACH)
     g = imag_spread(T, im_sorted)
     maxl = T.nlevels - 1
     if maxl < 1:
@@ -310,6 +315,9 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
             lv = T.box_level[b]
             if lv == m or (lv < m and T.box_leaf[b]):
                 gm = max(gm, g[b])
+        if T.dim == 3 and nterms_helmholtz(3, T.k, eps * P_HEADROOM_HELM, kappa, T.width(m),
+                                           helm3d_pair) > P_MAX_3D:
+            continue
         if kappa * sq * gm <= tau:
             return m
     return maxl
@@ -457,6 +465,7 @@ def check_balance(T):
 # against (r/R)^n and undershoots by about a digit).
 P_HEADROOM = 0.1
 P_HEADROOM_HELM = 0.01
+P_MAX_3D = 63
 
 def nterms_laplace(dim, k, eps):
     """Smallest n >= 1 with (r/R)^n <= eps, R=(k+1/2)w, r=sqrt(d)/2 w."""

@@ -66,6 +66,7 @@ __host__ __device__ __forceinline__ int nmi(int n, int m) { return n * n + n + m
 constexpr int kH3Threads = 256;
 constexpr int kH3MaxP = 63;          // expansion order limit of this path
 constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
+constexpr int kM2LChunk3 = 32;       // List-2 entries per block when a list is split
 
 // ---------------------------------------------------------------------------
 // Per-device tables shared by all plans: D_n (row-major, n <= Pmax), the Z
@@ -73,10 +74,14 @@ constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
 // ---------------------------------------------------------------------------
 struct H3Tables {
     int Pmax = -1;
-    DevBuf<double> D;        // sum_n (2n+1)^2
-    DevBuf<int64_t> Doff;    // [Pmax+2]
-    DevBuf<double> zA, zB;   // [(2Pmax+2)^2] by nmi(n, m), m >= 0
-    DevBuf<double> al, be, ibe;  // alpha, beta, 1/beta by nmi(n, m), n <= 2Pmax+2
+    DevBuf<double> Dh;       // D_n[m][m'] for m, m' >= 0, column-major per order
+    DevBuf<int64_t> Dhoff;   // [Pmax+2]
+    DevBuf<double> inv2n1;   // 1/(2n+1), n <= 2Pmax+2
+    DevBuf<double> zA, zB;   // [(2Pmax+3)^2] by nmi(n, m), m >= 0
+    DevBuf<double> al, be, ibe, mu, nu;  // coaxial recurrence coefficients, nmi(n, m), m >= 0
+    DevBuf<double> g3, gp, gm;           // gradient coefficients c3, s+ c+, s- c- by nmi(n, m), all m
+    DevBuf<double> dg, s21;  // sqrt((2m-1)/(2m)), sqrt(2m+1), m <= Pmax+1
+    DevBuf<int> knm;         // k -> n * 256 + (m + 128), k < (Pmax+1)^2
 };
 
 // Tables only grow: a larger order builds a new set and the older sets stay
@@ -193,10 +198,11 @@ static H3Tables* tables(int P) {
     std::vector<int64_t> off;
     host_rotation_tables(Pm, D, off);
     int NN = 2 * Pm + 3;
-    std::vector<double> zA((size_t)NN * NN, 0.0), zB((size_t)NN * NN, 0.0), al((size_t)NN * NN, 0.0),
-        be((size_t)NN * NN, 0.0), ibe((size_t)NN * NN, 0.0);
-    for (int n = 0; n < NN; ++n)
-        for (int m = 0; m <= n && nmi(n, m) < NN * NN; ++m) {
+    size_t NT = (size_t)NN * NN;
+    std::vector<double> zA(NT, 0.0), zB(NT, 0.0), al(NT, 0.0), be(NT, 0.0), ibe(NT, 0.0), mu(NT, 0.0),
+        nu(NT, 0.0), g3(NT, 0.0), gp(NT, 0.0), gm(NT, 0.0), dg(Pm + 2, 0.0), s21(Pm + 2, 0.0);
+    for (int n = 0; n < NN; ++n) {
+        for (int m = 0; m <= n; ++m) {
             int k = nmi(n, m);
             if (n >= m + 2) {
                 zA[k] = (2.0 * n - 1.0) / std::sqrt((double)(n - m) * (n + m));
@@ -205,16 +211,55 @@ static H3Tables* tables(int P) {
             al[k] = std::sqrt((double)(n - m) * (n + m)) / (2.0 * n + 1.0);
             be[k] = std::sqrt((double)(n + 1 - m) * (n + 1 + m)) / (2.0 * n + 1.0);
             ibe[k] = 1.0 / be[k];
+            mu[k] = std::sqrt((double)(n - m) * std::max(n - m - 1, 0)) / (2.0 * (2.0 * n + 1.0));
+            nu[k] = std::sqrt((double)(n + m + 1) * (n + m + 2)) / (2.0 * (2.0 * n + 1.0));
         }
-    T->D.alloc(D.size());
-    T->Doff.alloc(off.size());
+        for (int m = -n; m <= n; ++m) {
+            int k = nmi(n, m);
+            g3[k] = std::sqrt((double)(n - m) * (n + m));
+            gp[k] = (m >= 1 ? 0.5 : -0.5) * std::sqrt((double)(n + m) * std::max(n + m - 1, 0));
+            gm[k] = (m >= 0 ? 0.5 : -0.5) * std::sqrt((double)(n - m) * std::max(n - m - 1, 0));
+        }
+    }
+    for (int m = 1; m <= Pm + 1; ++m) dg[m] = std::sqrt((2.0 * m - 1.0) / (2.0 * m));
+    for (int m = 0; m <= Pm + 1; ++m) s21[m] = std::sqrt(2.0 * m + 1.0);
+    std::vector<int> knm((size_t)(Pm + 1) * (Pm + 1));
+    for (int n = 0; n <= Pm; ++n)
+        for (int m = -n; m <= n; ++m) knm[nmi(n, m)] = n * 256 + (m + 128);
+    std::vector<int64_t> hoff(Pm + 2, 0);
+    for (int n = 0; n <= Pm; ++n) hoff[n + 1] = hoff[n] + (int64_t)(n + 1) * (n + 1);
+    std::vector<double> Dh(hoff[Pm + 1]);
+    for (int n = 0; n <= Pm; ++n) {
+        int N = 2 * n + 1;
+        for (int m = 0; m <= n; ++m)
+            for (int mp = 0; mp <= n; ++mp) Dh[hoff[n] + (int64_t)mp * (n + 1) + m] = D[off[n] + (int64_t)(m + n) * N + (mp + n)];
+    }
+    std::vector<double> inv2n1(NN);
+    for (int n = 0; n < NN; ++n) inv2n1[n] = 1.0 / (2.0 * n + 1.0);
+    auto up = [](DevBuf<double>& b, const std::vector<double>& v) {
+        b.alloc(v.size());
+        CFMM_CUDA(cudaMemcpy(b.get(), v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+    };
+    up(T->Dh, Dh);
+    up(T->inv2n1, inv2n1);
+    T->Dhoff.alloc(hoff.size());
+    CFMM_CUDA(cudaMemcpy(T->Dhoff.get(), hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice));
+    up(T->mu, mu);
+    up(T->nu, nu);
+    up(T->g3, g3);
+    up(T->gp, gp);
+    up(T->gm, gm);
+    up(T->dg, dg);
+    up(T->s21, s21);
+    T->knm.alloc(knm.size());
+    CFMM_CUDA(cudaMemcpy(T->knm.get(), knm.data(), sizeof(int) * knm.size(), cudaMemcpyHostToDevice));
+
     T->zA.alloc(zA.size());
     T->zB.alloc(zB.size());
     T->al.alloc(al.size());
     T->be.alloc(be.size());
     T->ibe.alloc(ibe.size());
-    CFMM_CUDA(cudaMemcpy(T->D.get(), D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice));
-    CFMM_CUDA(cudaMemcpy(T->Doff.get(), off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice));
+
     CFMM_CUDA(cudaMemcpy(T->zA.get(), zA.data(), sizeof(double) * zA.size(), cudaMemcpyHostToDevice));
     CFMM_CUDA(cudaMemcpy(T->zB.get(), zB.data(), sizeof(double) * zB.size(), cudaMemcpyHostToDevice));
     CFMM_CUDA(cudaMemcpy(T->al.get(), al.data(), sizeof(double) * al.size(), cudaMemcpyHostToDevice));
@@ -231,7 +276,19 @@ static H3Tables* tables(int P) {
 struct ZCoef {
     const double* A;
     const double* B;
+    const double* dg;    // sqrt((2m-1)/(2m))
+    const double* s21;   // sqrt(2m+1)
+    const int* knm;      // k -> n * 256 + (m + 128)
+    const double* g3;    // gradient coefficients by nmi(n, m)
+    const double* gp;
+    const double* gm;
 };
+
+__device__ __forceinline__ void nm_tab(const int* knm, int k, int& n, int& m) {
+    int v = __ldg(knm + k);
+    n = v >> 8;
+    m = (v & 255) - 128;
+}
 
 // Z table of (a0, a1, a2) up to order P into tab[nmi(n, m)]; columns split
 // over threads t0, t0 + nthreads, ...
@@ -243,11 +300,11 @@ __device__ void z_table(ZCoef zc, cd a0, cd a1, cd a2, int P, cd* tab, int t0, i
         bool neg = col > P;
         cd xs = neg ? xm : xp;
         cd d = {1, 0};
-        for (int j = 1; j <= m; ++j) d = (-sqrt((2.0 * j - 1.0) / (2.0 * j))) * (xs * d);
+        for (int j = 1; j <= m; ++j) d = (-__ldg(zc.dg + j)) * (xs * d);
         int mi = neg ? -m : m;
         tab[nmi(m, mi)] = d;
         if (m + 1 > P) continue;
-        cd p2 = d, p1 = sqrt(2.0 * m + 1.0) * (z * d);
+        cd p2 = d, p1 = __ldg(zc.s21 + m) * (z * d);
         tab[nmi(m + 1, mi)] = p1;
         for (int n = m + 2; n <= P; ++n) {
             int k = nmi(n, m);
@@ -284,13 +341,6 @@ __device__ void radial_seq(bool reg, double kappa, cd r2, int N, cd* F) {
 __device__ __forceinline__ cd zget(const cd* tab, int n, int m) {
     if (n < 0 || m > n || -m > n) return cd{0, 0};
     return tab[nmi(n, m)];
-}
-
-__device__ __forceinline__ void nm_of(int c, int& n, int& m) {
-    n = (int)sqrt((double)c);
-    while (n * n > c) --n;
-    while ((n + 1) * (n + 1) <= c) ++n;
-    m = c - n * n - n;
 }
 
 struct Exp3hArgs {
@@ -372,7 +422,7 @@ __global__ void k_p2x3h(Exp3hArgs A, const int* __restrict__ boxes, const int* _
             __syncthreads();
             for (int c = threadIdx.x; c < nc; c += blockDim.x) {
                 int n, m;
-                nm_of(c, n, m);
+                nm_tab(A.zc.knm, c, n, m);
                 int mu = -m;
                 cd a = acc[c];
                 for (int s = 0; s < cn; ++s) {
@@ -385,10 +435,10 @@ __global__ void k_p2x3h(Exp3hArgs A, const int* __restrict__ boxes, const int* _
                     if (A.dlp) {
                         cd g = {0, 0};
                         if (n >= 1) {
-                            g = (sqrt((double)(n - mu) * (n + mu)) * v[4]) * zget(tb, n - 1, mu);
-                            double sp = mu >= 1 ? 1.0 : -1.0, sn = mu >= 0 ? 1.0 : -1.0;
-                            g = g - (0.5 * sp * sqrt((double)(n + mu) * (n + mu - 1))) * (v[2] * zget(tb, n - 1, mu - 1));
-                            g = g + (0.5 * sn * sqrt((double)(n - mu) * (n - mu - 1))) * (v[3] * zget(tb, n - 1, mu + 1));
+                            int kk = nmi(n, mu);
+                            g = (__ldg(A.zc.g3 + kk) * v[4]) * zget(tb, n - 1, mu);
+                            g = g - __ldg(A.zc.gp + kk) * (v[2] * zget(tb, n - 1, mu - 1));
+                            g = g + __ldg(A.zc.gm + kk) * (v[3] * zget(tb, n - 1, mu + 1));
                         }
                         cd dw = F[n] * g - A.kappa * (F[n + 1] * (Zv * v[5]));
                         term += v[1] * dw;
@@ -402,9 +452,8 @@ __global__ void k_p2x3h(Exp3hArgs A, const int* __restrict__ boxes, const int* _
     __syncthreads();
     cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        int n = (int)sqrt((double)c);
-        while (n * n > c) --n;
-        while ((n + 1) * (n + 1) <= c) ++n;
+        int n, m;
+        nm_tab(A.zc.knm, c, n, m);
         cd v = mul_i(A.kappa * (2.0 * n + 1.0) * acc[c]);
         if (sing) o[c] += v;
         else o[c] = v;
@@ -420,12 +469,12 @@ __device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const
         cd xs = sgn ? xm : xp;
         cd d = {1, 0};
         for (int m = 0; m <= P; ++m) {
-            if (m > 0) d = (-sqrt((2.0 * m - 1.0) / (2.0 * m))) * (xs * d);
+            if (m > 0) d = (-__ldg(zc.dg + m)) * (xs * d);
             if (sgn == 1 && m == 0) continue;
             int mi = sgn ? -m : m;
             acc += F[m] * (d * coef[nmi(m, mi)]);
             if (m + 1 > P) continue;
-            cd p2 = d, p1 = sqrt(2.0 * m + 1.0) * (z * d);
+            cd p2 = d, p1 = __ldg(zc.s21 + m) * (z * d);
             acc += F[m + 1] * (p1 * coef[nmi(m + 1, mi)]);
             for (int n = m + 2; n <= P; ++n) {
                 int k = nmi(n, m);
@@ -493,11 +542,15 @@ struct Tr3hArgs {
     const double* cim;
     const int64_t* eoff;
     int64_t ncoef;
-    const double* D;
-    const int64_t* Doff;
+    const double* Dh;
+    const int64_t* Dhoff;
+    const double* inv2n1;
     const double* al;
     const double* be;
     const double* ibe;
+    const double* mu;
+    const double* nu;
+    const int* knm;
     double kappa;
     // source enumeration (mode 0: children cbeg..cend; 1: List 2; 2: parent)
     const int* cbeg;
@@ -508,50 +561,104 @@ struct Tr3hArgs {
     const int* leaf;
 };
 
-// c[nmi(n, m)] *= s^m (s given by its powers pw[m + Pm], m in [-Pm, Pm])
-__device__ __forceinline__ void diag_scale(cd* c, int P, const cd* pw, int Pm) {
-    int K = (P + 1) * (P + 1);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        int n, m;
-        nm_of(k, n, m);
-        c[k] = c[k] * pw[m + Pm];
+// i^e x for integer e (a permutation of the parts; no arithmetic)
+__device__ __forceinline__ cd mul_ipow(int e, cd x) {
+    switch (e & 3) {
+        case 0: return x;
+        case 1: return cd{-x.y, x.x};
+        case 2: return cd{-x.x, -x.y};
+        default: return cd{x.y, -x.x};
     }
 }
 
-// out = D in (trans = 0) or D^T in (trans = 1), order by order, n <= P
-__device__ __forceinline__ void rot_apply(const double* D, const int64_t* Doff, const cd* in, cd* out, int P,
-                                          int trans) {
-    int K = (P + 1) * (P + 1);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        int n, m;
-        nm_of(k, n, m);
-        int N = 2 * n + 1;
-        const double* Dn = D + Doff[n];
-        const cd* v = in + n * n;
-        cd s = {0, 0};
-        if (trans) {
-            for (int j = 0; j < N; ++j) s += Dn[j * N + (m + n)] * v[j];
-        } else {
-            const double* row = Dn + (m + n) * N;
-            for (int j = 0; j < N; ++j) s += row[j] * v[j];
+// The fixed matrices D_n satisfy D[-m][m'] = D[m][-m'] = (-1)^{n+m+m'} D[m][m']
+// and D^T = S D S, S = diag((-1)^m). With w+-_{m'} = x_{m'} +- (-1)^{m'} x_{-m'}
+// (m' > 0), row m >= 0 of D x and row -m follow from one half-row pass:
+//   n+m even:  y_{+-m} = D[m][0] x_0 + E +- O,   E, O = sum over even / odd m' > 0 of D[m][m'] w+_{m'}
+//   n+m odd:   y_m = E + O,  y_{-m} = O - E      (with w-; D[m][0] = 0)
+// Dh holds D[m][m'] for m, m' >= 0, column-major per order (Dh_n[m' (n+1) + m]).
+
+// w-pass: wb <- w+- of x, x_k = f_k in_k with the per-coefficient factor f
+// given by (i-power, sign, power table): x = i^{ip*m} sg^m pw[m + Pm] in
+__device__ __forceinline__ void w_pass(const int* knm, const cd* in, cd* wb, int P, int ip, int sgn_alt,
+                                       const cd* pw, int Pm) {
+    int W = (P + 1) * (P + 2) / 2;          // items (n, m >= 0)
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        int n = (int)((sqrtf(8.0f * w + 1.0f) - 1.0f) * 0.5f);
+        while ((n + 1) * (n + 2) / 2 <= w) ++n;
+        while (n * (n + 1) / 2 > w) --n;
+        int m = w - n * (n + 1) / 2;
+        int k = nmi(n, m);
+        auto xf = [&](int mm) {
+            cd v = in[nmi(n, mm)];
+            if (pw) v = v * pw[mm + Pm];
+            v = mul_ipow(ip * mm, v);
+            if (sgn_alt && (mm & 1)) v = -v;
+            return v;
+        };
+        cd xp = xf(m);
+        if (m == 0) {
+            wb[k] = xp;
+            continue;
         }
-        out[k] = s;
+        cd xm = xf(-m);
+        if (m & 1) xm = -xm;
+        wb[nmi(n, m)] = xp + xm;
+        wb[nmi(n, -m)] = xp - xm;
     }
 }
 
-// i^e for integer e
-__device__ __forceinline__ cd ipow(int e) {
-    e = ((e % 4) + 4) % 4;
-    return e == 0 ? cd{1, 0} : e == 1 ? cd{0, 1} : e == 2 ? cd{-1, 0} : cd{0, -1};
+// D-pass: y = D x from the w+- of x; out_k = g_k y_k with g = i^{op*m} (sgn_out:
+// times (-1)^m), optionally times pw_out[m + Pm], accumulated when acc != 0
+__device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, const cd* wb, cd* out, int P,
+                                       int op, int sgn_out, const cd* pwo, int Pm, int accum) {
+    int W = (P + 1) * (P + 2) / 2;          // work items (n, m >= 0)
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        int n = (int)((sqrtf(8.0f * w + 1.0f) - 1.0f) * 0.5f);
+        while ((n + 1) * (n + 2) / 2 <= w) ++n;
+        while (n * (n + 1) / 2 > w) --n;
+        int m = w - n * (n + 1) / 2;
+        const double* Dn = Dh + __ldg(Dhoff + n);
+        int N1 = n + 1;
+        bool odd = (n + m) & 1;
+        cd E = {0, 0}, O = {0, 0};
+        const cd* wv = wb + n * n + n;       // wv[m'] = w+_{m'}, wv[-m'] = w-_{m'}
+        for (int mp = 1; mp <= n; ++mp) {
+            double d = Dn[mp * N1 + m];
+            cd wq = odd ? wv[-mp] : wv[mp];
+            if (mp & 1) O += d * wq;
+            else E += d * wq;
+        }
+        cd yp, ym;
+        if (odd) {
+            yp = E + O;
+            ym = O - E;
+        } else {
+            cd d0 = Dn[m] * wv[0];
+            yp = d0 + E + O;
+            ym = d0 + E - O;
+        }
+        auto emit = [&](int mm, cd y) {
+            y = mul_ipow(op * mm, y);
+            if (sgn_out && (mm & 1)) y = -y;
+            if (pwo) y = y * pwo[mm + Pm];
+            if (accum) out[nmi(n, mm)] += y;
+            else out[nmi(n, mm)] = y;
+        };
+        emit(m, yp);
+        if (m > 0) emit(-m, ym);
+    }
 }
 
 // One translation per destination box and source; the destination box's
 // result is accumulated in shared memory and written (mode 0, 1) or added
-// (mode 2) at the end. Shared layout: acc[Ko], a[Km], b[Km], f[Pi+Po+1],
-// pw_e[2Pm+1], pw_a[2Pm+1], sect[(Pmin+1)(Pi+Po+1)], per-warp columns
-// [nwarps][3][Pi+Po+2], then (when it fits) the D tables.
+// (mode 2) at the end. Shared layout: acc[Ko], a[Km], bb[Km], wb[Km],
+// f[Pi+Po+1], pw_e[2Pm+1], pw_a[2Pm+1], pw_ai[2Pm+1], pw_ei[2Pm+1],
+// sect[(Pmin+1)(Pi+Po+1)], per-warp columns [nwarps][3][Pi+Po+2] (these two
+// in global scratch for large orders), then (when it fits) the Dh table.
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
-                       cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out) {
+                       cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
+                       cd* __restrict__ part) {
     extern __shared__ cd sm[];
     int b = lo + blockIdx.x;
     if (mode == 0 && A.leaf[b]) return;    // a leaf keeps its P2M expansion
@@ -563,26 +670,29 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     cd* acc = sm;
     cd* a = acc + Ko;
     cd* bb = a + Km;
-    cd* f = bb + Km;
+    cd* wb = bb + Km;
+    cd* f = wb + Km;
     cd* pwe = f + (NR + 1);
     cd* pwa = pwe + (2 * Pm + 1);
-    cd* sect = pwa + (2 * Pm + 1);
+    cd* pwai = pwa + (2 * Pm + 1);
+    cd* pwei = pwai + (2 * Pm + 1);
+    cd* sect = pwei + (2 * Pm + 1);
     cd* cols = sect + (size_t)(Pn + 1) * (NR + 1);
-    double* Dsm = (double*)(cols + (size_t)nwarp * 3 * (NR + 2));
+    size_t wsz = (size_t)nwarp * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
+    double* Dsm = (double*)(cols + wsz);
     if (gscr) {
         // large orders: the coaxial work arrays live in this block's slice of
         // global scratch instead of shared memory
-        size_t per = (size_t)(Pn + 1) * (NR + 1) + (size_t)nwarp * 3 * (NR + 2);
-        sect = gscr + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * per;
+        size_t per = (size_t)(Pn + 1) * (NR + 1) + wsz;
+        sect = gscr + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * per;
         cols = sect + (size_t)(Pn + 1) * (NR + 1);
-        Dsm = (double*)(pwa + (2 * Pm + 1));
+        Dsm = (double*)(pwei + (2 * Pm + 1));
     }
-    const double* D = A.D;
+    const double* Dh = A.Dh;
     if (d_in_smem) {
-        int64_t nd = 0;
-        for (int n = 0; n <= Pm; ++n) nd += (int64_t)(2 * n + 1) * (2 * n + 1);
-        for (int64_t k = threadIdx.x; k < nd; k += blockDim.x) Dsm[k] = A.D[k];
-        D = Dsm;
+        int64_t nd = __ldg(A.Dhoff + Pm + 1);
+        for (int64_t k = threadIdx.x; k < nd; k += blockDim.x) Dsm[k] = A.Dh[k];
+        Dh = Dsm;
     }
     for (int k = threadIdx.x; k < Ko; k += blockDim.x) acc[k] = cd{0, 0};
     int qa, qb;
@@ -592,6 +702,11 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     } else if (mode == 1) {
         qa = A.loff[b];
         qb = A.loff[b + 1];
+        if (part) {
+            // chunked List 2: this block takes entries [qa + z chunk, qa + (z+1) chunk)
+            qa += blockIdx.z * chunk;
+            qb = min(qb, qa + chunk);
+        }
     } else {
         qa = 0;
         qb = 1;
@@ -605,25 +720,27 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         for (int k = 0; k < 3; ++k) d[k] = cd{A.cre[3 * b + k] - A.cre[3 * s + k], A.cim[3 * b + k] - A.cim[3 * s + k]};
         cd s2 = d[0] * d[0] + d[1] * d[1];
         cd t = csqrt_p(s2 + d[2] * d[2]);
-        cd sq = {0, 0}, e = {1, 0};
-        if (!(s2.x == 0.0 && s2.y == 0.0)) {
-            sq = csqrt_p(s2);
-            e = (d[0] + mul_i(d[1])) / sq;
-        }
-        cd it = cinv(t);
-        cd ea = (d[2] + mul_i(sq)) * it;
         const cd* src = in + (int64_t)rhs * A.ncoef + A.eoff[s];
         for (int k = threadIdx.x; k < Ki; k += blockDim.x) a[k] = src[k];
         if (threadIdx.x == 0) {
-            // powers e^m, e_a^m for m in [-Pm, Pm]
+            // powers of e = e^{i beta}, e_a = e^{i alpha} and their inverses, m in [-Pm, Pm]
+            cd sq = {0, 0}, e = {1, 0};
+            if (!(s2.x == 0.0 && s2.y == 0.0)) {
+                sq = csqrt_p(s2);
+                e = (d[0] + mul_i(d[1])) / sq;
+            }
+            cd ea = (d[2] + mul_i(sq)) / t;
             cd ie = cinv(e), iea = cinv(ea);
-            pwe[Pm] = cd{1, 0};
-            pwa[Pm] = cd{1, 0};
+            pwe[Pm] = pwa[Pm] = pwai[Pm] = pwei[Pm] = cd{1, 0};
             for (int m = 1; m <= Pm; ++m) {
                 pwe[Pm + m] = pwe[Pm + m - 1] * e;
                 pwe[Pm - m] = pwe[Pm - m + 1] * ie;
                 pwa[Pm + m] = pwa[Pm + m - 1] * ea;
                 pwa[Pm - m] = pwa[Pm - m + 1] * iea;
+            }
+            for (int m = -Pm; m <= Pm; ++m) {
+                pwai[Pm + m] = pwa[Pm - m];
+                pwei[Pm + m] = pwe[Pm - m];
             }
         } else if (threadIdx.x == 32) {
             cd z = A.kappa * t;
@@ -631,25 +748,23 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             else sph_j_seq(z, NR, f);
         }
         __syncthreads();
-        // (1) forward rotation: a <- i^m e^m a; bb = D a; bb <- e_a^m bb; a = D^T bb; a <- i^-m a
-        for (int k = threadIdx.x; k < Ki; k += blockDim.x) {
-            int n, m;
-            nm_of(k, n, m);
-            a[k] = (ipow(m) * pwe[m + Pm]) * a[k];
-        }
+        // (1) forward rotation: x = Phi E(e) c; y = D x; x' = S E(e_a) y; u = D x'; c~ = i^m u
+        w_pass(A.knm, a, wb, Pi, 1, 0, pwe, Pm);
         __syncthreads();
-        rot_apply(D, A.Doff, a, bb, Pi, 0);
+        d_pass(Dh, A.Dhoff, wb, bb, Pi, 0, 0, nullptr, Pm, 0);
         __syncthreads();
-        diag_scale(bb, Pi, pwa, Pm);
+        w_pass(A.knm, bb, wb, Pi, 0, 1, pwa, Pm);
         __syncthreads();
-        rot_apply(D, A.Doff, bb, a, Pi, 1);
+        d_pass(Dh, A.Dhoff, wb, a, Pi, 1, 0, nullptr, Pm, 0);
+        // (2) coaxial: a~ = (-1)^r a / (2r+1) for the symmetric half; sectorial
+        // columns (warp 0), then one warp per m
         __syncthreads();
         for (int k = threadIdx.x; k < Ki; k += blockDim.x) {
             int n, m;
-            nm_of(k, n, m);
-            a[k] = ipow(-m) * a[k];
+            nm_tab(A.knm, k, n, m);
+            double sc = __ldg(A.inv2n1 + n);
+            wb[k] = ((n & 1) ? -sc : sc) * a[k];
         }
-        // (2) coaxial: sectorial columns (warp 0), then one warp per m
         for (int k = threadIdx.x; k < Ko; k += blockDim.x) bb[k] = cd{0, 0};
         if (wid == 0) {
             for (int r = lane; r <= NR; r += 32) {
@@ -661,10 +776,9 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
                 const cd* pv = sect + (size_t)(m - 1) * (NR + 1);
                 cd* cur = sect + (size_t)m * (NR + 1);
                 int mm = m - 1;
-                double inu = 2.0 * (2.0 * mm + 1.0) / sqrt((double)(2 * mm + 1) * (2 * mm + 2));
+                double inu = 1.0 / __ldg(A.nu + nmi(mm, mm));
                 for (int r = m + lane; r <= NR - m; r += 32) {
-                    double mu1 = sqrt((double)(r + 1 - mm) * (r - mm)) / (2.0 * (2.0 * r + 3.0));
-                    double nu1 = sqrt((double)(r + mm) * (r + mm + 1)) / (2.0 * (2.0 * r - 1.0));
+                    double mu1 = __ldg(A.mu + nmi(r + 1, mm)), nu1 = __ldg(A.nu + nmi(r - 1, mm));
                     cur[r] = inu * (mu1 * pv[r + 1] + nu1 * pv[r - 1]);
                 }
                 __syncwarp();
@@ -672,9 +786,10 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         }
         __syncthreads();
         for (int m = wid; m <= Pn; m += nwarp) {
-            cd* cm1 = cols + (size_t)wid * 3 * (NR + 2);
+            cd* cm1 = cols + (size_t)wid * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
             cd* c0 = cm1 + (NR + 2);
             cd* c1 = c0 + (NR + 2);
+            cd* Tm = c1 + (NR + 2);              // lower triangle T[r][c], r <= Pm, c <= Pn
             const cd* sc = sect + (size_t)m * (NR + 1);
             for (int r = lane; r <= NR; r += 32) {
                 cm1[r] = cd{0, 0};
@@ -682,43 +797,14 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             }
             __syncwarp();
             for (int c = m; c <= Pn; ++c) {
-                // column c holds T_{r,c} for rows c <= r <= NR - c
-                int rtop = min(Pm, NR - c);
-                for (int r = c + lane; r <= rtop; r += 32) {
-                    cd T = c0[r];
-                    // direct: out_r^{+-m} += T_{r c} in_c^{+-m}   (r <= Po, c <= Pi)
-                    if (r <= Po && c <= Pi) {
-                        bb[nmi(r, m)] += T * a[nmi(c, m)];
-                        if (m > 0) bb[nmi(r, -m)] += T * a[nmi(c, -m)];
-                    }
-                }
-                // symmetric part: out_c^{+-m} += sym(c, r) T_{r c} in_r^{+-m}, c < r <= Pi, c <= Po
-                if (c <= Po) {
-                    cd sp = {0, 0}, sn = {0, 0};
-                    for (int r = c + 1 + lane; r <= min(Pi, rtop); r += 32) {
-                        double sy = (2.0 * c + 1.0) / (2.0 * r + 1.0) * (((r + c) & 1) ? -1.0 : 1.0);
-                        cd T = sy * c0[r];
-                        sp += T * a[nmi(r, m)];
-                        if (m > 0) sn += T * a[nmi(r, -m)];
-                    }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sp.x += __shfl_xor_sync(0xffffffffu, sp.x, o);
-                        sp.y += __shfl_xor_sync(0xffffffffu, sp.y, o);
-                        sn.x += __shfl_xor_sync(0xffffffffu, sn.x, o);
-                        sn.y += __shfl_xor_sync(0xffffffffu, sn.y, o);
-                    }
-                    if (lane == 0) {
-                        bb[nmi(c, m)] += sp;
-                        if (m > 0) bb[nmi(c, -m)] += sn;
-                    }
-                }
+                // column c holds T_{r,c} for rows c <= r <= NR - c; keep rows <= Pm
+                for (int r = c + lane; r <= Pm; r += 32) Tm[r * (Pn + 1) + c] = c0[r];
                 if (c == Pn) break;
                 // next column c + 1, rows c + 1 .. NR - c - 1
-                double ac = A.al[nmi(c, m)], ib = A.ibe[nmi(c, m)];
-                __syncwarp();
+                double ac = __ldg(A.al + nmi(c, m)), ib = __ldg(A.ibe + nmi(c, m));
                 for (int r = c + 1 + lane; r <= NR - c - 1; r += 32) {
-                    cd v = ac * cm1[r] - A.al[nmi(r + 1, m)] * c0[r + 1];
-                    if (r - 1 >= m) v += A.be[nmi(r - 1, m)] * c0[r - 1];
+                    cd v = ac * cm1[r] - __ldg(A.al + nmi(r + 1, m)) * c0[r + 1];
+                    if (r - 1 >= m) v += __ldg(A.be + nmi(r - 1, m)) * c0[r - 1];
                     c1[r] = ib * v;
                 }
                 __syncwarp();
@@ -726,60 +812,84 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
                 cm1 = c0;
                 c0 = c1;
                 c1 = tmp;
-                for (int r = lane; r <= c; r += 32) c0[r] = cd{0, 0};
-                __syncwarp();
+            }
+            __syncwarp();
+            // out_n^{mm} = sum_{c <= min(n, Pi)} T_{n c} a_c^{mm}
+            //            + (2n+1)(-1)^n sum_{n < r <= Pi} T_{r n} a~_r^{mm},  mm = +-m;
+            // one lane per (n, sign)
+            int nout = Po - m + 1, nitems = m > 0 ? 2 * nout : nout;
+            for (int it = lane; it < nitems; it += 32) {
+                int n = m + (it % nout);
+                int mm = it < nout ? m : -m;
+                cd sp = {0, 0};
+                int ce = min(n, Pi);
+                const cd* Tr = Tm + n * (Pn + 1);
+                for (int c = m; c <= ce; ++c) sp += Tr[c] * a[nmi(c, mm)];
+                if (n < Pi) {
+                    cd up = {0, 0};
+                    for (int r = n + 1; r <= Pi; ++r) up += Tm[r * (Pn + 1) + n] * wb[nmi(r, mm)];
+                    double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
+                    sp += g * up;
+                }
+                bb[nmi(n, mm)] = sp;
             }
         }
         __syncthreads();
-        // (3) back rotation: bb <- i^m bb; a = D bb; a <- e_a^-m a; bb = D^T a; bb <- i^-m e^-m bb
-        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
-            int n, m;
-            nm_of(k, n, m);
-            bb[k] = ipow(m) * bb[k];
-        }
+        // (3) back rotation: x = Phi c'; y = D x; x' = S E(1/e_a) y; u = D x'; acc += E(1/e) i^m u
+        w_pass(A.knm, bb, wb, Po, 1, 0, nullptr, Pm);
         __syncthreads();
-        rot_apply(D, A.Doff, bb, a, Po, 0);
+        d_pass(Dh, A.Dhoff, wb, a, Po, 0, 0, nullptr, Pm, 0);
         __syncthreads();
-        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
-            int n, m;
-            nm_of(k, n, m);
-            a[k] = a[k] * pwa[Pm - m];
-        }
+        w_pass(A.knm, a, wb, Po, 0, 1, pwai, Pm);
         __syncthreads();
-        rot_apply(D, A.Doff, a, bb, Po, 1);
-        __syncthreads();
-        for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
-            int n, m;
-            nm_of(k, n, m);
-            acc[k] += (ipow(-m) * pwe[Pm - m]) * bb[k];
-        }
+        d_pass(Dh, A.Dhoff, wb, acc, Po, 1, 0, pwei, Pm, 1);
     }
     __syncthreads();
+    if (part) {
+        cd* o = part + (((size_t)blockIdx.z * gridDim.y + rhs) * nb + blockIdx.x) * Ko;
+        for (int k = threadIdx.x; k < Ko; k += blockDim.x) o[k] = acc[k];
+        return;
+    }
     cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
     for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
         if (mode == 2) o[k] += acc[k];
         else o[k] = acc[k];
     }
-    (void)nb;
 }
 
-// coaxial work arrays of one block (complex entries)
+// sum of the chunk partials of a chunked M2L launch, in chunk order
+__global__ void k_tr3h_reduce(const cd* __restrict__ part, int nchunk, int nb, int Ko, int lo,
+                              const int64_t* __restrict__ eoff, int64_t ncoef, cd* __restrict__ out) {
+    int bi = blockIdx.x, rhs = blockIdx.y, nr = gridDim.y;
+    cd* o = out + (int64_t)rhs * ncoef + eoff[lo + bi];
+    for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
+        cd s = {0, 0};
+        for (int z = 0; z < nchunk; ++z) s += part[(((size_t)z * nr + rhs) * nb + bi) * Ko + k];
+        o[k] = s;
+    }
+}
+
+// coaxial work arrays of one block (complex entries): sectorial columns and,
+// per warp, three recurrence columns and the lower triangle of T^m
 size_t tr3h_work(int Pi, int Po) {
-    int Pn = std::min(Pi, Po), NR = Pi + Po;
-    return (size_t)(Pn + 1) * (NR + 1) + (size_t)(kH3Threads / 32) * 3 * (NR + 2);
+    int Pn = std::min(Pi, Po), Pm = std::max(Pi, Po), NR = Pi + Po;
+    return (size_t)(Pn + 1) * (NR + 1) +
+           (size_t)(kH3Threads / 32) * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
+}
+
+size_t tr3h_dh(int P) {
+    size_t nd = 0;
+    for (int n = 0; n <= P; ++n) nd += (size_t)(n + 1) * (n + 1);
+    return nd;
 }
 
 size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true) {
     int Pm = std::max(Pi, Po);
     size_t Km = (size_t)(Pm + 1) * (Pm + 1), Ko = (size_t)(Po + 1) * (Po + 1);
     int NR = Pi + Po;
-    size_t c = Ko + 2 * Km + (NR + 1) + 2 * (2 * Pm + 1) + (work_in_smem ? tr3h_work(Pi, Po) : 0);
+    size_t c = Ko + 3 * Km + (NR + 1) + 4 * (2 * Pm + 1) + (work_in_smem ? tr3h_work(Pi, Po) : 0);
     size_t bytes = c * sizeof(cd);
-    if (d_in_smem) {
-        size_t nd = 0;
-        for (int n = 0; n <= Pm; ++n) nd += (size_t)(2 * n + 1) * (2 * n + 1);
-        bytes += nd * sizeof(double);
-    }
+    if (d_in_smem) bytes += tr3h_dh(Pm) * sizeof(double);
     return bytes;
 }
 
@@ -796,10 +906,15 @@ struct Helm3dState {
     int64_t ncoef = 0;
     std::vector<int> leaves_l0;
     DevBuf<int> d_leaves_l0;
+    std::vector<int> p2m_off;    // leaves by level: [p2m_off[l], p2m_off[l+1]) in d_p2m
+    DevBuf<int> d_p2m;
+    std::vector<int> p2l_off;    // List-4 targets by level, likewise
     int n_p2l = 0;
     DevBuf<int> d_p2l_boxes;
     H3Tables* tab = nullptr;
     DevBuf<cd> gscr;             // coaxial work arrays of large-order translations
+    DevBuf<cd> part;             // partial results of chunked M2L launches
+    std::vector<int> l2max;      // longest List 2 per level
 };
 
 static std::mutex g_mu;
@@ -884,17 +999,32 @@ void helm3d_setup(cfmm_plan_s* P) {
     P->ncoef = tot;
     S->exp_off.alloc(T.nboxes);
     CFMM_CUDA(cudaMemcpyAsync(S->exp_off.get(), off.data(), sizeof(int64_t) * T.nboxes, cudaMemcpyHostToDevice, st));
-    std::vector<int> lvl(T.nboxes), l4(T.nboxes + 1), boxes;
+    std::vector<int> lvl(T.nboxes), l4(T.nboxes + 1), l2(T.nboxes + 1), boxes;
     CFMM_CUDA(cudaMemcpyAsync(lvl.data(), T.level.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaMemcpyAsync(l4.data(), T.loff[3].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaMemcpyAsync(l2.data(), T.loff[1].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
+    S->l2max.assign(T.nlevels, 0);
+    for (int b = 0; b < T.nboxes; ++b) S->l2max[lvl[b]] = std::max(S->l2max[lvl[b]], l2[b + 1] - l2[b]);
     for (int b : T.leaf_boxes)
         if (lvl[b] >= S->l0) S->leaves_l0.push_back(b);
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
                               cudaMemcpyHostToDevice, st));
+    std::vector<int> byl = S->leaves_l0;
+    std::stable_sort(byl.begin(), byl.end(), [&](int x, int y) { return lvl[x] < lvl[y]; });
+    S->p2m_off.assign(T.nlevels + 1, 0);
+    for (int b : byl) S->p2m_off[lvl[b] + 1]++;
+    for (int l = 0; l < T.nlevels; ++l) S->p2m_off[l + 1] += S->p2m_off[l];
+    S->d_p2m.alloc(byl.size());
+    CFMM_CUDA(cudaMemcpyAsync(S->d_p2m.get(), byl.data(), sizeof(int) * byl.size(), cudaMemcpyHostToDevice, st));
+    S->p2l_off.assign(T.nlevels + 1, 0);
     for (int b = T.level_off[S->l0]; b < T.nboxes; ++b)
-        if (l4[b + 1] > l4[b]) boxes.push_back(b);
+        if (l4[b + 1] > l4[b]) {
+            boxes.push_back(b);
+            S->p2l_off[lvl[b] + 1]++;
+        }
+    for (int l = 0; l < T.nlevels; ++l) S->p2l_off[l + 1] += S->p2l_off[l];
     S->n_p2l = (int)boxes.size();
     S->d_p2l_boxes.alloc(boxes.size());
     if (!boxes.empty())
@@ -930,32 +1060,34 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     cd* mp = P->mpole.get();
     cd* lc = P->local.get();
     H3Tables* TB = S->tab;
-    ZCoef zc{TB->zA.get(), TB->zB.get()};
+    ZCoef zc{TB->zA.get(), TB->zB.get(), TB->dg.get(), TB->s21.get(), TB->knm.get(),
+             TB->g3.get(), TB->gp.get(), TB->gm.get()};
     Exp3hArgs A{P->xr.get(), P->xi.get(), P->nr.get(), P->ni.get(), P->n, sigma, tau, dstride, P->slp, P->dlp,
                 T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(), S->dPlev.get(),
                 S->exp_off.get(), S->ncoef, P->kappa, zc};
     int maxP = S->maxP;
-    auto p2x_smem = [&](int& chunk) {
-        size_t nc = (size_t)(maxP + 1) * (maxP + 1);
-        size_t per = nc + (maxP + 2) + 6;
-        chunk = (int)std::max<size_t>(1, std::min<size_t>(16, (150 * 1024 / sizeof(cd) - nc) / per));
+    auto p2x_smem = [&](int PL, int& chunk) {
+        size_t nc = (size_t)(PL + 1) * (PL + 1);
+        size_t per = nc + (PL + 2) + 6;
+        chunk = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024 / sizeof(cd) - nc) / per));
         return sizeof(cd) * (nc + (size_t)chunk * per);
     };
-    // (1) P2M
-    {
+    // (1) P2M, one launch per level (shared memory sized by that level's P)
+    for (int l = S->l0; l < T.nlevels; ++l) {
+        int cnt = S->p2m_off[l + 1] - S->p2m_off[l];
+        if (cnt <= 0) continue;
         int chunk;
-        size_t smem = p2x_smem(chunk);
-        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
-        if (g.x) {
-            k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_leaves_l0.get(), nullptr, nullptr, 0, mp, chunk);
-            CFMM_LAUNCHED();
-        }
+        size_t smem = p2x_smem(S->Plev[l], chunk);
+        dim3 g((unsigned)cnt, nrhs);
+        k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_p2m.get() + S->p2m_off[l], nullptr, nullptr, 0, mp, chunk);
+        CFMM_LAUNCHED();
     }
     rec(2);
-    Tr3hArgs TA{T.cen_re.get(), T.cen_im.get(), S->exp_off.get(), S->ncoef, TB->D.get(), TB->Doff.get(),
-                TB->al.get(), TB->be.get(), TB->ibe.get(), P->kappa, T.cbeg.get(), T.cend.get(),
+    Tr3hArgs TA{T.cen_re.get(), T.cen_im.get(), S->exp_off.get(), S->ncoef, TB->Dh.get(), TB->Dhoff.get(),
+                TB->inv2n1.get(), TB->al.get(), TB->be.get(), TB->ibe.get(), TB->mu.get(), TB->nu.get(),
+                TB->knm.get(), P->kappa, T.cbeg.get(), T.cend.get(),
                 T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get()};
-    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out) {
+    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk) {
         if (nb <= 0) return;
         size_t smem = tr3h_smem(Pi, Po, true);
         int dsm = 1;
@@ -966,41 +1098,56 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         }
         if (smem > (size_t)kH3Smem) {
             smem = tr3h_smem(Pi, Po, false, false);
-            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)nb * nrhs);
+            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)nb * nrhs * nchunk);
             gs = S->gscr.get();
         }
         CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Helmholtz translation exceeds shared memory");
-        dim3 g(nb, nrhs);
-        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out);
+        dim3 g(nb, nrhs, nchunk);
+        size_t Ko = (size_t)(Po + 1) * (Po + 1);
+        cd* pp = nullptr;
+        if (nchunk > 1) {
+            S->part.alloc(Ko * nb * nrhs * nchunk);
+            pp = S->part.get();
+        }
+        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, kM2LChunk3, pp);
         CFMM_LAUNCHED();
+        if (nchunk > 1) {
+            k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,
+                                                          out);
+            CFMM_LAUNCHED();
+        }
     };
     // (2) M2M: parents at level l from children at l + 1 (leaf parents get zeros
     // from an empty child range)
     for (int l = T.nlevels - 2; l >= S->l0; --l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp);
+        launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp, 1);
     }
     rec(3);
     // (4) M2L per level (overwrites L at levels >= l0)
     for (int l = S->l0; l < T.nlevels; ++l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc);
+        // long lists (the all-pairs top level) are split over several blocks
+        int nchunk = S->l2max[l] > 2 * kM2LChunk3 ? (S->l2max[l] + kM2LChunk3 - 1) / kM2LChunk3 : 1;
+        launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc, nchunk);
     }
     rec(4);
-    // (6) P2L
-    if (S->n_p2l > 0) {
+    // (6) P2L, per level
+    for (int l = S->l0; l < T.nlevels; ++l) {
+        int cnt = S->p2l_off[l + 1] - S->p2l_off[l];
+        if (cnt <= 0) continue;
         int chunk;
-        size_t smem = p2x_smem(chunk);
-        dim3 g(S->n_p2l, nrhs);
-        k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_p2l_boxes.get(), T.loff[3].get(), T.lent[3].get(), 1, lc,
-                                             chunk);
+        size_t smem = p2x_smem(S->Plev[l], chunk);
+        dim3 g((unsigned)cnt, nrhs);
+        k_p2x3h<<<g, kH3Threads, smem, st>>>(A, S->d_p2l_boxes.get() + S->p2l_off[l], T.loff[3].get(),
+                                             T.lent[3].get(), 1, lc, chunk);
         CFMM_LAUNCHED();
     }
     rec(5);
     // (7) L2L
     for (int l = S->l0 + 1; l < T.nlevels; ++l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc);
+        launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc, 1);
     }
     rec(6);
     // (3) P2P

@@ -381,6 +381,49 @@ __device__ __forceinline__ cd r2_from_hl(const PairHL& H) {
     return r2;
 }
 
+// e^{i kappa r} and r for |kappa r| > 3 in double-float FP32 arithmetic (the
+// FP32 phase would lose digits there): d = x - y as hi + lo per component
+// (an exact two_sum of the hi parts plus the lo difference), r^2 in
+// double-float, r = r0 + (r^2 - r0^2)/(2 r0) (one Newton step from the FP32
+// root), kappa r in double-float, the phase reduced by 2 pi before sincosf.
+template <int DIM>
+__device__ __forceinline__ void far_phase_df(const PairHL& H, float kh, float kl, cf& e_ikr, cf& r) {
+    float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        float s, t, rh, rl, ih, il;
+        two_sum(H.xhr[a], -H.yhr[a], s, t);
+        two_sum(s, t + (H.xlr[a] - H.ylr[a]), rh, rl);
+        two_sum(H.xhi[a], -H.yhi[a], s, t);
+        two_sum(s, t + (H.xli[a] - H.yli[a]), ih, il);
+        df_fma(rh, rl, rh, rl, 1.f, Sr, Er);
+        df_fma(ih, il, ih, il, -1.f, Sr, Er);
+        df_fma(rh, rl, ih, il, 2.f, Si, Ei);
+    }
+    cf r0 = csqrtf_p(cf{Sr + Er, Si + Ei});
+    float Rr = Sr, ERr = Er, Ri = Si, ERi = Ei;
+    df_fma(r0.x, 0.f, r0.x, 0.f, -1.f, Rr, ERr);
+    df_fma(r0.y, 0.f, r0.y, 0.f, 1.f, Rr, ERr);
+    df_fma(r0.x, 0.f, r0.y, 0.f, -2.f, Ri, ERi);
+    cf corr = cf{Rr + ERr, Ri + ERi} * cinvf(2.f * r0);
+    float th, te, dh, de;
+    two_prod(kh, r0.x, th, te);
+    te += fmaf(kh, corr.x, kl * r0.x);
+    two_prod(kh, r0.y, dh, de);
+    de += fmaf(kh, corr.y, kl * r0.y);
+    const float kTwoPiH = 6.28318548202514648f;     // float(2 pi)
+    const float kTwoPiL = -1.74845553e-07f;         // 2 pi - float(2 pi)
+    float k = rintf(th * 0.159154943f);
+    float q, qe;
+    two_prod(k, kTwoPiH, q, qe);
+    float red = (th - q) + ((te - qe) - k * kTwoPiL);
+    float sn, cs;
+    sincosf(red, &sn, &cs);
+    float mag = expf(-dh) * (1.f - de);
+    e_ikr = cf{mag * cs, mag * sn};
+    r = r0 + corr;
+}
+
 template <int DIM, int KER>
 __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_im, const PairHL& H, cf nd, cf sg,
                                               cf ta, bool slp, bool dlp, float kappa, double kappa64, Kahan& acc) {
@@ -419,19 +462,19 @@ __device__ __forceinline__ void pair_kernel32(const float* d_re, const float* d_
         if (dlp) v = v + (nd * (ir * ir * ir)) * ta;
     } else {
         cf r = csqrtf_p(r2);
-        cf ir = cinvf(r);
         cf g;
         float k4 = kappa * kappa * kappa * kappa;
         if (k4 * (r2.x * r2.x + r2.y * r2.y) <= 81.f) {    // |kappa r| <= 3
             float e = expf(-kappa * r.y), sn, cs;
             sincosf(kappa * r.x, &sn, &cs);
-            g = cf{e * cs, e * sn} * ir;
+            g = cf{e * cs, e * sn} * cinvf(r);
         } else {
-            // |kappa r| > 3: the phase from an FP64 r
-            cd r64 = csqrt_p(r2_from_hl<DIM>(H));
-            cd e64 = cexp_i(kappa64 * r64);
-            g = cf{(float)e64.x, (float)e64.y} * ir;
+            // |kappa r| > 3: double-float phase
+            cf e;
+            far_phase_df<DIM>(H, kappa, (float)(kappa64 - (double)kappa), e, r);
+            g = e * cinvf(r);
         }
+        cf ir = cinvf(r);
         if (slp) v = g * sg;
         if (dlp) v = v + (nd * (cf{1.f, 0.f} - mul_if(kappa * r)) * g * (ir * ir)) * ta;
     }
