@@ -37,6 +37,13 @@ sys.path.insert(0, ROOT)
 KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
 METRIC = "complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, N=1e5)"
 WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
+SEP, DIM, DLP = 1, 2, True
+# --workload helm3d: the 3D Helmholtz surface configuration (a second bench line,
+# not the headline)
+W3D = dict(KAPPA=10.0, EPS=1e-6, LEAF=64, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
+           METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Helmholtz SLP, k=10, N=1e6)",
+           WORKLOAD="3D Helmholtz SLP k=10, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
+                    "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, leaf 64, separation k=2")
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
 
 
@@ -127,7 +134,7 @@ def run_gpu(args):
     import torch
 
     import paper_2509_05458_gb300 as cf
-    from cfmm_inputs import config2, densities
+    from cfmm_inputs import config2, config3, densities
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -135,25 +142,26 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    g = config2(N_POINTS, seed=0)
-    dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2)
+    g = config2(N_POINTS, seed=0) if DIM == 2 else config3(N_POINTS, seed=0)
+    dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2 if DLP else 1)
     re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
-    nre, nim = torch.from_numpy(g.nrm_re).to(dev), torch.from_numpy(g.nrm_im).to(dev)
+    nre = torch.from_numpy(g.nrm_re).to(dev) if DLP else None
+    nim = torch.from_numpy(g.nrm_im).to(dev) if DLP else None
     dens = torch.from_numpy(dens_np).to(dev)
     out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
-    kernel = cf.HELMHOLTZ | cf.SLP | cf.DLP
+    kernel = cf.HELMHOLTZ | cf.SLP | (cf.DLP if DLP else 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     # work model of the workload (host bookkeeping, outside the timed regions)
-    wp = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream)
+    wp = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream)
     work = work_model(wp)
     wp.destroy()
 
     def measure(precision, check):
         def step(timing=False):
-            p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream,
+            p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream,
                         precision=precision)
             if timing:
                 p.set_timing(True)
@@ -171,8 +179,8 @@ def run_gpu(args):
             from oracle.direct import direct
             idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
             pts = g.re + 1j * g.im
-            u0 = direct(2, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0], tau=dens_np[0, 1],
-                        nrm=g.nrm_re + 1j * g.nrm_im)
+            u0 = direct(DIM, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0],
+                        tau=dens_np[0, 1] if DLP else None, nrm=(g.nrm_re + 1j * g.nrm_im) if DLP else None)
             u = out.cpu().numpy()[0, idx]
             acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
         clocks = ClockSampler(local)
@@ -197,7 +205,8 @@ def run_gpu(args):
         launches = cf.launch_count() - n0
         ms = _max_over_ranks(statistics.mean(step_ms), ws, dev)
         # apply alone on a resident plan (the GMRES matvec)
-        p = cf.plan(2, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, stream=stream, precision=precision)
+        p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream,
+                    precision=precision)
         for _ in range(3):
             p.apply(dens, out=out)
         torch.cuda.synchronize()
@@ -223,21 +232,22 @@ def run_gpu(args):
         fp64 = measure(cf.FP64, rank == 0 and not args.skip_check)
 
     # end to end through the C ABI with host buffers (copies inside the timed region), MIXED
-    hre, him, hnre, hnim = g.re, g.im, g.nrm_re, g.nrm_im
+    hre, him = g.re, g.im
+    hnre, hnim = (g.nrm_re, g.nrm_im) if DLP else (None, None)
     hd = np.ascontiguousarray(dens_np)
     ho = np.empty((1, g.n), dtype=np.complex128)
     e2e = []
     for i in range(max(3, args.steps) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ph = cf.plan(2, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF, precision=cf.MIXED)
+        ph = cf.plan(DIM, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF, sep=SEP, precision=cf.MIXED)
         ph.apply(hd, out=ho)
         ph.destroy()
         t1 = time.perf_counter()
         if i > 0:
             e2e.append(t1 - t0)
     e2e_s = statistics.median(e2e)
-    h2d = 4 * hre.nbytes + hd.nbytes
+    h2d = (4 if DLP else 2) * hre.nbytes + hd.nbytes
     d2h = ho.nbytes
 
     if rank != 0:
@@ -260,8 +270,9 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
-                   "layers": "SLP+DLP", "precision": "MIXED (near field complex64, translations FP64)",
+        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF, "sep": SEP,
+                   "layers": "SLP+DLP" if DLP else "SLP",
+                   "precision": "MIXED (near field complex64, translations FP64)",
                    "parallelism": f"replicas{ws}",
                    "l2": "flushed (256 MB write) before every timed step",
                    "tree": {k: info[k] for k in ("nlevels", "nboxes", "nleaves", "l0", "p2p_pairs", "m2l_pairs")}},
@@ -302,10 +313,22 @@ def work_model(p):
         npairs = int(cnt[t["level"] == l].sum())
         if npairs:
             pairs_per_level[int(l)] = npairs
-            m2l_flops += npairs * 8 * (2 * int(P[l]) + 1) ** 2
+            m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if DIM == 3 else 8 * (2 * int(P[l]) + 1) ** 2)
     return {"p2p_pairs": int(inf["p2p_pairs"]), "m2l_pairs": int(inf["m2l_pairs"]),
             "m2l_pairs_per_level": pairs_per_level, "orders": [int(x) for x in P],
             "m2l_flops": int(m2l_flops), "p2p_flops_per_pair": P2P_FLOPS_PER_PAIR}
+
+
+def m2l_flops_pair_3d(P):
+    """FP64 flops of one 3D Helmholtz point-and-shoot M2L at order P as the CUDA
+    path computes it: four fixed-rotation products (sum_n n(n+1) real x complex
+    multiply-adds each, 4 flops), the coaxial recurrence (sum_j j^2 rows, three
+    real x complex multiply-adds, 12 flops) and the coaxial product
+    (sum_m (1 + [m > 0]) (P - m + 1)^2 complex multiply-adds, 8 flops)."""
+    rot = 4 * 4 * P * (P + 1) * (P + 2) // 3
+    rec = 12 * P * (P + 1) * (2 * P + 1) // 6
+    app = 8 * sum((1 + (m > 0)) * (P - m + 1) ** 2 for m in range(P + 1))
+    return rot + rec + app
 
 
 def dominant_roofline(name, ms, work, fp64_peak_gflops):
@@ -330,9 +353,28 @@ P2P_FLOPS_PER_PAIR = 0
 
 
 def cpu_baseline(args):
-    """The oracle FMM, as it stands, on a bounded sample of the workload
-    (20,000 points of the same curve family, same k, eps, leaf size), one core."""
+    """The oracle, as it stands, on a bounded sample of the workload, one core:
+    2D, its FMM on 20,000 points of the same curve family (same k, eps, leaf
+    size); 3D, its direct sum for 200 targets against all N sources (the oracle
+    FMM's top level alone takes minutes there)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    if DIM == 3:
+        code = ("import sys,time,json; sys.path.insert(0, %r)\n"
+                "import numpy as np\n"
+                "from cfmm_inputs import config3, densities\n"
+                "from oracle.direct import direct\n"
+                "g = config3(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=1)\n"
+                "pts = g.re + 1j * g.im; idx = np.arange(200)\n"
+                "t=time.perf_counter(); direct(3, 1, %r, pts, pts[idx], sigma=d[0,0]); t=time.perf_counter()-t\n"
+                "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, N_POINTS, KAPPA)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            return {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
+                    "sample": "failed: " + r.stderr.strip()[-200:]}
+        o = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": 200 / o["s"], "unit": "points/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle direct sum (numpy), 200 targets against all {o['n']} sources: {o['s']:.1f} s; "
+                          "points/s = targets evaluated per second"}
     code = ("import sys,time,json; sys.path.insert(0, %r)\n"
             "from cfmm_inputs import config2, densities\n"
             "from oracle import fmm2d\n"
@@ -366,7 +408,8 @@ def run_reference(args):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "n": N_POINTS, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
-                       "layers": "SLP+DLP", "precision": "FP64", "parallelism": "cpu"},
+                       "sep": SEP, "layers": "SLP+DLP" if DLP else "SLP", "precision": "FP64",
+                       "parallelism": "cpu"},
             "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
                              "sample": res["sample"] if res else None},
             "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -384,7 +427,11 @@ def main():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
+    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d"],
+                    help="helm2d: the 2D Helmholtz headline; helm3d: the 3D Helmholtz surface line")
     args = ap.parse_args()
+    if args.workload == "helm3d":
+        globals().update(W3D)
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))
         args.steps = max(1, min(args.steps, 2))

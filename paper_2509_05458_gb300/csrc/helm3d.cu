@@ -559,6 +559,7 @@ struct Tr3hArgs {
     const int* lent;
     const int* parent;
     const int* leaf;
+    const int* qbox;     // owner (destination) box of each List-2 entry
 };
 
 // i^e x for integer e (a permutation of the parts; no arithmetic)
@@ -650,6 +651,54 @@ __device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, c
     }
 }
 
+// Per-shift quantities of a launch, one thread per (destination, source)
+// pair: e = e^{i beta}, e_a = e^{i alpha} and f_l(kappa t), l <= NR. Pair p
+// of the launch is list entry qfirst + p (mode 1), child box qfirst + p
+// (mode 0) or destination box lo + p (mode 2).
+__global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, int NR, int use_h,
+                           cd* __restrict__ sc, cd* __restrict__ fl) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npair) return;
+    int b, s;
+    if (mode == 1) {
+        int q = qfirst + p;
+        s = A.lent[q];
+        b = A.qbox[q];
+    } else if (mode == 0) {
+        s = qfirst + p;
+        b = A.parent[s];
+    } else {
+        b = lo + p;
+        s = A.parent[b];
+    }
+    cd d[3];
+    for (int k = 0; k < 3; ++k) d[k] = cd{A.cre[3 * b + k] - A.cre[3 * s + k], A.cim[3 * b + k] - A.cim[3 * s + k]};
+    cd s2 = d[0] * d[0] + d[1] * d[1];
+    cd t = csqrt_p(s2 + d[2] * d[2]);
+    cd sq = {0, 0}, e = {1, 0};
+    if (!(s2.x == 0.0 && s2.y == 0.0)) {
+        sq = csqrt_p(s2);
+        e = (d[0] + mul_i(d[1])) / sq;
+    }
+    sc[2 * (size_t)p] = e;
+    sc[2 * (size_t)p + 1] = (d[2] + mul_i(sq)) / t;
+    cd* f = fl + (size_t)p * (NR + 1);
+    cd z = A.kappa * t;
+    if (use_h) sph_h_seq(z, NR, f);
+    else sph_j_seq(z, NR, f);
+}
+
+// x^m for m = 0..M by binary exponentiation (one lane per m)
+__device__ __forceinline__ cd cpow_int(cd x, int m) {
+    cd r = {1, 0};
+    while (m) {
+        if (m & 1) r = r * x;
+        x = x * x;
+        m >>= 1;
+    }
+    return r;
+}
+
 // One translation per destination box and source; the destination box's
 // result is accumulated in shared memory and written (mode 0, 1) or added
 // (mode 2) at the end. Shared layout: acc[Ko], a[Km], bb[Km], wb[Km],
@@ -658,7 +707,7 @@ __device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, c
 // in global scratch for large orders), then (when it fits) the Dh table.
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
-                       cd* __restrict__ part) {
+                       cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl) {
     extern __shared__ cd sm[];
     int b = lo + blockIdx.x;
     if (mode == 0 && A.leaf[b]) return;    // a leaf keeps its P2M expansion
@@ -716,38 +765,30 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         __syncthreads();
         // shift d = c_new - c_old: M2M new = parent b, old = child s; M2L new =
         // target b, old = source s; L2L new = child b, old = parent s
-        cd d[3];
-        for (int k = 0; k < 3; ++k) d[k] = cd{A.cre[3 * b + k] - A.cre[3 * s + k], A.cim[3 * b + k] - A.cim[3 * s + k]};
-        cd s2 = d[0] * d[0] + d[1] * d[1];
-        cd t = csqrt_p(s2 + d[2] * d[2]);
+        // this pair's index in the launch's prologue arrays
+        int p = mode == 1 ? q - qfirst : mode == 0 ? q - qfirst : b - lo;
         const cd* src = in + (int64_t)rhs * A.ncoef + A.eoff[s];
         for (int k = threadIdx.x; k < Ki; k += blockDim.x) a[k] = src[k];
-        if (threadIdx.x == 0) {
-            // powers of e = e^{i beta}, e_a = e^{i alpha} and their inverses, m in [-Pm, Pm]
-            cd sq = {0, 0}, e = {1, 0};
-            if (!(s2.x == 0.0 && s2.y == 0.0)) {
-                sq = csqrt_p(s2);
-                e = (d[0] + mul_i(d[1])) / sq;
+        for (int l = threadIdx.x; l <= NR; l += blockDim.x) f[l] = fl[(size_t)p * (NR + 1) + l];
+        {
+            // powers of e, e_a and of their inverses, m in [-Pm, Pm]: warp w < 4
+            // takes one of the four sequences, a lane per |m|
+            int w4 = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            if (w4 < 4) {
+                cd x = sc[2 * (size_t)p + (w4 >> 1)];
+                if (w4 & 1) x = cinv(x);
+                cd* dst = (w4 >> 1) ? pwa : pwe;
+                for (int m = ln; m <= Pm; m += 32) {
+                    cd v = cpow_int(x, m);
+                    dst[Pm + ((w4 & 1) ? -m : m)] = v;
+                }
             }
-            cd ea = (d[2] + mul_i(sq)) / t;
-            cd ie = cinv(e), iea = cinv(ea);
-            pwe[Pm] = pwa[Pm] = pwai[Pm] = pwei[Pm] = cd{1, 0};
-            for (int m = 1; m <= Pm; ++m) {
-                pwe[Pm + m] = pwe[Pm + m - 1] * e;
-                pwe[Pm - m] = pwe[Pm - m + 1] * ie;
-                pwa[Pm + m] = pwa[Pm + m - 1] * ea;
-                pwa[Pm - m] = pwa[Pm - m + 1] * iea;
-            }
-            for (int m = -Pm; m <= Pm; ++m) {
-                pwai[Pm + m] = pwa[Pm - m];
-                pwei[Pm + m] = pwe[Pm - m];
-            }
-        } else if (threadIdx.x == 32) {
-            cd z = A.kappa * t;
-            if (use_h) sph_h_seq(z, NR, f);
-            else sph_j_seq(z, NR, f);
         }
         __syncthreads();
+        for (int m = threadIdx.x - Pm; m <= Pm; m += blockDim.x) {
+            pwai[Pm + m] = pwa[Pm - m];
+            pwei[Pm + m] = pwe[Pm - m];
+        }
         // (1) forward rotation: x = Phi E(e) c; y = D x; x' = S E(e_a) y; u = D x'; c~ = i^m u
         w_pass(A.knm, a, wb, Pi, 1, 0, pwe, Pm);
         __syncthreads();
@@ -915,6 +956,15 @@ struct Helm3dState {
     DevBuf<cd> gscr;             // coaxial work arrays of large-order translations
     DevBuf<cd> part;             // partial results of chunked M2L launches
     std::vector<int> l2max;      // longest List 2 per level
+    std::vector<int> l2off;      // host copy of the List-2 offsets
+    DevBuf<int> qbox;            // owner box of each List-2 entry
+    DevBuf<cd> pre_sc, pre_fl;   // per-pair prologue of a translation launch
+    std::vector<int> level_off;
+    int lvl_of_lo(int lo) const {
+        for (size_t l = 0; l + 1 < level_off.size(); ++l)
+            if (level_off[l] == lo) return (int)l;
+        return -1;
+    }
 };
 
 static std::mutex g_mu;
@@ -976,6 +1026,7 @@ void helm3d_setup(cfmm_plan_s* P) {
     }
     S->l0 = T.l0;
     S->nlev = T.nlevels;
+    S->level_off = T.level_off;
     S->Plev.resize(T.nlevels);
     for (int l = 0; l < T.nlevels; ++l) S->Plev[l] = nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, P->W / (double)(1 << l));
     P->P = S->Plev;
@@ -1006,6 +1057,15 @@ void helm3d_setup(cfmm_plan_s* P) {
     CFMM_CUDA(cudaStreamSynchronize(st));
     S->l2max.assign(T.nlevels, 0);
     for (int b = 0; b < T.nboxes; ++b) S->l2max[lvl[b]] = std::max(S->l2max[lvl[b]], l2[b + 1] - l2[b]);
+    S->l2off = l2;
+    {
+        std::vector<int> qb(std::max(1, l2[T.nboxes]));
+        for (int b = 0; b < T.nboxes; ++b)
+            for (int q = l2[b]; q < l2[b + 1]; ++q) qb[q] = b;
+        S->qbox.alloc(qb.size());
+        CFMM_CUDA(cudaMemcpyAsync(S->qbox.get(), qb.data(), sizeof(int) * qb.size(), cudaMemcpyHostToDevice, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+    }
     for (int b : T.leaf_boxes)
         if (lvl[b] >= S->l0) S->leaves_l0.push_back(b);
     S->d_leaves_l0.alloc(S->leaves_l0.size());
@@ -1086,7 +1146,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     Tr3hArgs TA{T.cen_re.get(), T.cen_im.get(), S->exp_off.get(), S->ncoef, TB->Dh.get(), TB->Dhoff.get(),
                 TB->inv2n1.get(), TB->al.get(), TB->be.get(), TB->ibe.get(), TB->mu.get(), TB->nu.get(),
                 TB->knm.get(), P->kappa, T.cbeg.get(), T.cend.get(),
-                T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get()};
+                T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get(), S->qbox.get()};
     auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk) {
         if (nb <= 0) return;
         size_t smem = tr3h_smem(Pi, Po, true);
@@ -1109,7 +1169,29 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             S->part.alloc(Ko * nb * nrhs * nchunk);
             pp = S->part.get();
         }
-        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, kM2LChunk3, pp);
+        // per-pair prologue (shift, rotation scalars, radial sequence)
+        int qfirst, npair;
+        if (mode == 1) {
+            qfirst = S->l2off[lo];
+            npair = S->l2off[lo + nb] - qfirst;
+        } else if (mode == 0) {
+            int l = S->lvl_of_lo(lo);
+            qfirst = T.level_off[l + 1];
+            npair = T.level_off[l + 2] - qfirst;
+        } else {
+            qfirst = lo;
+            npair = nb;
+        }
+        int NR = Pi + Po;
+        S->pre_sc.alloc((size_t)2 * std::max(npair, 1));
+        S->pre_fl.alloc((size_t)(NR + 1) * std::max(npair, 1));
+        if (npair > 0) {
+            k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, NR, use_h, S->pre_sc.get(),
+                                                           S->pre_fl.get());
+            CFMM_LAUNCHED();
+        }
+        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, kM2LChunk3, pp,
+                                            qfirst, S->pre_sc.get(), S->pre_fl.get());
         CFMM_LAUNCHED();
         if (nchunk > 1) {
             k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,

@@ -524,9 +524,117 @@ static int leaf_maxlevel(LeafArrays& L, cudaStream_t st) {
     return h;
 }
 
-static void refine(LeafArrays& L, const uint64_t* keys, int dim, int B, int Ns, int force, cudaStream_t st) {
-    while (split_pass(L, keys, dim, B, Ns, force, nullptr, st)) {
+// Leaves in one pass. Repeated splitting (split while a box holds more than Ns
+// points or lies above level `force`) puts point i in the box of level
+//   l_i = max(min{l : count of the level-l box containing i <= Ns}, force),
+// capped at B, since the counts of the boxes containing i do not increase with
+// the level; the leaves are the runs of equal (l_i, prefix) in key order, in
+// the same (Morton) order as the splitting produces them. base_lev, when
+// given, is a per-point lower bound (the level of the point's current leaf).
+__global__ void k_pt_level(int64_t n, const uint64_t* __restrict__ keys, int dim, int B, int Ns, int force,
+                           const int* __restrict__ base_lev, int* __restrict__ lev) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = keys[i];
+    auto count = [&](int l) -> int64_t {
+        int sh = dim * (B - l);
+        uint64_t p = sh >= 64 ? 0 : (k >> sh);
+        uint64_t ks = sh >= 64 ? 0 : (p << sh);
+        // first index with key >= ks, first index with key >> sh > p
+        int64_t lo = 0, hi = i;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < ks) lo = mid + 1;
+            else hi = mid;
+        }
+        int64_t a = lo;
+        lo = i + 1;
+        hi = n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (sh < 64 && (keys[mid] >> sh) <= p) lo = mid + 1;
+            else if (sh >= 64) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo - a;
+    };
+    int l;
+    if (base_lev) {
+        l = base_lev[i];
+    } else {
+        // smallest l in [0, B] with count(l) <= Ns (count(B) may still exceed Ns)
+        int lo = 0, hi = B;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (count(mid) <= Ns) hi = mid;
+            else lo = mid + 1;
+        }
+        l = lo;
     }
+    if (l < force) l = force < B ? force : B;
+    lev[i] = l;
+}
+
+__global__ void k_pt_from_leaves(int nl, const int* __restrict__ lev, const int* __restrict__ st,
+                                 const int* __restrict__ en, int* __restrict__ plev) {
+    int j = blockIdx.x;
+    for (int i = st[j] + threadIdx.x; i < en[j]; i += blockDim.x) plev[i] = lev[j];
+}
+
+__global__ void k_leaf_starts(int64_t n, const uint64_t* __restrict__ keys, int dim, int B,
+                              const int* __restrict__ plev, int* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = 1;
+    if (i > 0) {
+        int l = plev[i], lp = plev[i - 1];
+        int sh = dim * (B - l);
+        f = !(l == lp && (sh >= 64 || (keys[i] >> sh) == (keys[i - 1] >> sh)));
+    }
+    flag[i] = f;
+}
+
+__global__ void k_leaf_from_pts(int64_t n, const uint64_t* __restrict__ keys, int dim, int B,
+                                const int* __restrict__ plev, const int* __restrict__ flag,
+                                const int* __restrict__ off, int nl, int* __restrict__ lev,
+                                uint64_t* __restrict__ pre, int* __restrict__ st, int* __restrict__ en) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    int j = off[i];
+    int l = plev[i];
+    int sh = dim * (B - l);
+    lev[j] = l;
+    pre[j] = sh >= 64 ? 0 : (keys[i] >> sh);
+    st[j] = (int)i;
+    if (j > 0) en[j - 1] = (int)i;
+    if (j == nl - 1) en[j] = (int)n;
+}
+
+// leaves of the whole point set (first call: base = null) or of the current
+// leaves refined down to level `force` (base = current leaves)
+static void refine_onepass(LeafArrays& L, const uint64_t* keys, int64_t n, int dim, int B, int Ns, int force,
+                           bool from_current, cudaStream_t st) {
+    Scratch& scr = plan_scratch();
+    int* plev = scr.take_n<int>(n);
+    int* base = nullptr;
+    if (from_current) {
+        base = scr.take_n<int>(n);
+        k_pt_from_leaves<<<L.n, 128, 0, st>>>(L.n, L.lev, L.st, L.en, base);
+        CFMM_LAUNCHED();
+    }
+    k_pt_level<<<blocks_for(n, 256), 256, 0, st>>>(n, keys, dim, B, Ns, force, base, plev);
+    CFMM_LAUNCHED();
+    int* flag = scr.take_n<int>(n);
+    int* off = scr.take_n<int>(n);
+    k_leaf_starts<<<blocks_for(n, 256), 256, 0, st>>>(n, keys, dim, B, plev, flag);
+    CFMM_LAUNCHED();
+    int64_t nl = scan_exclusive(flag, off, (int)n, st);
+    LeafArrays N;
+    N.take((int)nl);
+    k_leaf_from_pts<<<blocks_for(n, 256), 256, 0, st>>>(n, keys, dim, B, plev, flag, off, (int)nl, N.lev, N.pre,
+                                                       N.st, N.en);
+    CFMM_LAUNCHED();
+    L = N;
 }
 
 static void balance(LeafArrays& L, const uint64_t* keys, int dim, int B, int k, cudaStream_t st) {
@@ -1107,7 +1215,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         CFMM_CUDA(cudaStreamSynchronize(st));
     }
     int Ns = P->leaf_size;
-    refine(L, P->keys.get(), dim, B, Ns, 0, st);
+    refine_onepass(L, P->keys.get(), n, dim, B, Ns, 0, false, st);
     pt.mark("refine");
     balance(L, P->keys.get(), dim, B, P->sep, st);
     pt.mark("balance");
@@ -1136,7 +1244,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
             }
         }
         if (l0 > 1) {
-            refine(L, P->keys.get(), dim, B, Ns, l0, st);
+            refine_onepass(L, P->keys.get(), n, dim, B, Ns, l0, true, st);
             balance(L, P->keys.get(), dim, B, P->sep, st);
             build_boxes(P, L, st);
             box_stats(P, st, nullptr);
