@@ -16,11 +16,11 @@
 //   M2L  L_k^l = (-1)^{k+l} sum M_n^m T_{n+k}^{m-l}(c_t - c_s)
 //   L2L  L'_k^l = sum L_n^m U_{n-k}^{m-l}(c' - c)
 //   P2L  L_k^l = sum s (-1)^l T_k^{-l}(y - c)          L2P  u = sum L_k^l U_k^l(x - c)
+// The translations run as point-and-shoot (rotate the shift onto the z-axis,
+// translate along it, rotate back; O(P^3)), in helm3d.cu's k_tr3l.
 // Double layer: n.grad = nu+ d+ + nu- d- + n3 dz (nu+- = n1 +- i n2),
 //   d+ U_n^m = -U_{n-1}^{m-1}/2, d- U_n^m = U_{n-1}^{m+1}/2, dz U_n^m = U_{n-1}^m,
 //   d+ T_n^m = -T_{n+1}^{m-1}/2, d- T_n^m = T_{n+1}^{m+1}/2, dz T_n^m = -T_{n+1}^m.
-// Translations are the direct O(P^4) sums (the paper's point-and-shoot
-// rotations are not used).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -194,152 +194,6 @@ __global__ void k_point_to_exp3(Exp3Args A, const int* __restrict__ boxes, const
     }
 }
 
-struct Trans3Args {
-    const int* blevel;
-    const int* parent;
-    const int* cbeg;
-    const int* cend;
-    const double* cre;
-    const double* cim;
-    const int* Plev;
-    const int64_t* eoff;
-    int64_t ncoef;
-};
-
-__device__ __forceinline__ void nm_of(int c, int& n, int& m) {
-    n = (int)sqrt((double)c);
-    while (n * n > c) --n;
-    while ((n + 1) * (n + 1) <= c) ++n;
-    m = c - n * n - n;
-}
-
-// M2M: parent b gathers its children (children one level finer)
-__global__ void k_m2m3(Trans3Args T, int lo, const int* __restrict__ leaf, cd* __restrict__ mp) {
-    extern __shared__ cd sm[];
-    int b = lo + blockIdx.x;
-    if (leaf[b]) return;
-    int rhs = blockIdx.y;
-    int Pp = T.Plev[T.blevel[b]], Pc = T.Plev[T.blevel[b] + 1];
-    int ncp = (Pp + 1) * (Pp + 1), ncc = (Pc + 1) * (Pc + 1);
-    cd* acc = sm;
-    cd* src = acc + ncp;
-    cd* tab = src + ncc;
-    for (int c = threadIdx.x; c < ncp; c += blockDim.x) acc[c] = cd{0, 0};
-    for (int ch = T.cbeg[b]; ch < T.cend[b]; ++ch) {
-        __syncthreads();
-        const cd* m = mp + (int64_t)rhs * T.ncoef + T.eoff[ch];
-        for (int c = threadIdx.x; c < ncc; c += blockDim.x) src[c] = m[c];
-        cd a[3];
-        for (int d = 0; d < 3; ++d)
-            a[d] = cd{T.cre[3 * ch + d] - T.cre[3 * b + d], T.cim[3 * ch + d] - T.cim[3 * b + d]};
-        for (int col = threadIdx.x; col < 2 * Pp + 1; col += blockDim.x)
-            solid_table(true, a[0], a[1], a[2], Pp, tab, col, 2 * Pp + 1);
-        __syncthreads();
-        for (int c = threadIdx.x; c < ncp; c += blockDim.x) {
-            int n, mm;
-            nm_of(c, n, mm);
-            cd v = acc[c];
-            for (int k = 0; k <= n; ++k) {
-                int nk = n - k;
-                if (nk > Pc) continue;
-                for (int l = -k; l <= k; ++l) {
-                    int ml = mm + l;
-                    if (ml > nk || -ml > nk) continue;
-                    cd t = tab[nm_idx(k, l)] * src[nm_idx(nk, ml)];
-                    v += (l & 1) ? -t : t;
-                }
-            }
-            acc[c] = v;
-        }
-    }
-    __syncthreads();
-    cd* o = mp + (int64_t)rhs * T.ncoef + T.eoff[b];
-    for (int c = threadIdx.x; c < ncp; c += blockDim.x) o[c] = acc[c];
-}
-
-// L2L: child b receives its parent's local expansion
-__global__ void k_l2l3(Trans3Args T, int lo, cd* __restrict__ loc) {
-    extern __shared__ cd sm[];
-    int b = lo + blockIdx.x;
-    int rhs = blockIdx.y;
-    int p = T.parent[b];
-    int Pc = T.Plev[T.blevel[b]], Pp = T.Plev[T.blevel[p]];
-    int ncp = (Pp + 1) * (Pp + 1), ncc = (Pc + 1) * (Pc + 1);
-    cd* src = sm;
-    cd* tab = src + ncp;
-    const cd* lp = loc + (int64_t)rhs * T.ncoef + T.eoff[p];
-    for (int c = threadIdx.x; c < ncp; c += blockDim.x) src[c] = lp[c];
-    cd a[3];
-    for (int d = 0; d < 3; ++d) a[d] = cd{T.cre[3 * b + d] - T.cre[3 * p + d], T.cim[3 * b + d] - T.cim[3 * p + d]};
-    for (int col = threadIdx.x; col < 2 * Pp + 1; col += blockDim.x)
-        solid_table(true, a[0], a[1], a[2], Pp, tab, col, 2 * Pp + 1);
-    __syncthreads();
-    cd* o = loc + (int64_t)rhs * T.ncoef + T.eoff[b];
-    for (int c = threadIdx.x; c < ncc; c += blockDim.x) {
-        int k, l;
-        nm_of(c, k, l);
-        cd v = {0, 0};
-        for (int n = k; n <= Pp; ++n)
-            for (int mm = -n; mm <= n; ++mm) {
-                int d = mm - l;
-                if (d > n - k || -d > n - k) continue;
-                v += src[nm_idx(n, mm)] * tab[nm_idx(n - k, d)];
-            }
-        o[c] += v;
-    }
-}
-
-struct M2L3Args {
-    const int* blevel;
-    const double* cre;
-    const double* cim;
-    const int* Plev;
-    const int64_t* eoff;
-    int64_t ncoef;
-    const int* loff;
-    const int* lent;
-};
-
-// M2L over List 2: per target box, per source, the T table of c_t - c_s up to
-// order 2P, then L_k^l += (-1)^{k+l} sum_{n,m} M_n^m T_{n+k}^{m-l}
-__global__ void k_m2l3(M2L3Args A, int first_box, const cd* __restrict__ mp, cd* __restrict__ loc) {
-    extern __shared__ cd sm[];
-    int b = first_box + blockIdx.x;
-    int rhs = blockIdx.y;
-    int P = A.Plev[A.blevel[b]];
-    int nc = (P + 1) * (P + 1);
-    int P2 = 2 * P;
-    cd* acc = sm;
-    cd* src = acc + nc;
-    cd* tab = src + nc;                        // (2P+1)^2
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) acc[c] = cd{0, 0};
-    for (int q = A.loff[b]; q < A.loff[b + 1]; ++q) {
-        int s = A.lent[q];
-        __syncthreads();
-        const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
-        for (int c = threadIdx.x; c < nc; c += blockDim.x) src[c] = m[c];
-        cd x0[3];
-        for (int d = 0; d < 3; ++d) x0[d] = cd{A.cre[3 * b + d] - A.cre[3 * s + d], A.cim[3 * b + d] - A.cim[3 * s + d]};
-        for (int col = threadIdx.x; col < 2 * P2 + 1; col += blockDim.x)
-            solid_table(false, x0[0], x0[1], x0[2], P2, tab, col, 2 * P2 + 1);
-        __syncthreads();
-        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-            int k, l;
-            nm_of(c, k, l);
-            cd v = {0, 0};
-            for (int n = 0; n <= P; ++n) {
-                const cd* t = tab + nm_idx(n + k, 0) - l;   // T_{n+k}^{mm - l} = t[mm]
-                const cd* ms = src + nm_idx(n, 0);
-                for (int mm = -n; mm <= n; ++mm) v += ms[mm] * t[mm];
-            }
-            acc[c] += ((k + l) & 1) ? -v : v;
-        }
-    }
-    __syncthreads();
-    cd* o = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) o[c] = acc[c];
-}
-
 // M2P over List 3 and L2P: one thread per target; harmonics column by column
 // in registers (no table)
 __device__ cd eval_series(bool reg, cd a0, cd a1, cd a2, int P, const cd* coef) {
@@ -433,6 +287,8 @@ struct Fmm3dState {
     DevBuf<int> d_leaves_l0;
     int n_p2l = 0;
     DevBuf<int> d_p2l_boxes;
+    Lap3Tr* tr = nullptr;
+    ~Fmm3dState() { lap3_tr_destroy(tr); }
 };
 
 static std::mutex g_mu3;
@@ -487,7 +343,7 @@ void fmm3d_setup(cfmm_plan_s* P) {
     // translations are not (unless the tree is a single leaf)
     if (T.nboxes <= 1 || P->kernel != CFMM_LAPLACE) return;
     int maxP = S->Plev[0];
-    CFMM_REQUIRE(maxP <= 40, CFMM_EUNSUPPORTED, "3D Laplace: expansion order above 40 (eps too small)");
+    CFMM_REQUIRE(maxP <= 63, CFMM_EUNSUPPORTED, "3D Laplace: expansion order above 63 (eps too small)");
     S->maxP = maxP;
     S->dPlev.alloc(T.nlevels);
     CFMM_CUDA(cudaMemcpyAsync(S->dPlev.get(), S->Plev.data(), sizeof(int) * T.nlevels, cudaMemcpyHostToDevice, st));
@@ -519,9 +375,9 @@ void fmm3d_setup(cfmm_plan_s* P) {
         CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
-    for (auto f : {(const void*)k_point_to_exp3, (const void*)k_m2m3, (const void*)k_l2l3, (const void*)k_m2l3,
-                   (const void*)k_eval3})
+    for (auto f : {(const void*)k_point_to_exp3, (const void*)k_eval3})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax3Smem));
+    S->tr = lap3_tr_create(P, maxP);
 }
 
 void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
@@ -570,27 +426,14 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
         }
     }
     rec(2);
-    Trans3Args TA{T.level.get(), T.parent.get(), T.cbeg.get(), T.cend.get(), T.cen_re.get(), T.cen_im.get(),
-                  S->dPlev.get(), S->exp_off.get(), S->ncoef};
-    size_t nc = (size_t)(maxP + 1) * (maxP + 1);
+    int Pu = S->Plev[0];
     // (2) M2M
-    for (int l = T.nlevels - 2; l >= S->l0; --l) {
-        int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        dim3 g(nb, nrhs);
-        k_m2m3<<<g, kExp3Threads, sizeof(cd) * 3 * nc, st>>>(TA, lo, T.leaf.get(), mp);
-        CFMM_LAUNCHED();
-    }
+    for (int l = T.nlevels - 2; l >= S->l0; --l)
+        lap3_tr_launch(S->tr, P, 0, l, Pu, S->exp_off.get(), S->ncoef, mp, mp, nrhs);
     rec(3);
     // (4) M2L
-    {
-        M2L3Args MA{T.level.get(), T.cen_re.get(), T.cen_im.get(), S->dPlev.get(), S->exp_off.get(), S->ncoef,
-                    T.loff[1].get(), T.lent[1].get()};
-        int first = T.level_off[S->l0], nb = T.nboxes - first;
-        size_t smem = sizeof(cd) * (2 * nc + (size_t)(2 * maxP + 1) * (2 * maxP + 1));
-        dim3 g(nb, nrhs);
-        k_m2l3<<<g, kExp3Threads, smem, st>>>(MA, first, mp, lc);
-        CFMM_LAUNCHED();
-    }
+    for (int l = S->l0; l < T.nlevels; ++l)
+        lap3_tr_launch(S->tr, P, 1, l, Pu, S->exp_off.get(), S->ncoef, mp, lc, nrhs);
     rec(4);
     // (6) P2L
     if (S->n_p2l > 0) {
@@ -603,12 +446,8 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     }
     rec(5);
     // (7) L2L
-    for (int l = S->l0 + 1; l < T.nlevels; ++l) {
-        int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        dim3 g(nb, nrhs);
-        k_l2l3<<<g, kExp3Threads, sizeof(cd) * 2 * nc, st>>>(TA, lo, lc);
-        CFMM_LAUNCHED();
-    }
+    for (int l = S->l0 + 1; l < T.nlevels; ++l)
+        lap3_tr_launch(S->tr, P, 2, l, Pu, S->exp_off.get(), S->ncoef, lc, lc, nrhs);
     rec(6);
     // (3) P2P
     launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
@@ -617,7 +456,7 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     // (5) M2P, (8) L2P
     {
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
-        k_eval3<<<g, kExp3Threads, sizeof(cd) * nc, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
+        k_eval3<<<g, kExp3Threads, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
                                                           mp, lc, u, maxP);
         CFMM_LAUNCHED();
     }

@@ -82,6 +82,8 @@ struct H3Tables {
     DevBuf<double> g3, gp, gm;           // gradient coefficients c3, s+ c+, s- c- by nmi(n, m), all m
     DevBuf<double> dg, s21;  // sqrt((2m-1)/(2m)), sqrt(2m+1), m <= Pmax+1
     DevBuf<int> knm;         // k -> n * 256 + (m + 128), k < (Pmax+1)^2
+    DevBuf<double> lsm, lsd; // eps_m s_n^m and eps_m / s_n^m, s = sqrt((n-|m|)! (n+|m|)!)
+    DevBuf<double> fact, ifact;  // j! and 1/j!, j <= 2 Pmax + 2
 };
 
 // Tables only grow: a larger order builds a new set and the older sets stay
@@ -251,6 +253,24 @@ static H3Tables* tables(int P) {
     up(T->gm, gm);
     up(T->dg, dg);
     up(T->s21, s21);
+    {
+        std::vector<double> f(2 * Pm + 3), fi(2 * Pm + 3), lm(knm.size()), ld(knm.size());
+        f[0] = 1.0;
+        for (int j = 1; j < (int)f.size(); ++j) f[j] = f[j - 1] * j;
+        for (size_t j = 0; j < f.size(); ++j) fi[j] = 1.0 / f[j];
+        for (int n = 0; n <= Pm; ++n)
+            for (int m = -n; m <= n; ++m) {
+                int am = std::abs(m);
+                double sv = std::sqrt(f[n - am] * f[n + am]);
+                double e = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+                lm[nmi(n, m)] = e * sv;
+                ld[nmi(n, m)] = e / sv;
+            }
+        up(T->fact, f);
+        up(T->ifact, fi);
+        up(T->lsm, lm);
+        up(T->lsd, ld);
+    }
     T->knm.alloc(knm.size());
     CFMM_CUDA(cudaMemcpy(T->knm.get(), knm.data(), sizeof(int) * knm.size(), cudaMemcpyHostToDevice));
 
@@ -682,6 +702,10 @@ __global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, 
     }
     sc[2 * (size_t)p] = e;
     sc[2 * (size_t)p + 1] = (d[2] + mul_i(sq)) / t;
+    if (NR < 0) {                      // Laplace: only t
+        fl[p] = t;
+        return;
+    }
     cd* f = fl + (size_t)p * (NR + 1);
     cd z = A.kappa * t;
     if (use_h) sph_h_seq(z, NR, f);
@@ -907,6 +931,128 @@ __global__ void k_tr3h_reduce(const cd* __restrict__ part, int nchunk, int nb, i
         cd s = {0, 0};
         for (int z = 0; z < nchunk; ++z) s += part[(((size_t)z * nr + rhs) * nb + bi) * Ko + k];
         o[k] = s;
+    }
+}
+
+// 3D Laplace translations by the same point-and-shoot scheme (Sec. 5.2,
+// Lemma 5.2.4's z-axis forms written for the solid harmonics of fmm3d.cu):
+// with U_n^m = Z_n^m / (eps_m s_n^m), T_n^m = eps_m s_n^m Y_n^m / rho^{n+1},
+// s_n^m = sqrt((n-|m|)! (n+|m|)!), the Y-basis coefficients of a multipole
+// are eps_m s_n^m M_n^m and of a local expansion eps_m L_n^m / s_n^m; the
+// rotations of the Helmholtz kernel act on them. Along the z-axis (new centre
+// at (0, 0, t) from the old, U_k^0(0,0,z) = z^k/k!, T_j^0(0,0,t) = j!/t^{j+1}):
+//   M2M  M'_n^m = sum_k ((-t)^k / k!) M_{n-k}^m
+//   M2L  L_k^m  = (-1)^{k+m} sum_n M_n^m (n+k)! / t^{n+k+1}
+//   L2L  L'_k^m = sum_{n >= k} L_n^m t^{n-k} / (n-k)!
+__global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const double* __restrict__ lsm,
+                       const double* __restrict__ lsd, const double* __restrict__ fact,
+                       const double* __restrict__ ifact, const cd* __restrict__ in, cd* __restrict__ out,
+                       int qfirst, const cd* __restrict__ sc, const cd* __restrict__ tt) {
+    extern __shared__ cd sm[];
+    int b = lo + blockIdx.x;
+    if (mode == 0 && A.leaf[b]) return;
+    int rhs = blockIdx.y;
+    int K = (P + 1) * (P + 1);
+    cd* acc = sm;
+    cd* a = acc + K;
+    cd* bb = a + K;
+    cd* wb = bb + K;
+    cd* g = wb + K;                     // 2P + 2
+    cd* pwe = g + (2 * P + 2);
+    cd* pwa = pwe + (2 * P + 1);
+    cd* pwai = pwa + (2 * P + 1);
+    cd* pwei = pwai + (2 * P + 1);
+    double* Dsm = (double*)(pwei + (2 * P + 1));
+    const double* Dh = A.Dh;
+    if (d_in_smem) {
+        int64_t nd = __ldg(A.Dhoff + P + 1);
+        for (int64_t k = threadIdx.x; k < nd; k += blockDim.x) Dsm[k] = A.Dh[k];
+        Dh = Dsm;
+    }
+    bool in_local = mode == 2, out_local = mode != 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) acc[k] = cd{0, 0};
+    int qa, qb;
+    if (mode == 0) {
+        qa = A.cbeg[b];
+        qb = A.cend[b];
+    } else if (mode == 1) {
+        qa = A.loff[b];
+        qb = A.loff[b + 1];
+    } else {
+        qa = 0;
+        qb = 1;
+    }
+    for (int q = qa; q < qb; ++q) {
+        int s = mode == 0 ? q : mode == 1 ? A.lent[q] : A.parent[b];
+        int p = mode == 2 ? b - lo : q - qfirst;
+        __syncthreads();
+        const cd* src = in + (int64_t)rhs * A.ncoef + A.eoff[s];
+        // Y-basis input
+        for (int k = threadIdx.x; k < K; k += blockDim.x) a[k] = (in_local ? __ldg(lsd + k) : __ldg(lsm + k)) * src[k];
+        cd t = tt[p];
+        int w4 = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        if (w4 < 4) {
+            cd x = sc[2 * (size_t)p + (w4 >> 1)];
+            if (w4 & 1) x = cinv(x);
+            cd* dst = (w4 >> 1) ? pwa : pwe;
+            for (int m = ln; m <= P; m += 32) dst[P + ((w4 & 1) ? -m : m)] = cpow_int(x, m);
+        } else if (w4 == 4) {
+            // coaxial factors g[j], j <= 2P+1
+            cd base = mode == 0 ? -t : mode == 1 ? cinv(t) : t;
+            for (int j = ln; j <= 2 * P + 1; j += 32) {
+                cd v = cpow_int(base, mode == 1 ? j + 1 : j);
+                g[j] = (mode == 1 ? __ldg(fact + j) : __ldg(ifact + j)) * v;
+            }
+        }
+        __syncthreads();
+        for (int m = threadIdx.x - P; m <= P; m += blockDim.x) {
+            pwai[P + m] = pwa[P - m];
+            pwei[P + m] = pwe[P - m];
+        }
+        // forward rotation
+        w_pass(A.knm, a, wb, P, 1, 0, pwe, P);
+        __syncthreads();
+        d_pass(Dh, A.Dhoff, wb, bb, P, 0, 0, nullptr, P, 0);
+        __syncthreads();
+        w_pass(A.knm, bb, wb, P, 0, 1, pwa, P);
+        __syncthreads();
+        d_pass(Dh, A.Dhoff, wb, a, P, 1, 0, nullptr, P, 0);
+        __syncthreads();
+        // back to the solid-harmonic basis, z-axis translation, to the Y basis
+        for (int k = threadIdx.x; k < K; k += blockDim.x) a[k] = (in_local ? __ldg(lsm + k) : __ldg(lsd + k)) * a[k];
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            int n, m;
+            nm_tab(A.knm, k, n, m);
+            int am = m < 0 ? -m : m;
+            cd v = {0, 0};
+            if (mode == 0) {
+                for (int kk = 0; kk <= n - am; ++kk) v += g[kk] * a[nmi(n - kk, m)];
+            } else if (mode == 1) {
+                for (int nn = am; nn <= P; ++nn) v += g[nn + n] * a[nmi(nn, m)];
+                if ((n + m) & 1) v = -v;
+            } else {
+                for (int nn = n; nn <= P; ++nn) v += g[nn - n] * a[nmi(nn, m)];
+            }
+            bb[k] = (out_local ? __ldg(lsd + k) : __ldg(lsm + k)) * v;
+        }
+        __syncthreads();
+        // back rotation, accumulated in the solid-harmonic basis
+        w_pass(A.knm, bb, wb, P, 1, 0, nullptr, P);
+        __syncthreads();
+        d_pass(Dh, A.Dhoff, wb, a, P, 0, 0, nullptr, P, 0);
+        __syncthreads();
+        w_pass(A.knm, a, wb, P, 0, 1, pwai, P);
+        __syncthreads();
+        d_pass(Dh, A.Dhoff, wb, bb, P, 1, 0, pwei, P, 0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) acc[k] += (out_local ? __ldg(lsm + k) : __ldg(lsd + k)) * bb[k];
+    }
+    __syncthreads();
+    cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (mode == 2) o[k] += acc[k];
+        else o[k] = acc[k];
     }
 }
 
@@ -1244,6 +1390,80 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         CFMM_LAUNCHED();
     }
     rec(8);
+}
+
+// ---------------------------------------------------------------------------
+// 3D Laplace translations through k_tr3l (used by fmm3d.cu)
+// ---------------------------------------------------------------------------
+struct Lap3Tr {
+    H3Tables* tab = nullptr;
+    std::vector<int> l2off, level_off;
+    DevBuf<int> qbox;
+    DevBuf<cd> sc, tt;
+};
+
+Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord) {
+    TreeDev& T = P->tree;
+    cudaStream_t st = P->stream;
+    Lap3Tr* L = new Lap3Tr();
+    L->tab = tables(Pord);
+    L->level_off = T.level_off;
+    L->l2off.resize(T.nboxes + 1);
+    CFMM_CUDA(cudaMemcpyAsync(L->l2off.data(), T.loff[1].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost,
+                              st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> qb(std::max(1, L->l2off[T.nboxes]));
+    for (int b = 0; b < T.nboxes; ++b)
+        for (int q = L->l2off[b]; q < L->l2off[b + 1]; ++q) qb[q] = b;
+    L->qbox.alloc(qb.size());
+    CFMM_CUDA(cudaMemcpyAsync(L->qbox.get(), qb.data(), sizeof(int) * qb.size(), cudaMemcpyHostToDevice, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    CFMM_CUDA(cudaFuncSetAttribute((const void*)k_tr3l, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
+    return L;
+}
+
+void lap3_tr_destroy(Lap3Tr* L) { delete L; }
+
+// mode 0: M2M into the non-leaf boxes of level l from level l+1; 1: M2L at
+// level l (writes L); 2: L2L into level l from level l-1 (adds)
+void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const int64_t* eoff, int64_t ncoef,
+                    const cd* in, cd* out, int nrhs) {
+    TreeDev& T = P->tree;
+    cudaStream_t st = P->stream;
+    int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
+    if (nb <= 0) return;
+    H3Tables* TB = L->tab;
+    Tr3hArgs TA{T.cen_re.get(), T.cen_im.get(), eoff, ncoef, TB->Dh.get(), TB->Dhoff.get(),
+                TB->inv2n1.get(), TB->al.get(), TB->be.get(), TB->ibe.get(), TB->mu.get(), TB->nu.get(),
+                TB->knm.get(), 0.0, T.cbeg.get(), T.cend.get(), T.loff[1].get(), T.lent[1].get(), T.parent.get(),
+                T.leaf.get(), L->qbox.get()};
+    int qfirst, npair;
+    if (mode == 1) {
+        qfirst = L->l2off[lo];
+        npair = L->l2off[lo + nb] - qfirst;
+    } else if (mode == 0) {
+        qfirst = T.level_off[l + 1];
+        npair = T.level_off[l + 2] - qfirst;
+    } else {
+        qfirst = lo;
+        npair = nb;
+    }
+    L->sc.alloc((size_t)2 * std::max(npair, 1));
+    L->tt.alloc((size_t)std::max(npair, 1));
+    if (npair > 0) {
+        k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, -1, 0, L->sc.get(), L->tt.get());
+        CFMM_LAUNCHED();
+    }
+    size_t K = (size_t)(Pord + 1) * (Pord + 1);
+    size_t smem = sizeof(cd) * (4 * K + (2 * Pord + 2) + 4 * (2 * Pord + 1));
+    size_t nd = tr3h_dh(Pord) * sizeof(double);
+    int dsm = smem + nd <= (size_t)kH3Smem;
+    if (dsm) smem += nd;
+    CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Laplace translation exceeds shared memory");
+    dim3 g(nb, nrhs);
+    k_tr3l<<<g, kH3Threads, smem, st>>>(TA, mode, lo, Pord, dsm, TB->lsm.get(), TB->lsd.get(), TB->fact.get(),
+                                        TB->ifact.get(), in, out, qfirst, L->sc.get(), L->tt.get());
+    CFMM_LAUNCHED();
 }
 
 }  // namespace cfmm

@@ -52,6 +52,12 @@ void helm3d_setup(cfmm_plan_s* P);
 void helm3d_release(cfmm_plan_s* P);
 void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 int nterms_helm3d(int k, double eps, double kappa, double w);
+// 3D Laplace point-and-shoot translations (helm3d.cu, used by fmm3d.cu)
+struct Lap3Tr;
+Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord);
+void lap3_tr_destroy(Lap3Tr* L);
+void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const int64_t* eoff, int64_t ncoef,
+                    const cd* in, cd* out, int nrhs);
 
 void upload_lag_rule_p2p();
 void upload_lag_rule_fmm2d();
