@@ -38,12 +38,14 @@ KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
 METRIC = "complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, N=1e5)"
 WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
 SEP, DIM, DLP = 1, 2, True
+LEAF_FP64 = 64
 # --workload helm3d: the 3D Helmholtz surface configuration (a second bench line,
 # not the headline)
-W3D = dict(KAPPA=10.0, EPS=1e-6, LEAF=64, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
+W3D = dict(KAPPA=10.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
            METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Helmholtz SLP, k=10, N=1e6)",
            WORKLOAD="3D Helmholtz SLP k=10, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
-                    "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, leaf 64, separation k=2")
+                    "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / 128 (FP64) "
+                    "as picked by the leaf-size autotuner")
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
 
 
@@ -160,8 +162,10 @@ def run_gpu(args):
     wp.destroy()
 
     def measure(precision, check):
+        leaf = LEAF if precision == cf.MIXED else LEAF_FP64
+
         def step(timing=False):
-            p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream,
+            p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=leaf, sep=SEP, stream=stream,
                         precision=precision)
             if timing:
                 p.set_timing(True)
@@ -205,7 +209,7 @@ def run_gpu(args):
         launches = cf.launch_count() - n0
         ms = _max_over_ranks(statistics.mean(step_ms), ws, dev)
         # apply alone on a resident plan (the GMRES matvec)
-        p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream,
+        p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=leaf, sep=SEP, stream=stream,
                     precision=precision)
         for _ in range(3):
             p.apply(dens, out=out)
@@ -270,7 +274,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF, "sep": SEP,
+        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
+                   "leaf_size_fp64": LEAF_FP64, "sep": SEP,
                    "layers": "SLP+DLP" if DLP else "SLP",
                    "precision": "MIXED (near field complex64, translations FP64)",
                    "parallelism": f"replicas{ws}",

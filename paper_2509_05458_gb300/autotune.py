@@ -21,19 +21,19 @@ from . import plan as make_plan
 _CACHE = {}
 
 
-def _bucket(dim, kernel, precision, n, eps, kappa, width):
-    return (dim, kernel & 0xF, precision, int(round(math.log2(max(n, 1)))),
+def _bucket(dim, kernel, precision, n, eps, kappa, width, sep=1):
+    return (dim, kernel & 0xF, precision, sep, int(round(math.log2(max(n, 1)))),
             int(round(math.log10(eps))), int(round(math.log2(1.0 + kappa * width))))
 
 
 def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=None,
                    precision=0, candidates=(32, 48, 64, 96, 128, 192), reps=3, stream=None,
-                   use_cache=True):
+                   use_cache=True, sep=1):
     """Returns (best_leaf_size, {leaf_size: median apply ms}). Inputs are CUDA tensors."""
     import torch
     n = int(pts_re.shape[0])
     width = float((pts_re.max(0).values - pts_re.min(0).values).max())
-    key = _bucket(dim, kernel, precision, n, eps, kappa, width)
+    key = _bucket(dim, kernel, precision, n, eps, kappa, width, sep)
     if use_cache and key in _CACHE:
         return _CACHE[key]
     dev = pts_re.device
@@ -44,7 +44,7 @@ def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = {}
     for ls in candidates:
-        p = make_plan(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re, nrm_im, leaf_size=ls,
+        p = make_plan(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re, nrm_im, leaf_size=ls, sep=sep,
                       precision=precision, stream=stream)
         out = p.apply(dens)
         ms = []

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 
@@ -43,6 +44,80 @@ void* Scratch::take(size_t bytes) {
     cur_ = chunks_.size() - 1;
     off_ = bytes;
     return p;
+}
+
+// ---- caching device allocator -------------------------------------------
+// Size classes: powers of two from 256 B to 64 MiB, then multiples of 64 MiB.
+// At most kPoolCap bytes are kept per device; beyond that freed blocks go back
+// to the driver. An allocation that fails releases the device's cache and is
+// retried once.
+namespace {
+constexpr size_t kPoolCap = (size_t)8 << 30;
+struct PoolDev {
+    std::map<size_t, std::vector<void*>> free;
+    size_t cached = 0;
+};
+std::mutex g_pool_mu;
+std::map<int, PoolDev>& pool_devs() {
+    static std::map<int, PoolDev> m;
+    return m;
+}
+size_t pool_class(size_t b) {
+    const size_t big = (size_t)64 << 20;
+    if (b > big) return (b + big - 1) / big * big;
+    size_t s = 256;
+    while (s < b) s <<= 1;
+    return s;
+}
+}  // namespace
+
+void* pool_alloc(size_t bytes, int* dev_out) {
+    int dev = 0;
+    CFMM_CUDA(cudaGetDevice(&dev));
+    *dev_out = dev;
+    size_t sz = pool_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        PoolDev& D = pool_devs()[dev];
+        auto it = D.free.find(sz);
+        if (it != D.free.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            D.cached -= sz;
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lk(g_pool_mu);
+            PoolDev& D = pool_devs()[dev];
+            cudaDeviceSynchronize();
+            for (auto& kv : D.free)
+                for (void* q : kv.second) cudaFree(q);
+            D.free.clear();
+            D.cached = 0;
+        }
+        if (cudaMalloc(&p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{CFMM_ENOMEM, "device allocation failed"};
+        }
+    }
+    return p;
+}
+
+void pool_free(void* p, size_t bytes, int dev) {
+    if (!p) return;
+    size_t sz = pool_class(bytes);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    PoolDev& D = pool_devs()[dev];
+    if (D.cached + sz > kPoolCap) {
+        cudaFree(p);
+        return;
+    }
+    D.free[sz].push_back(p);
+    D.cached += sz;
 }
 
 Scratch::~Scratch() {
@@ -250,6 +325,8 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
 
 static void destroy_plan(cfmm_plan_s* P) {
     if (!P) return;
+    // queued work of this plan must finish before its buffers return to the pool
+    cudaStreamSynchronize(P->stream);
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     if (P->graph) cudaGraphDestroy(P->graph);
     fmm2d_release(P);

@@ -93,25 +93,37 @@ struct Error {
         if (!(cond)) throw ::cfmm::Error{status, msg};                               \
     } while (0)
 
-// simple owning device buffer
+// Caching device allocator (api.cu): blocks freed by plans are kept in
+// per-device size classes and handed out again, so plan construction and
+// destruction make no cudaMalloc/cudaFree calls in steady state.
+void* pool_alloc(size_t bytes, int* dev_out);
+void pool_free(void* p, size_t bytes, int dev);
+
+// owning device buffer (memory from the caching allocator). Growing a buffer
+// that may still be read by queued work synchronises the device first, as the
+// cudaFree it replaces did; plans synchronise their stream before they free.
 template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    int dev = 0;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) pool_free(p, (n ? n : 1) * sizeof(T), dev);
         p = nullptr;
         n = 0;
     }
     void alloc(size_t count) {
         if (count <= n && p) return;
-        release();
+        if (p) {
+            cudaDeviceSynchronize();
+            release();
+        }
         size_t bytes = (count ? count : 1) * sizeof(T);
-        CFMM_CUDA(cudaMalloc((void**)&p, bytes));
+        p = (T*)pool_alloc(bytes, &dev);
         n = count;
     }
     T* get() const { return p; }
