@@ -480,6 +480,102 @@ __global__ void k_p2x3h(Exp3hArgs A, const int* __restrict__ boxes, const int* _
     }
 }
 
+// Radial factors f_n(kappa rho)/rho^n, n <= P, of every point of the listed
+// boxes relative to a box centre (one thread per point): the centre is the
+// box itself (P2M, f = j) or, for P2L, the target box of List-4 entry q.
+__global__ void k_radial3h(Exp3hArgs A, const int* __restrict__ boxes, int nboxes, const int* __restrict__ loff,
+                           const int* __restrict__ lent, int sing, int P, const int* __restrict__ roff,
+                           cd* __restrict__ rad) {
+    int bi = blockIdx.x;
+    if (bi >= nboxes) return;
+    int b = boxes[bi];
+    cd cen[3];
+    for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+    int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
+    int64_t o = roff[bi];
+    for (int q = qa; q < qb; ++q) {
+        int src = loff ? lent[q] : b;
+        int s0 = A.bst[src], s1 = A.ben[src];
+        for (int j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
+            cd y[3];
+            load3(A.xr, A.xi, A.n, j, y);
+            for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
+            radial_seq(!sing, A.kappa, y[0] * y[0] + y[1] * y[1] + y[2] * y[2], P,
+                       rad + (o + (j - s0)) * (int64_t)(P + 1));
+        }
+        o += s1 - s0;
+    }
+}
+
+// Single-layer P2M (sing = 0) / P2L (sing = 1) with one warp per source at a
+// time and one lane per harmonic column: lane c of warp w walks the column
+// of Z_n^{mu} (mu = -m for coefficient m) of its source, n = |mu|..P, and adds
+// F[n] Z sigma into the warp's private accumulator row; the warp rows are
+// summed in warp order at the end, so the result does not depend on timing.
+__global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const int* __restrict__ loff,
+                            const int* __restrict__ lent, int sing, const int* __restrict__ roff,
+                            const cd* __restrict__ rad, cd* __restrict__ out) {
+    extern __shared__ cd sm[];
+    int bi = blockIdx.x;
+    int b = boxes[bi];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    int nc = (P + 1) * (P + 1);
+    int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    cd* accw = sm + (size_t)wid * nc;
+    for (int c = lane; c < nc; c += 32) accw[c] = cd{0, 0};
+    cd cen[3];
+    for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+    int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
+    int64_t o = roff[bi];
+    for (int q = qa; q < qb; ++q) {
+        int src = loff ? lent[q] : b;
+        int s0 = A.bst[src], s1 = A.ben[src];
+        for (int j = s0 + wid; j < s1; j += nwarp) {
+            cd y[3];
+            load3(A.xr, A.xi, A.n, j, y);
+            for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
+            cd sg = A.sigma[rhs * A.dstride + j];
+            const cd* F = rad + (o + (j - s0)) * (int64_t)(P + 1);
+            cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
+            cd r2 = xp * xm + z * z;
+            for (int col = lane; col < 2 * P + 1; col += 32) {
+                // column of Z_n^{mu}: mu >= 0 with x+, mu < 0 with x-; it feeds coefficient m = -mu
+                int am = col <= P ? col : col - P;
+                bool neg = col > P;
+                int mu = neg ? -am : am;
+                cd xs = neg ? xm : xp;
+                cd d = sg;
+                for (int i = 1; i <= am; ++i) d = (-__ldg(A.zc.dg + i)) * (xs * d);
+                int m = -mu;
+                accw[nmi(am, m)] += F[am] * d;
+                if (am + 1 > P) continue;
+                cd p2 = d, p1 = __ldg(A.zc.s21 + am) * (z * d);
+                accw[nmi(am + 1, m)] += F[am + 1] * p1;
+                for (int n = am + 2; n <= P; ++n) {
+                    int k = nmi(n, am);
+                    cd cur = __ldg(A.zc.A + k) * (z * p1) - __ldg(A.zc.B + k) * (r2 * p2);
+                    accw[nmi(n, m)] += F[n] * cur;
+                    p2 = p1;
+                    p1 = cur;
+                }
+            }
+        }
+        o += s1 - s0;
+    }
+    __syncthreads();
+    cd* op = out + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        cd v = {0, 0};
+        for (int w = 0; w < nwarp; ++w) v += sm[(size_t)w * nc + c];
+        int n, m;
+        nm_tab(A.zc.knm, c, n, m);
+        v = mul_i(A.kappa * (2.0 * n + 1.0) * v);
+        if (sing) op[c] += v;
+        else op[c] = v;
+    }
+}
+
 // Sum over n, m of coef_n^m F[n] Z_n^m(x) with Z generated column by column.
 __device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const cd* coef) {
     cd xp = a0 + mul_i(a1), xm = a0 - mul_i(a1), z = a2;
@@ -1098,6 +1194,11 @@ struct Helm3dState {
     std::vector<int> p2l_off;    // List-4 targets by level, likewise
     int n_p2l = 0;
     DevBuf<int> d_p2l_boxes;
+    // single-layer P2M / P2L: per listed box, the offset of its source points in
+    // the radial-factor buffer (prefix over the level's boxes)
+    DevBuf<int> d_p2m_roff, d_p2l_roff;
+    std::vector<int64_t> p2m_rtot, p2l_rtot;    // per level: points in the level's launch
+    DevBuf<cd> rad;
     H3Tables* tab = nullptr;
     DevBuf<cd> gscr;             // coaxial work arrays of large-order translations
     DevBuf<cd> part;             // partial results of chunked M2L launches
@@ -1232,12 +1333,46 @@ void helm3d_setup(cfmm_plan_s* P) {
         }
     for (int l = 0; l < T.nlevels; ++l) S->p2l_off[l + 1] += S->p2l_off[l];
     S->n_p2l = (int)boxes.size();
+    {
+        // radial-buffer offsets of the single-layer P2M / P2L launches
+        std::vector<int> hst(T.nboxes), hen(T.nboxes), l4e(std::max(1, l4[T.nboxes]));
+        CFMM_CUDA(cudaMemcpyAsync(hst.data(), T.start.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaMemcpyAsync(hen.data(), T.end.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
+        if (l4[T.nboxes] > 0)
+            CFMM_CUDA(cudaMemcpyAsync(l4e.data(), T.lent[3].get(), sizeof(int) * l4[T.nboxes], cudaMemcpyDeviceToHost,
+                                      st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> ro(byl.size()), rl(boxes.size());
+        S->p2m_rtot.assign(T.nlevels, 0);
+        S->p2l_rtot.assign(T.nlevels, 0);
+        for (int l = 0; l < T.nlevels; ++l) {
+            int64_t acc = 0;
+            for (int i = S->p2m_off[l]; i < S->p2m_off[l + 1]; ++i) {
+                ro[i] = (int)acc;
+                acc += hen[byl[i]] - hst[byl[i]];
+            }
+            S->p2m_rtot[l] = acc;
+            acc = 0;
+            for (int i = S->p2l_off[l]; i < S->p2l_off[l + 1]; ++i) {
+                rl[i] = (int)acc;
+                int b = boxes[i];
+                for (int q = l4[b]; q < l4[b + 1]; ++q) acc += hen[l4e[q]] - hst[l4e[q]];
+            }
+            S->p2l_rtot[l] = acc;
+        }
+        S->d_p2m_roff.alloc(std::max<size_t>(1, ro.size()));
+        S->d_p2l_roff.alloc(std::max<size_t>(1, rl.size()));
+        if (!ro.empty())
+            CFMM_CUDA(cudaMemcpyAsync(S->d_p2m_roff.get(), ro.data(), sizeof(int) * ro.size(), cudaMemcpyHostToDevice, st));
+        if (!rl.empty())
+            CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_roff.get(), rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice, st));
+    }
     S->d_p2l_boxes.alloc(boxes.size());
     if (!boxes.empty())
         CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
-    for (auto f : {(const void*)k_p2x3h, (const void*)k_eval3h, (const void*)k_tr3h})
+    for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp, (const void*)k_eval3h, (const void*)k_tr3h})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
 }
 
@@ -1278,10 +1413,33 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         chunk = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024 / sizeof(cd) - nc) / per));
         return sizeof(cd) * (nc + (size_t)chunk * per);
     };
+    bool slp_only = P->slp && !P->dlp;
+    auto slp_fits = [&](int l) {
+        size_t K = (size_t)(S->Plev[l] + 1) * (S->Plev[l] + 1);
+        return sizeof(cd) * (kH3Threads / 32) * K <= (size_t)kH3Smem;
+    };
+    // single-layer P2M / P2L of one level: radial factors of every source point,
+    // then one warp per source and one lane per harmonic column
+    auto p2x_slp = [&](int l, int sing, const int* boxes, int cnt, const int* roff, int64_t rtot, cd* dst) {
+        int PL = S->Plev[l];
+        S->rad.alloc((size_t)std::max<int64_t>(1, rtot) * (PL + 1));
+        k_radial3h<<<cnt, 128, 0, st>>>(A, boxes, cnt, sing ? T.loff[3].get() : nullptr,
+                                         sing ? T.lent[3].get() : nullptr, sing, PL, roff, S->rad.get());
+        CFMM_LAUNCHED();
+        size_t smem = sizeof(cd) * (size_t)(kH3Threads / 32) * (PL + 1) * (PL + 1);
+        dim3 g((unsigned)cnt, nrhs);
+        k_p2x3h_slp<<<g, kH3Threads, smem, st>>>(A, boxes, sing ? T.loff[3].get() : nullptr,
+                                                 sing ? T.lent[3].get() : nullptr, sing, roff, S->rad.get(), dst);
+        CFMM_LAUNCHED();
+    };
     // (1) P2M, one launch per level (shared memory sized by that level's P)
     for (int l = S->l0; l < T.nlevels; ++l) {
         int cnt = S->p2m_off[l + 1] - S->p2m_off[l];
         if (cnt <= 0) continue;
+        if (slp_only && slp_fits(l)) {
+            p2x_slp(l, 0, S->d_p2m.get() + S->p2m_off[l], cnt, S->d_p2m_roff.get() + S->p2m_off[l], S->p2m_rtot[l], mp);
+            continue;
+        }
         int chunk;
         size_t smem = p2x_smem(S->Plev[l], chunk);
         dim3 g((unsigned)cnt, nrhs);
@@ -1364,6 +1522,11 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     for (int l = S->l0; l < T.nlevels; ++l) {
         int cnt = S->p2l_off[l + 1] - S->p2l_off[l];
         if (cnt <= 0) continue;
+        if (slp_only && slp_fits(l)) {
+            p2x_slp(l, 1, S->d_p2l_boxes.get() + S->p2l_off[l], cnt, S->d_p2l_roff.get() + S->p2l_off[l],
+                    S->p2l_rtot[l], lc);
+            continue;
+        }
         int chunk;
         size_t smem = p2x_smem(S->Plev[l], chunk);
         dim3 g((unsigned)cnt, nrhs);

@@ -637,19 +637,17 @@ static void refine_onepass(LeafArrays& L, const uint64_t* keys, int64_t n, int d
     L = N;
 }
 
+// The deepest leaf level does not change while balancing (only leaves two or
+// more levels coarser than a neighbour are split), so it is read once; a split
+// pass that splits nothing ends the loop.
 static void balance(LeafArrays& L, const uint64_t* keys, int dim, int B, int k, cudaStream_t st) {
     int* any = plan_scratch().take_n<int>(1);
+    int maxl = leaf_maxlevel(L, st);
     for (;;) {
-        int maxl = leaf_maxlevel(L, st);
         int* flag = plan_scratch().take_n<int>(L.n);
-        CFMM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
         k_balance_flags<<<blocks_for(L.n, 128), 128, 0, st>>>(L.n, L.lev, L.pre, dim, B, k, maxl, flag, any);
         CFMM_LAUNCHED();
-        int h = 0;
-        CFMM_CUDA(cudaMemcpyAsync(&h, any, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CFMM_CUDA(cudaStreamSynchronize(st));
-        if (!h) return;
-        split_pass(L, keys, dim, B, 0, 0, flag, st);
+        if (!split_pass(L, keys, dim, B, 0, 0, flag, st)) return;
     }
 }
 
@@ -1091,20 +1089,26 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
     int nb = T.nboxes;
     ListCtx C{nb, T.nlevels, P->dim, P->sep, T.l0, P->B, T.level.get(), T.leaf.get(), T.parent.get(),
               T.prefix.get(), T.d_level_off.get()};
-    int* cnt = plan_scratch().take_n<int>(nb);
+    // counts and scans of the four lists, then one read of the four totals
+    int* cnt = plan_scratch().take_n<int>((size_t)4 * (nb + 1));
     for (int w = 0; w < 4; ++w) {
-        k_list_count<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(C, w, cnt);
+        int* cw = cnt + (size_t)w * (nb + 1);
+        k_list_count<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(C, w, cw);
         CFMM_LAUNCHED();
+        CFMM_CUDA(cudaMemsetAsync(cw + nb, 0, sizeof(int), st));
         T.loff[w].alloc(nb + 1);
-        int64_t tot = scan_exclusive(cnt, T.loff[w].get(), nb, st);
-        CFMM_REQUIRE(tot < (int64_t)1 << 31, CFMM_EUNSUPPORTED, "interaction list longer than 2^31 entries");
-        int t32 = (int)tot;
-        CFMM_CUDA(cudaMemcpyAsync(T.loff[w].get() + nb, &t32, sizeof(int), cudaMemcpyHostToDevice, st));
-        T.llen[w] = tot;
-        T.lent[w].alloc(tot > 0 ? tot : 1);
+        scan_exclusive_async(cw, T.loff[w].get(), nb + 1, st);   // loff[nb] = total
+    }
+    int tot[4];
+    for (int w = 0; w < 4; ++w)
+        CFMM_CUDA(cudaMemcpyAsync(&tot[w], T.loff[w].get() + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CFMM_CUDA(cudaStreamSynchronize(st));
+    for (int w = 0; w < 4; ++w) {
+        CFMM_REQUIRE(tot[w] >= 0, CFMM_EUNSUPPORTED, "interaction list longer than 2^31 entries");
+        T.llen[w] = tot[w];
+        T.lent[w].alloc(tot[w] > 0 ? tot[w] : 1);
         k_list_fill<<<blocks_for((int64_t)nb * 32, 128), 128, 0, st>>>(C, w, T.loff[w].get(), T.lent[w].get());
         CFMM_LAUNCHED();
-        CFMM_CUDA(cudaStreamSynchronize(st));
     }
     // work counters
     unsigned long long* acc = plan_scratch().take_n<unsigned long long>(1);

@@ -39,6 +39,21 @@ def test_helm3d_vs_oracle_fmm(cuda, eps, sep):
     assert relerr_paper(u[0], u0, dens[0].reshape(-1)) <= eps
 
 
+@pytest.mark.parametrize("leaf", [24, 96])
+def test_helm3d_single_layer_vs_oracle_fmm(cuda, leaf):
+    """The single-layer-only P2M/P2L path (one lane per harmonic column)."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    eps = 1e-3
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, KAPPA, eps, cuda, leaf, sep=2, dlp=False)
+    dens = densities(g.n, seed=5, nrhs=2, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=KAPPA, eps=eps, helmholtz=True)
+    uo, _ = H.apply(g.re, g.im, KAPPA, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
+    for r in range(2):
+        assert relerr_l2(u[r], uo[r]) <= 1e-12
+
+
 def test_helm3d_mixed_precision(cuda):
     import paper_2509_05458_gb300 as cf
     g = _geom()
