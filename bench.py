@@ -46,6 +46,15 @@ W3D = dict(KAPPA=10.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SE
            WORKLOAD="3D Helmholtz SLP k=10, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
                     "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / 128 (FP64) "
                     "as picked by the leaf-size autotuner")
+# --workload batch3d: the batched 3D Helmholtz configuration (one geometry with
+# 64 right-hand sides plus 32 uneven geometries, all replayed as one CUDA graph)
+W4 = dict(KAPPA=15.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=200_000, SEP=2, DIM=3, DLP=False,
+          METRIC="complex-FMM pts/s at rel.err<=1e-6 (batched 3D Helmholtz SLP, k=15: N=2e5 x 64 RHS "
+                 "+ 32 uneven geometries, one CUDA graph)",
+          WORKLOAD="batched 3D Helmholtz SLP k=15, eps=1e-6: plane-with-bump surface N=2e5 (Halton in "
+                   "[-20,20]^2, slope 0.4) with 64 RHS, plus 32 surfaces of N log-uniform in [1e4, 2e5], "
+                   "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; separation k=2; "
+                   "leaf sizes from the autotuner per geometry")
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
 
 
@@ -303,6 +312,183 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """--workload batch3d: one step = one replay of the batch graph (every
+    geometry's apply on its resident plan); value = point evaluations (points x
+    right-hand sides, summed over the geometries) per second."""
+    import numpy as np
+    import torch
+
+    import paper_2509_05458_gb300 as cf
+    from paper_2509_05458_gb300.autotune import tune_leaf_size
+    from cfmm_inputs import config3, config4_uneven, densities
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    geoms = [config3(N_POINTS, seed=0)] + config4_uneven()
+    nrhs = [64] + [1] * (len(geoms) - 1)
+    kernel = cf.HELMHOLTZ | cf.SLP
+    main = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pts_re = [torch.from_numpy(g.re).to(dev) for g in geoms]
+    pts_im = [torch.from_numpy(g.im).to(dev) for g in geoms]
+    dens_np = [densities(g.n, seed=100 + i, nrhs=nrhs[i], ncomp=1) for i, g in enumerate(geoms)]
+    dens = [torch.from_numpy(d).to(dev) for d in dens_np]
+    evals = sum(g.n * r for g, r in zip(geoms, nrhs))
+
+    def build(precision):
+        cands = (128, 192, 256, 384) if precision == cf.MIXED else (64, 96, 128, 192)
+        plans, outs, leaves, streams = [], [], [], []
+        for i, g in enumerate(geoms):
+            s = torch.cuda.Stream(device=dev)
+            leaf, _ = tune_leaf_size(3, kernel, KAPPA, EPS, pts_re[i], pts_im[i], precision=precision,
+                                     candidates=cands, reps=2, stream=s, sep=SEP)
+            p = cf.plan(3, kernel, KAPPA, EPS, pts_re[i], pts_im[i], leaf_size=leaf, sep=SEP,
+                        precision=precision, stream=s)
+            plans.append(p)
+            outs.append(torch.empty((nrhs[i], g.n), dtype=torch.complex128, device=dev))
+            leaves.append(leaf)
+            streams.append(s)
+        torch.cuda.synchronize()
+        b = cf.Batch([(plans[i], dens[i], outs[i]) for i in range(len(geoms))], main)
+        main.synchronize()
+        return plans, outs, leaves, streams, b
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(main):
+                flush.zero_()
+            ev0.record(main)
+            fn()
+            ev1.record(main)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        return ms
+
+    def measure(precision, check):
+        plans, outs, leaves, streams, b = build(precision)
+        acc = None
+        if check:
+            from oracle.direct import direct
+            errs = []
+            rng = np.random.default_rng(1)
+            for i, g in enumerate(geoms):
+                nt = 60 if i == 0 else 20
+                idx = rng.choice(g.n, nt, replace=False)
+                pts = g.re + 1j * g.im
+                for r in ((0, nrhs[i] - 1) if nrhs[i] > 1 else (0,)):
+                    u0 = direct(3, 1, KAPPA, pts, pts[idx], sigma=dens_np[i][r, 0])
+                    u = outs[i][r].cpu().numpy()[idx]
+                    errs.append(float(np.linalg.norm(u - u0) / np.linalg.norm(u0)))
+            acc = {"max_rel_l2": max(errs), "median_rel_l2": float(np.median(errs)),
+                   "per_geometry_rhs0": [errs[0]] + errs[2:]}
+        clocks = ClockSampler(local)
+        n0 = cf.launch_count()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        clocks.start()
+        ms = timed(b.replay)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        clk = clocks.stop()
+        launches = (cf.launch_count() - n0) // max(1, args.steps + args.warmup)
+
+        # the same applies issued eagerly (host launches, one stream per geometry)
+        def eager():
+            for i, p in enumerate(plans):
+                streams[i].wait_event(ev0)
+                p.apply(dens[i], out=outs[i])
+                main.wait_stream(streams[i])
+        ems = timed(eager)
+        # per-step breakdown of the 64-RHS geometry (dominant kernel)
+        plans[0].set_timing(True)
+        plans[0].apply(dens[0], out=outs[0])
+        kt = np.array(plans[0].timings())
+        plans[0].set_timing(False)
+        work = work_model(plans[0])
+        # end to end: pinned host densities in, results out, around one replay
+        hd = [torch.from_numpy(d).pin_memory() for d in dens_np]
+        ho = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        e2e = []
+        for k in range(max(3, args.steps) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(main):
+                for i in range(len(geoms)):
+                    dens[i].copy_(hd[i], non_blocking=True)
+                b.replay()
+                for i in range(len(geoms)):
+                    ho[i].copy_(outs[i], non_blocking=True)
+            main.synchronize()
+            if k > 0:
+                e2e.append(time.perf_counter() - t0)
+        out = dict(ms=_max_over_ranks(statistics.mean(ms), ws, dev), eager_ms=statistics.mean(ems), acc=acc,
+                   clk=clk, launches=launches, kernels=b.kernels, leaves=leaves, kt=kt, work=work,
+                   e2e_s=statistics.median(e2e), h2d=sum(d.nbytes for d in dens_np),
+                   d2h=sum(o.numel() * 16 for o in outs), info=plans[0].info())
+        b.destroy()
+        for p in plans:
+            p.destroy()
+        return out
+
+    check = rank == 0 and not args.skip_check
+    mixed = measure(cf.MIXED, check)
+    fp64 = measure(cf.FP64, check) if args.precision == "both" else None
+    if rank != 0:
+        return
+    kt = mixed["kt"]
+    dom = int(np.argmax(kt))
+    work = dict(mixed["work"])
+    work["m2l_flops"] *= nrhs[0]
+    work["p2p_pairs"] *= nrhs[0]
+    roof = dominant_roofline(STEP_NAMES[dom], kt[dom], work, 1250.0)
+    roof["scope"] = "the 64-RHS geometry's apply, timed alone with per-step events"
+    line = {
+        "metric": METRIC,
+        "value": evals * ws / (mixed["ms"] / 1e3),
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": mixed["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "geometries": len(geoms), "points": [g.n for g in geoms],
+                   "nrhs": nrhs, "point_evaluations_per_step": evals, "kappa": KAPPA, "eps": EPS, "sep": SEP,
+                   "leaf_sizes": mixed["leaves"], "precision": "MIXED (near field complex64, translations FP64)",
+                   "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) before every timed step"},
+        "accuracy": mixed["acc"],
+        "eager_same_applies": {"value": evals / (mixed["eager_ms"] / 1e3), "unit": "points/s",
+                               "ms": mixed["eager_ms"]},
+        "step_breakdown_ms_64rhs": {STEP_NAMES[i]: float(kt[i]) for i in range(9)},
+        "work_64rhs": work,
+        "roofline": roof,
+        "e2e": {"value": evals / mixed["e2e_s"], "unit": "points/s", "h2d_bytes_per_step": int(mixed["h2d"]),
+                "d2h_bytes_per_step": int(mixed["d2h"])},
+        "gpu_launches": int(mixed["kernels"]),
+        "gpu_launches_counted": int(mixed["launches"]),
+        "clocks": mixed["clk"],
+    }
+    if fp64:
+        line["fp64"] = {"value": evals / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"], "accuracy": fp64["acc"],
+                        "leaf_sizes": fp64["leaves"], "clocks": fp64["clk"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+
+
 def work_model(p):
     """Algorithmic work of one apply: List-2 pairs and M2L flops (8 flops per
     complex multiply-add, (2P+1)^2 per pair at the pair's level), List-1 pairs."""
@@ -432,15 +618,20 @@ def main():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
-    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d"],
-                    help="helm2d: the 2D Helmholtz headline; helm3d: the 3D Helmholtz surface line")
+    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "batch3d"],
+                    help="helm2d: the 2D Helmholtz headline; helm3d: the 3D Helmholtz surface line; "
+                         "batch3d: the batched 3D Helmholtz line")
     args = ap.parse_args()
     if args.workload == "helm3d":
         globals().update(W3D)
+    elif args.workload == "batch3d":
+        globals().update(W4)
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))
         args.steps = max(1, min(args.steps, 2))
         run_reference(args)
+    elif args.workload == "batch3d":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -24,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["curve2d", "surface3d", "densities", "halton", "Geometry",
-           "config1", "config2", "config3"]
+           "config1", "config2", "config3", "config4_uneven"]
 
 
 class Geometry:
@@ -140,3 +140,14 @@ def config2(n=100000, seed=0):
 def config3(n=1000000, seed=0):
     """3D workload: complexified plane with bump, Halton points in [-20, 20]^2."""
     return surface3d(n, seed=seed, half=20.0, amp=0.5, width=1.0, slope=0.4, rho0=6.0)
+
+
+def config4_uneven(count=32, seed0=100, nmin=10_000, nmax=200_000):
+    """The uneven batch of the batched 3D Helmholtz workload: `count` surfaces
+    of the ``surface3d`` family ([-20, 20]^2, bump 0.5, rho0 = 6), geometry i
+    with N log-uniform in [nmin, nmax] (drawn from seed0) and its width ~
+    U[0.5, 3] and slope ~ U[0.2, 0.8] drawn from seed0 + 1 + i."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    ns = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=count))
+    return [surface3d(int(round(n)), seed=seed0 + 1 + i, half=20.0, amp=0.5, rho0=6.0, random_shape=True)
+            for i, n in enumerate(ns)]

@@ -129,6 +129,34 @@ int cfmm_apply(cfmm_plan_t plan, const double* densities, int nrhs, double* out)
 int cfmm_apply_capture(cfmm_plan_t plan, const double* densities, int nrhs, double* out);
 int cfmm_apply_replay(cfmm_plan_t plan);
 
+/*
+ * Batches of geometries. The paper applies one geometry at a time; a batched
+ * solve applies many resident plans (uneven sizes) per step, and one CUDA
+ * graph over all of them lets the small geometries' kernels overlap.
+ *
+ * cfmm_batch_capture: applies each of the `count` plans once eagerly (device
+ * buffers densities[i] [nrhs[i]][ncomp_i][n_i] and out[i] [nrhs[i]][n_i]
+ * complex128, as in cfmm_apply; `out` holds that result on return), then
+ * records the same applies into ONE CUDA graph: `stream` (non-NULL) forks to
+ * each plan's stream, the plan's apply runs there, and `stream` joins them.
+ * Plans on different streams become concurrent branches; plans sharing a
+ * stream run in array order. Every plan needs a non-NULL stream and must live
+ * on the current device. The graph keeps the pointers: until
+ * cfmm_batch_destroy, the buffers must stay valid, and no member plan may be
+ * destroyed or applied with a larger nrhs than captured (that regrows its
+ * workspaces). Returns NULL on failure (see cfmm_last_status).
+ * cfmm_batch_replay: launches the graph on `stream` (asynchronous); each
+ * out[i] is overwritten with the apply of what densities[i] then holds.
+ * cfmm_batch_kernels: kernel nodes in the graph (kernels per replay).
+ * cfmm_batch_destroy: waits for `stream`, frees the graph; NULL is OK.
+ */
+typedef struct cfmm_batch_s* cfmm_batch_t;
+cfmm_batch_t cfmm_batch_capture(const cfmm_plan_t* plans, int count, const double* const* densities,
+                                const int* nrhs, double* const* out, void* stream);
+int cfmm_batch_replay(cfmm_batch_t batch);
+int64_t cfmm_batch_kernels(cfmm_batch_t batch);
+int cfmm_batch_destroy(cfmm_batch_t batch);
+
 /* cfmm_destroy: frees the plan; NULL is OK. */
 int cfmm_destroy(cfmm_plan_t plan);
 

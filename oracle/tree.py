@@ -320,6 +320,14 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
             continue
         if kappa * sq * gm <= tau:
             return m
+    if T.dim == 3:
+        # no level of the tree qualifies: take at least the coarsest level whose
+        # order fits, which the forced refinement of build_tree then reaches
+        m = 1
+        while m < T.B and nterms_helmholtz(3, T.k, eps * P_HEADROOM_HELM, kappa, T.width(m),
+                                           helm3d_pair) > P_MAX_3D:
+            m += 1
+        return max(maxl, m)
     return maxl
 
 

@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["LAPLACE", "HELMHOLTZ", "SLP", "DLP", "GREEN_SCALE", "FP64", "MIXED", "AUTO",
-           "Plan", "plan", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
+           "Plan", "plan", "Batch", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
 
 LAPLACE, HELMHOLTZ = 0, 1
 SLP, DLP, GREEN_SCALE = 1 << 4, 1 << 5, 1 << 6
@@ -66,6 +66,14 @@ def lib():
     L.cfmm_apply_capture.argtypes = [vp, vp, ci, vp]
     L.cfmm_apply_replay.restype = ci
     L.cfmm_apply_replay.argtypes = [vp]
+    L.cfmm_batch_capture.restype = vp
+    L.cfmm_batch_capture.argtypes = [C.POINTER(vp), ci, C.POINTER(vp), C.POINTER(ci), C.POINTER(vp), vp]
+    L.cfmm_batch_replay.restype = ci
+    L.cfmm_batch_replay.argtypes = [vp]
+    L.cfmm_batch_kernels.restype = i64
+    L.cfmm_batch_kernels.argtypes = [vp]
+    L.cfmm_batch_destroy.restype = ci
+    L.cfmm_batch_destroy.argtypes = [vp]
     L.cfmm_destroy.restype = ci
     L.cfmm_destroy.argtypes = [vp]
     L.cfmm_direct.restype = ci
@@ -251,6 +259,48 @@ class Plan:
         _check(lib().cfmm_plan_timings(self._h, t.ctypes.data, 9))
         return t
 
+
+
+class Batch:
+    """One CUDA graph over one apply of each of several plans (cfmm_batch_capture).
+
+    members: list of (plan, densities, out) with CUDA tensors as in
+    Plan.capture; each plan must have been created with its own (non-default)
+    stream. The tensors are kept alive here; replay() reruns every apply, the
+    members on different streams concurrently."""
+
+    def __init__(self, members, stream):
+        n = len(members)
+        for p, d, o in members:
+            if not (d.is_cuda and o.is_cuda and d.is_contiguous() and o.is_contiguous()):
+                raise ValueError("a batch takes contiguous CUDA tensors")
+        self._keep = list(members)
+        hp = (C.c_void_p * n)(*[p.handle for p, _, _ in members])
+        dp = (C.c_void_p * n)(*[_ptr(d) for _, d, _ in members])
+        nr = (C.c_int * n)(*[int(d.shape[0]) for _, d, _ in members])
+        op = (C.c_void_p * n)(*[_ptr(o) for _, _, o in members])
+        self._stream = stream
+        self._h = lib().cfmm_batch_capture(hp, n, dp, nr, op, _stream_ptr(stream))
+        if not self._h:
+            _check(lib().cfmm_last_status() or -5)
+
+    def replay(self):
+        _check(lib().cfmm_batch_replay(self._h))
+
+    @property
+    def kernels(self):
+        return int(lib().cfmm_batch_kernels(self._h))
+
+    def destroy(self):
+        if self._h:
+            lib().cfmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 def plan(dim, kernel, k, eps, pts_re, pts_im, nrm_re=None, nrm_im=None, leaf_size=64, sep=1,
          precision=FP64, top_level=0, stream=None):

@@ -16,7 +16,7 @@ import statistics
 
 import numpy as np
 
-from . import plan as make_plan
+from . import CfmmError, plan as make_plan
 
 _CACHE = {}
 
@@ -44,8 +44,11 @@ def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = {}
     for ls in candidates:
-        p = make_plan(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re, nrm_im, leaf_size=ls, sep=sep,
-                      precision=precision, stream=stream)
+        try:
+            p = make_plan(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re, nrm_im, leaf_size=ls, sep=sep,
+                          precision=precision, stream=stream)
+        except CfmmError:
+            continue          # a candidate the plan rejects (e.g. an order limit) is skipped
         out = p.apply(dens)
         ms = []
         for _ in range(reps):
@@ -56,6 +59,8 @@ def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=
             ms.append(ev0.elapsed_time(ev1))
         times[ls] = statistics.median(ms)
         p.destroy()
+    if not times:
+        raise CfmmError(-7, "no leaf-size candidate gives a valid plan")
     best = min(times, key=times.get)
     _CACHE[key] = (best, times)
     return best, times

@@ -339,6 +339,27 @@ static void destroy_plan(cfmm_plan_s* P) {
 
 }  // namespace cfmm
 
+// One CUDA graph over the applies of several plans (a batch of geometries).
+struct cfmm_batch_s {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;              // kernel nodes in the graph
+    std::vector<cudaEvent_t> ev;      // fork + one join per member
+};
+
+namespace cfmm {
+static void destroy_batch(cfmm_batch_s* B) {
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    for (auto& e : B->ev)
+        if (e) cudaEventDestroy(e);
+    delete B;
+}
+}  // namespace cfmm
+
 using namespace cfmm;
 
 extern "C" {
@@ -464,6 +485,7 @@ int cfmm_apply_capture(cfmm_plan_t P, const double* densities, int nrhs, double*
             cudaGraphDestroy(P->graph);
             P->graph = nullptr;
         }
+        int64_t c0 = launch_counter().load();
         CFMM_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
         try {
             apply_device(P, d_in, nrhs, d_out);
@@ -474,6 +496,9 @@ int cfmm_apply_capture(cfmm_plan_t P, const double* densities, int nrhs, double*
             P->timing = timing;
             throw;
         }
+        // the kernels were recorded, not launched: count them at each replay
+        P->graph_kernels = launch_counter().load() - c0;
+        launch_counter().fetch_sub(P->graph_kernels);
         CFMM_CUDA(cudaStreamEndCapture(P->stream, &P->graph));
         CFMM_CUDA(cudaGraphInstantiate(&P->graph_exec, P->graph, 0));
         P->timing = timing;
@@ -484,8 +509,88 @@ int cfmm_apply_replay(cfmm_plan_t P) {
     return guarded([&] {
         CFMM_REQUIRE(P && P->graph_exec, CFMM_EINVAL, "no captured apply");
         CFMM_CUDA(cudaGraphLaunch(P->graph_exec, P->stream));
-        count_launch();
+        count_launch((int)P->graph_kernels);
     });
+}
+
+cfmm_batch_t cfmm_batch_capture(const cfmm_plan_t* plans, int count, const double* const* densities,
+                                const int* nrhs, double* const* out, void* stream) {
+    auto* B = new cfmm_batch_s;
+    std::vector<std::pair<cfmm_plan_s*, bool>> saved;
+    int rc = guarded([&] {
+        CFMM_REQUIRE(plans && densities && nrhs && out && count >= 1, CFMM_EINVAL, "bad arguments");
+        CFMM_REQUIRE(stream != nullptr, CFMM_EINVAL, "batch capture needs a non-NULL stream");
+        B->stream = (cudaStream_t)stream;
+        int dev = 0;
+        CFMM_CUDA(cudaGetDevice(&dev));
+        for (int i = 0; i < count; ++i) {
+            cfmm_plan_s* P = plans[i];
+            CFMM_REQUIRE(P, CFMM_EINVAL, "null plan in batch");
+            CFMM_REQUIRE(P->stream != nullptr, CFMM_EINVAL, "every plan of a batch needs a non-NULL stream");
+            CFMM_REQUIRE(P->device == dev, CFMM_EINVAL, "every plan of a batch must live on the current device");
+            CFMM_REQUIRE(nrhs[i] >= 1 && densities[i] && out[i], CFMM_EINVAL, "bad batch member arguments");
+            CFMM_REQUIRE(is_device_ptr(densities[i]) && is_device_ptr(out[i]), CFMM_EINVAL,
+                         "batch capture takes device pointers");
+        }
+        for (int i = 0; i < count; ++i) {
+            saved.push_back({plans[i], plans[i]->timing});
+            plans[i]->timing = false;
+        }
+        auto din = [&](int i) { return reinterpret_cast<const cd*>(densities[i]); };
+        auto dout = [&](int i) { return reinterpret_cast<cd*>(out[i]); };
+        // one eager apply per member sizes every workspace, so nothing is
+        // allocated while capturing
+        for (int i = 0; i < count; ++i) apply_device(plans[i], din(i), nrhs[i], dout(i));
+        for (int i = 0; i < count; ++i) CFMM_CUDA(cudaStreamSynchronize(plans[i]->stream));
+        B->ev.assign(count + 1, nullptr);
+        for (auto& e : B->ev) CFMM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        int64_t c0 = launch_counter().load();
+        CFMM_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            // fork: every member stream waits for the batch stream, runs its
+            // apply, and the batch stream joins them all
+            CFMM_CUDA(cudaEventRecord(B->ev[0], B->stream));
+            for (int i = 0; i < count; ++i) {
+                cudaStream_t ps = plans[i]->stream;
+                if (ps != B->stream) CFMM_CUDA(cudaStreamWaitEvent(ps, B->ev[0], 0));
+                apply_device(plans[i], din(i), nrhs[i], dout(i));
+                if (ps != B->stream) {
+                    CFMM_CUDA(cudaEventRecord(B->ev[i + 1], ps));
+                    CFMM_CUDA(cudaStreamWaitEvent(B->stream, B->ev[i + 1], 0));
+                }
+            }
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(B->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            launch_counter().store(c0);
+            throw;
+        }
+        B->kernels = launch_counter().load() - c0;
+        launch_counter().fetch_sub(B->kernels);
+        CFMM_CUDA(cudaStreamEndCapture(B->stream, &B->graph));
+        CFMM_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+    });
+    for (auto& s : saved) s.first->timing = s.second;
+    if (rc != 0) {
+        destroy_batch(B);
+        return nullptr;
+    }
+    return B;
+}
+
+int cfmm_batch_replay(cfmm_batch_t B) {
+    return guarded([&] {
+        CFMM_REQUIRE(B && B->exec, CFMM_EINVAL, "no captured batch");
+        CFMM_CUDA(cudaGraphLaunch(B->exec, B->stream));
+        count_launch((int)B->kernels);
+    });
+}
+
+int64_t cfmm_batch_kernels(cfmm_batch_t B) { return B ? B->kernels : 0; }
+
+int cfmm_batch_destroy(cfmm_batch_t B) {
+    return guarded([&] { destroy_batch(B); });
 }
 
 int cfmm_destroy(cfmm_plan_t P) {

@@ -223,4 +223,5 @@ struct cfmm_plan_s {
     // captured apply
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_kernels = 0;       // kernel nodes recorded in `graph`
 };

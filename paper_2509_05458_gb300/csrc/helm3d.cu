@@ -507,11 +507,37 @@ __global__ void k_radial3h(Exp3hArgs A, const int* __restrict__ boxes, int nboxe
     }
 }
 
-// Single-layer P2M (sing = 0) / P2L (sing = 1) with one warp per source at a
-// time and one lane per harmonic column: lane c of warp w walks the column
-// of Z_n^{mu} (mu = -m for coefficient m) of its source, n = |mu|..P, and adds
-// F[n] Z sigma into the warp's private accumulator row; the warp rows are
-// summed in warp order at the end, so the result does not depend on timing.
+// One harmonic column of a single-layer source: Z_n^{mu}(y) sigma for
+// n = |mu|..P (mu >= 0 from x+, mu < 0 from x-, col = mu or P - mu), times
+// the radial factor F[n], added into acc at coefficient (n, -mu).
+__device__ __forceinline__ void p2x_column(const ZCoef& zc, int P, int col, cd xp, cd xm, cd z, cd r2, cd sg,
+                                           const cd* __restrict__ F, cd* acc) {
+    int am = col <= P ? col : col - P;
+    bool neg = col > P;
+    int m = neg ? am : -am;
+    cd xs = neg ? xm : xp;
+    cd d = sg;
+    for (int i = 1; i <= am; ++i) d = (-__ldg(zc.dg + i)) * (xs * d);
+    acc[nmi(am, m)] += F[am] * d;
+    if (am + 1 > P) return;
+    cd p2 = d, p1 = __ldg(zc.s21 + am) * (z * d);
+    acc[nmi(am + 1, m)] += F[am + 1] * p1;
+    for (int n = am + 2; n <= P; ++n) {
+        int k = nmi(n, am);
+        cd cur = __ldg(zc.A + k) * (z * p1) - __ldg(zc.B + k) * (r2 * p2);
+        acc[nmi(n, m)] += F[n] * cur;
+        p2 = p1;
+        p1 = cur;
+    }
+}
+
+// Single-layer P2M (sing = 0) / P2L (sing = 1). Each warp owns an accumulator
+// row in shared memory and takes the (source, column) items of its box in
+// rounds of 32 consecutive items, one per lane; with 2P+1 >= 32 columns the
+// lanes of a round hold distinct columns, so they touch disjoint coefficients,
+// and __syncwarp orders the rounds. With fewer columns a warp takes one source
+// at a time, one lane per column. The warp rows are summed in warp order at
+// the end, so the result does not depend on timing.
 __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const int* __restrict__ loff,
                             const int* __restrict__ lent, int sing, const int* __restrict__ roff,
                             const cd* __restrict__ rad, cd* __restrict__ out) {
@@ -521,9 +547,11 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
     int rhs = blockIdx.y;
     int P = A.Plev[A.blevel[b]];
     int nc = (P + 1) * (P + 1);
+    int C = 2 * P + 1;
     int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     cd* accw = sm + (size_t)wid * nc;
     for (int c = lane; c < nc; c += 32) accw[c] = cd{0, 0};
+    __syncwarp();
     cd cen[3];
     for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
     int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
@@ -531,33 +559,31 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
     for (int q = qa; q < qb; ++q) {
         int src = loff ? lent[q] : b;
         int s0 = A.bst[src], s1 = A.ben[src];
-        for (int j = s0 + wid; j < s1; j += nwarp) {
-            cd y[3];
-            load3(A.xr, A.xi, A.n, j, y);
-            for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
-            cd sg = A.sigma[rhs * A.dstride + j];
-            const cd* F = rad + (o + (j - s0)) * (int64_t)(P + 1);
-            cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
-            cd r2 = xp * xm + z * z;
-            for (int col = lane; col < 2 * P + 1; col += 32) {
-                // column of Z_n^{mu}: mu >= 0 with x+, mu < 0 with x-; it feeds coefficient m = -mu
-                int am = col <= P ? col : col - P;
-                bool neg = col > P;
-                int mu = neg ? -am : am;
-                cd xs = neg ? xm : xp;
-                cd d = sg;
-                for (int i = 1; i <= am; ++i) d = (-__ldg(A.zc.dg + i)) * (xs * d);
-                int m = -mu;
-                accw[nmi(am, m)] += F[am] * d;
-                if (am + 1 > P) continue;
-                cd p2 = d, p1 = __ldg(A.zc.s21 + am) * (z * d);
-                accw[nmi(am + 1, m)] += F[am + 1] * p1;
-                for (int n = am + 2; n <= P; ++n) {
-                    int k = nmi(n, am);
-                    cd cur = __ldg(A.zc.A + k) * (z * p1) - __ldg(A.zc.B + k) * (r2 * p2);
-                    accw[nmi(n, m)] += F[n] * cur;
-                    p2 = p1;
-                    p1 = cur;
+        if (C >= 32) {
+            int items = (s1 - s0) * C;
+            for (int base = wid * 32; base < items; base += nwarp * 32) {
+                int it = base + lane;
+                if (it < items) {
+                    int js = it / C, col = it - js * C;
+                    int j = s0 + js;
+                    cd y[3];
+                    load3(A.xr, A.xi, A.n, j, y);
+                    for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
+                    cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
+                    p2x_column(A.zc, P, col, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
+                               rad + (o + js) * (int64_t)(P + 1), accw);
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int j = s0 + wid; j < s1; j += nwarp) {
+                if (lane < C) {
+                    cd y[3];
+                    load3(A.xr, A.xi, A.n, j, y);
+                    for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
+                    cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
+                    p2x_column(A.zc, P, lane, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
+                               rad + (o + (j - s0)) * (int64_t)(P + 1), accw);
                 }
             }
         }

@@ -1239,12 +1239,24 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
             double tau = (dim == 2 ? 0.25 : 1.0) * std::log(P->eps / std::ldexp(1.0, -52));
             int maxl = P->tree.nlevels - 1;
             l0 = maxl < 1 ? 1 : maxl;
+            bool found = false;
+            auto p_fits = [&](int m) {
+                return dim != 3 || nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -m)) <= 63;
+            };
             for (int m = 1; m <= maxl; ++m) {
-                if (dim == 3 && nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -m)) > 63) continue;
+                if (!p_fits(m)) continue;
                 if (P->kappa * std::sqrt((double)dim) * spread[m] <= tau) {
                     l0 = m;
+                    found = true;
                     break;
                 }
+            }
+            if (!found && dim == 3 && maxl >= 1) {
+                // no level of the tree qualifies: take at least the coarsest level
+                // whose order fits; the forced refinement below reaches it
+                int m = 1;
+                while (m < B && !p_fits(m)) ++m;
+                l0 = std::max(l0, m);
             }
         }
         if (l0 > 1) {

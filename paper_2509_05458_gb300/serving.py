@@ -181,7 +181,12 @@ def summarize(results: List[Result], wall_s: float):
         i = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
         return lat[i]
 
-    return {"requests": len(results), "errors": sum(1 for r in results if r.error),
+    kinds = {}
+    for r in results:
+        if r.error:
+            k = r.error[:80]
+            kinds[k] = kinds.get(k, 0) + 1
+    return {"requests": len(results), "errors": sum(1 for r in results if r.error), "error_kinds": kinds,
             "p50_s": pct(50), "p99_s": pct(99), "mean_s": statistics.mean(lat) if lat else None,
             "points_per_s": pts / wall_s if wall_s > 0 else None, "wall_s": wall_s}
 

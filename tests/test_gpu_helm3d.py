@@ -85,3 +85,19 @@ def test_helm3d_repeat_bitwise(cuda):
     a = p.apply(d).cpu().numpy()
     b = p.apply(d).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+def test_helm3d_top_level_deeper_than_initial_tree(cuda):
+    """A shallow initial tree whose levels all need orders above the 3D limit:
+    both sides refine to the coarsest level whose order fits."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    kap, eps, leaf = 20.0, 1e-3, 700
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2)
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True)
+    assert p.info()["l0"] == T.l0 == 2
+    assert list(p.orders()) == H.expansion_orders(T, kap, eps)
+    dens = densities(g.n, seed=9, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
+    assert relerr_l2(u[0], uo[0]) <= 1e-12

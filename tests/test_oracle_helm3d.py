@@ -229,3 +229,16 @@ def test_single_leaf_is_direct():
     assert T.nboxes == 1
     u0 = direct(3, 1, KAPPA, pts, pts, sigma=dens[0, 0])
     assert relerr_l2(u, u0) < 1e-14
+
+
+def test_top_level_deeper_than_initial_tree():
+    """When no level of the initial tree has an order within the 3D limit (a
+    shallow tree at high kappa), the top level is the coarsest level whose
+    order fits, and the forced refinement makes the tree reach it."""
+    from oracle import tree as tr
+    g = surface3d(1500, seed=2, half=4.0, amp=0.5, width=1.0, slope=0.3, rho0=1.0)
+    T = tr.build_tree(g.re, g.im, 700, k=2, kappa=20.0, eps=1e-3, helmholtz=True)
+    P = H.expansion_orders(T, 20.0, 1e-3)
+    assert T.l0 == 2 and T.nlevels == 3
+    assert P[T.l0] <= tr.P_MAX_3D and all(P[l] > tr.P_MAX_3D for l in range(T.l0))
+    assert min(T.box_level[b] for b in range(T.nboxes) if T.box_leaf[b]) >= T.l0
