@@ -38,6 +38,7 @@ KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
 METRIC = "complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, N=1e5)"
 WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
 SEP, DIM, DLP = 1, 2, True
+KERNEL = 1            # 1 = Helmholtz, 0 = Laplace
 LEAF_FP64 = 64
 # --workload helm3d: the 3D Helmholtz surface configuration (a second bench line,
 # not the headline)
@@ -55,6 +56,11 @@ W4 = dict(KAPPA=15.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=200_000, SEP=2
                    "[-20,20]^2, slope 0.4) with 64 RHS, plus 32 surfaces of N log-uniform in [1e4, 2e5], "
                    "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; separation k=2; "
                    "leaf sizes from the autotuner per geometry")
+# --workload lap3d: the 3D Laplace surface configuration (same surface as helm3d)
+WL3D = dict(KAPPA=0.0, KERNEL=0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
+            METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Laplace SLP, N=1e6)",
+            WORKLOAD="3D Laplace SLP, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
+                     "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / 128 (FP64)")
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
 
 
@@ -160,7 +166,7 @@ def run_gpu(args):
     nim = torch.from_numpy(g.nrm_im).to(dev) if DLP else None
     dens = torch.from_numpy(dens_np).to(dev)
     out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
-    kernel = cf.HELMHOLTZ | cf.SLP | (cf.DLP if DLP else 0)
+    kernel = (cf.HELMHOLTZ if KERNEL else cf.LAPLACE) | cf.SLP | (cf.DLP if DLP else 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -192,7 +198,7 @@ def run_gpu(args):
             from oracle.direct import direct
             idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
             pts = g.re + 1j * g.im
-            u0 = direct(DIM, 1, KAPPA, pts, pts[idx], sigma=dens_np[0, 0],
+            u0 = direct(DIM, KERNEL, KAPPA, pts, pts[idx], sigma=dens_np[0, 0],
                         tau=dens_np[0, 1] if DLP else None, nrm=(g.nrm_re + 1j * g.nrm_im) if DLP else None)
             u = out.cpu().numpy()[0, idx]
             acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
@@ -504,7 +510,10 @@ def work_model(p):
         npairs = int(cnt[t["level"] == l].sum())
         if npairs:
             pairs_per_level[int(l)] = npairs
-            m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if DIM == 3 else 8 * (2 * int(P[l]) + 1) ** 2)
+            if DIM == 2:
+                m2l_flops += npairs * 8 * (2 * int(P[l]) + 1) ** 2
+            else:
+                m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if KERNEL else m2l_flops_pair_lap3d(int(P[l])))
     return {"p2p_pairs": int(inf["p2p_pairs"]), "m2l_pairs": int(inf["m2l_pairs"]),
             "m2l_pairs_per_level": pairs_per_level, "orders": [int(x) for x in P],
             "m2l_flops": int(m2l_flops), "p2p_flops_per_pair": P2P_FLOPS_PER_PAIR}
@@ -520,6 +529,15 @@ def m2l_flops_pair_3d(P):
     rec = 12 * P * (P + 1) * (2 * P + 1) // 6
     app = 8 * sum((1 + (m > 0)) * (P - m + 1) ** 2 for m in range(P + 1))
     return rot + rec + app
+
+
+def m2l_flops_pair_lap3d(P):
+    """FP64 flops of one 3D Laplace point-and-shoot M2L at order P: the four
+    fixed-rotation products (as for Helmholtz) and the z-axis solid-harmonic
+    shift (sum_m (1 + [m > 0]) (P - m + 1)^2 complex multiply-adds, 8 flops)."""
+    rot = 4 * 4 * P * (P + 1) * (P + 2) // 3
+    app = 8 * sum((1 + (m > 0)) * (P - m + 1) ** 2 for m in range(P + 1))
+    return rot + app
 
 
 def dominant_roofline(name, ms, work, fp64_peak_gflops):
@@ -556,8 +574,8 @@ def cpu_baseline(args):
                 "from oracle.direct import direct\n"
                 "g = config3(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=1)\n"
                 "pts = g.re + 1j * g.im; idx = np.arange(200)\n"
-                "t=time.perf_counter(); direct(3, 1, %r, pts, pts[idx], sigma=d[0,0]); t=time.perf_counter()-t\n"
-                "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, N_POINTS, KAPPA)
+                "t=time.perf_counter(); direct(3, %d, %r, pts, pts[idx], sigma=d[0,0]); t=time.perf_counter()-t\n"
+                "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, N_POINTS, KERNEL, KAPPA)
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
         if r.returncode != 0:
             return {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
@@ -618,14 +636,20 @@ def main():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
-    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "batch3d"],
-                    help="helm2d: the 2D Helmholtz headline; helm3d: the 3D Helmholtz surface line; "
-                         "batch3d: the batched 3D Helmholtz line")
+    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "lap3d", "batch3d"],
+                    help="helm2d: the 2D Helmholtz headline; helm3d / lap3d: the 3D Helmholtz / Laplace "
+                         "surface lines; batch3d: the batched 3D Helmholtz line")
+    ap.add_argument("--n", type=int, default=0,
+                    help="override the point count (small cases for profiler captures; not a bench line)")
     args = ap.parse_args()
     if args.workload == "helm3d":
         globals().update(W3D)
+    elif args.workload == "lap3d":
+        globals().update(WL3D)
     elif args.workload == "batch3d":
         globals().update(W4)
+    if args.n > 0:
+        globals()["N_POINTS"] = args.n
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))
         args.steps = max(1, min(args.steps, 2))
