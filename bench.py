@@ -495,6 +495,81 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """--workload serve: the serving loop on a Poisson stream of apply requests
+    (dims 2 and 3, Laplace or Helmholtz, N log-uniform in [1e3, nmax], eps in
+    {1e-3, 1e-6, 1e-9}, 1-20 matvecs each). One step = one whole stream; value
+    = point evaluations completed per second of wall time; p50/p99 request
+    latency (arrival to last result on the host) beside it. A short stream of
+    small requests runs first, untimed."""
+    import torch
+
+    from paper_2509_05458_gb300.serving import Server, make_stream, summarize
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    srv = Server(slots=args.slots, device=local)
+    warm = make_stream(max(4, args.warmup), seed=99 + rank, rate_hz=100.0, nmin=1000, nmax=20000, dims=(2, 3))
+    srv.run(warm, realtime=False)
+    runs = []
+    clocks = ClockSampler(local)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        reqs = make_stream(args.requests, seed=7 + 1000 * k + rank, rate_hz=args.rate, nmin=1000,
+                           nmax=args.nmax, dims=(2, 3))
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = summarize(res, wall)
+        st["evaluations"] = sum(len(r.rhs) * r.n for r in reqs)
+        runs.append(st)
+    _barrier(ws)
+    clk = clocks.stop()
+    wall = _max_over_ranks(sum(r["wall_s"] for r in runs), ws, dev)
+    if rank != 0:
+        return
+    evals = sum(r["evaluations"] for r in runs)
+    line = {
+        "metric": "complex-FMM serving: points/s and p50/p99 solve latency (Poisson stream, dims 2+3)",
+        "value": evals * ws / wall,
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / max(1, args.steps),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"serving loop: Poisson stream of {args.requests} apply requests at "
+                               f"{args.rate} Hz, dim in {{2,3}}, Laplace or Helmholtz (k in [1,50], 3D mapped "
+                               f"to [1,10]), N log-uniform in [1e3, {args.nmax:.0e}], eps in {{1e-3,1e-6,1e-9}}, "
+                               "1-20 matvecs per request on a resident plan, admission by free HBM",
+                   "slots": args.slots, "requests_per_step": args.requests, "rate_hz": args.rate,
+                   "nmax": args.nmax, "parallelism": f"replicas{ws}",
+                   "timing": "host wall clock per stream (latency is arrival to result on the host)"},
+        "p50_s": runs[-1]["p50_s"], "p99_s": runs[-1]["p99_s"], "mean_s": runs[-1]["mean_s"],
+        "errors": sum(r["errors"] for r in runs),
+        "error_kinds": runs[-1]["error_kinds"],
+        "streams": runs,
+        "e2e": {"value": evals * ws / wall, "unit": "points/s",
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "the stream itself is end to end: host points and densities in, host results out"},
+        "roofline": None,
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def work_model(p):
     """Algorithmic work of one apply: List-2 pairs and M2L flops (8 flops per
     complex multiply-add, (2P+1)^2 per pair at the pair's level), List-1 pairs."""
@@ -636,9 +711,13 @@ def main():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
-    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "lap3d", "batch3d"],
+    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "lap3d", "batch3d", "serve"],
                     help="helm2d: the 2D Helmholtz headline; helm3d / lap3d: the 3D Helmholtz / Laplace "
-                         "surface lines; batch3d: the batched 3D Helmholtz line")
+                         "surface lines; batch3d: the batched 3D Helmholtz line; serve: the serving loop")
+    ap.add_argument("--requests", type=int, default=100, help="serve: requests per stream")
+    ap.add_argument("--rate", type=float, default=10.0, help="serve: Poisson arrival rate (Hz)")
+    ap.add_argument("--nmax", type=int, default=1_000_000, help="serve: largest request size")
+    ap.add_argument("--slots", type=int, default=4, help="serve: requests in flight")
     ap.add_argument("--n", type=int, default=0,
                     help="override the point count (small cases for profiler captures; not a bench line)")
     args = ap.parse_args()
@@ -656,6 +735,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch3d":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 
