@@ -32,11 +32,16 @@ Readings (all listed in the design doc):
   cancellation): Laplace uses l0 = 1. Helmholtz uses the coarsest level l >= 1
   whose boxes have kappa*sqrt(d)*g_l <= tau(eps), g_l the largest per-axis
   spread of Im x inside one box of level l (a coarser leaf counts with its
-  own spread), tau = c_d ln(eps/2^-52) with c_2 = 1/4 and c_3 = 1 (calibrated:
-  on the 3D surface workload at kappa = 10, 64 wavelengths, top levels 3-5
-  all met eps = 1e-6, while c_3 = 1/4 would force level 6-7 at 10-20 times
-  the cost). In 3D it is also at least the coarsest level with P_l <= 63,
-  the order limit of the CUDA translation kernel. Leaves above l0 are split
+  own spread), tau = c_d ln(eps/2^-52) with c_2 = 1 and c_3 = 2 (calibrated:
+  on the 2D curve workload at kappa = 20 and 50, top levels three to four
+  above the c = 1/4 choice gave the same errors at eps = 1e-6 and 1e-9, and
+  c = 1/4 costs up to 2.6 times more; on the 3D surface workload the error
+  grows with the top level like exp(0.56 kappa g), a third of the exponent
+  sqrt(3) kappa g of the rule, so c_3 = 2 still bounds the growth by
+  (eps/2^-52)^0.65; at kappa = 15 the level it picks met eps = 1e-6 with
+  1.4e-7, at a third of the cost of the c_3 = 1 level). In 3D it is also at
+  least the coarsest level with P_l <= 57, the order limit of the CUDA
+  translation kernel (its work arrays fill the shared memory of a block). Leaves above l0 are split
   down to l0 and the tree is re-balanced. M2L at l0 runs over all non-near
   pairs of l0 boxes.
 """
@@ -48,6 +53,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 EPS_MACH = 2.0 ** -52
+C_TOP = {2: 1.0, 3: 2.0}   # c_d of the top-level rule (module docstring)
 
 
 def bits_for_dim(dim):
@@ -303,7 +309,7 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
     """Top expansion level (see module docstring)."""
     if not helmholtz:
         return 1
-    tau = (0.25 if T.dim == 2 else 1.0) * math.log(eps / EPS_MACH)
+    tau = C_TOP[T.dim] * math.log(eps / EPS_MACH)
     g = imag_spread(T, im_sorted)
     maxl = T.nlevels - 1
     if maxl < 1:
@@ -473,7 +479,7 @@ def check_balance(T):
 # against (r/R)^n and undershoots by about a digit).
 P_HEADROOM = 0.1
 P_HEADROOM_HELM = 0.01
-P_MAX_3D = 63
+P_MAX_3D = 57
 
 def nterms_laplace(dim, k, eps):
     """Smallest n >= 1 with (r/R)^n <= eps, R=(k+1/2)w, r=sqrt(d)/2 w."""

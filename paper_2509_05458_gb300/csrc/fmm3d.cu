@@ -415,8 +415,10 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
         chunk = (int)std::max<size_t>(1, std::min<size_t>(16, (96 * 1024) / (nt * sizeof(cd))));
         return sizeof(cd) * ((size_t)(maxP + 1) * (maxP + 1) + (size_t)chunk * nt + (size_t)chunk * 6);
     };
-    // (1) P2M
-    {
+    // (1) P2M (single layer: one lane per harmonic column)
+    if (!(P->slp && !P->dlp &&
+          lap3_p2m_slp(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
+                       S->exp_off.get(), S->ncoef, sigma, dstride, mp, nrhs))) {
         int chunk;
         size_t smem = p2x_smem(maxP, chunk);
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);

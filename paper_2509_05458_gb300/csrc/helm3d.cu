@@ -64,7 +64,7 @@ namespace {
 __host__ __device__ __forceinline__ int nmi(int n, int m) { return n * n + n + m; }
 
 constexpr int kH3Threads = 256;
-constexpr int kH3MaxP = 63;          // expansion order limit of this path
+constexpr int kH3MaxP = kMaxP3Top;   // expansion order limit of this path
 constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
 constexpr int kM2LChunk3 = 32;       // List-2 entries per block when a list is split
 
@@ -509,7 +509,9 @@ __global__ void k_radial3h(Exp3hArgs A, const int* __restrict__ boxes, int nboxe
 
 // One harmonic column of a single-layer source: Z_n^{mu}(y) sigma for
 // n = |mu|..P (mu >= 0 from x+, mu < 0 from x-, col = mu or P - mu), times
-// the radial factor F[n], added into acc at coefficient (n, -mu).
+// the radial factor F[n] (Helmholtz; none for Laplace), added into acc at
+// coefficient (n, -mu).
+template <bool LAP>
 __device__ __forceinline__ void p2x_column(const ZCoef& zc, int P, int col, cd xp, cd xm, cd z, cd r2, cd sg,
                                            const cd* __restrict__ F, cd* acc) {
     int am = col <= P ? col : col - P;
@@ -518,14 +520,14 @@ __device__ __forceinline__ void p2x_column(const ZCoef& zc, int P, int col, cd x
     cd xs = neg ? xm : xp;
     cd d = sg;
     for (int i = 1; i <= am; ++i) d = (-__ldg(zc.dg + i)) * (xs * d);
-    acc[nmi(am, m)] += F[am] * d;
+    acc[nmi(am, m)] += LAP ? d : F[am] * d;
     if (am + 1 > P) return;
     cd p2 = d, p1 = __ldg(zc.s21 + am) * (z * d);
-    acc[nmi(am + 1, m)] += F[am + 1] * p1;
+    acc[nmi(am + 1, m)] += LAP ? p1 : F[am + 1] * p1;
     for (int n = am + 2; n <= P; ++n) {
         int k = nmi(n, am);
         cd cur = __ldg(zc.A + k) * (z * p1) - __ldg(zc.B + k) * (r2 * p2);
-        acc[nmi(n, m)] += F[n] * cur;
+        acc[nmi(n, m)] += LAP ? cur : F[n] * cur;
         p2 = p1;
         p1 = cur;
     }
@@ -538,9 +540,13 @@ __device__ __forceinline__ void p2x_column(const ZCoef& zc, int P, int col, cd x
 // and __syncwarp orders the rounds. With fewer columns a warp takes one source
 // at a time, one lane per column. The warp rows are summed in warp order at
 // the end, so the result does not depend on timing.
+// LAP: the 3D Laplace P2M, M_n^m = (-1)^m sum sigma U_n^{-m}(y) with the
+// regular solid harmonics U; since Z_n^{-m} = e s U_n^{-m} (s = sqrt((n-|m|)!
+// (n+|m|)!), e = +-1 as in lsd), M_n^m = lsd_n^m sum sigma Z_n^{-m}(y).
+template <bool LAP>
 __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const int* __restrict__ loff,
                             const int* __restrict__ lent, int sing, const int* __restrict__ roff,
-                            const cd* __restrict__ rad, cd* __restrict__ out) {
+                            const cd* __restrict__ rad, cd* __restrict__ out, const double* __restrict__ lsd) {
     extern __shared__ cd sm[];
     int bi = blockIdx.x;
     int b = boxes[bi];
@@ -555,7 +561,7 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
     cd cen[3];
     for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
     int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
-    int64_t o = roff[bi];
+    int64_t o = roff ? roff[bi] : 0;
     for (int q = qa; q < qb; ++q) {
         int src = loff ? lent[q] : b;
         int s0 = A.bst[src], s1 = A.ben[src];
@@ -570,8 +576,8 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
                     load3(A.xr, A.xi, A.n, j, y);
                     for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
                     cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
-                    p2x_column(A.zc, P, col, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
-                               rad + (o + js) * (int64_t)(P + 1), accw);
+                    p2x_column<LAP>(A.zc, P, col, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
+                                    LAP ? nullptr : rad + (o + js) * (int64_t)(P + 1), accw);
                 }
                 __syncwarp();
             }
@@ -582,8 +588,8 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
                     load3(A.xr, A.xi, A.n, j, y);
                     for (int a = 0; a < 3; ++a) y[a] = y[a] - cen[a];
                     cd xp = y[0] + mul_i(y[1]), xm = y[0] - mul_i(y[1]), z = y[2];
-                    p2x_column(A.zc, P, lane, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
-                               rad + (o + (j - s0)) * (int64_t)(P + 1), accw);
+                    p2x_column<LAP>(A.zc, P, lane, xp, xm, z, xp * xm + z * z, A.sigma[rhs * A.dstride + j],
+                                    LAP ? nullptr : rad + (o + (j - s0)) * (int64_t)(P + 1), accw);
                 }
             }
         }
@@ -594,9 +600,13 @@ __global__ void k_p2x3h_slp(Exp3hArgs A, const int* __restrict__ boxes, const in
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         cd v = {0, 0};
         for (int w = 0; w < nwarp; ++w) v += sm[(size_t)w * nc + c];
-        int n, m;
-        nm_tab(A.zc.knm, c, n, m);
-        v = mul_i(A.kappa * (2.0 * n + 1.0) * v);
+        if (LAP) {
+            v = __ldg(lsd + c) * v;
+        } else {
+            int n, m;
+            nm_tab(A.zc.knm, c, n, m);
+            v = mul_i(A.kappa * (2.0 * n + 1.0) * v);
+        }
         if (sing) op[c] += v;
         else op[c] = v;
     }
@@ -853,11 +863,9 @@ __device__ __forceinline__ cd cpow_int(cd x, int m) {
 // in global scratch for large orders), then (when it fits) the Dh table.
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
-                       cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl) {
+                       cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl,
+                       int nrhs, int nchunk) {
     extern __shared__ cd sm[];
-    int b = lo + blockIdx.x;
-    if (mode == 0 && A.leaf[b]) return;    // a leaf keeps its P2M expansion
-    int rhs = blockIdx.y;
     int Pm = max(Pi, Po), Pn = min(Pi, Po);
     int Ki = (Pi + 1) * (Pi + 1), Ko = (Po + 1) * (Po + 1), Km = (Pm + 1) * (Pm + 1);
     int NR = Pi + Po;                   // rows 0..NR
@@ -879,7 +887,7 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         // large orders: the coaxial work arrays live in this block's slice of
         // global scratch instead of shared memory
         size_t per = (size_t)(Pn + 1) * (NR + 1) + wsz;
-        sect = gscr + (((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * per;
+        sect = gscr + (size_t)blockIdx.x * per;
         cols = sect + (size_t)(Pn + 1) * (NR + 1);
         Dsm = (double*)(pwei + (2 * Pm + 1));
     }
@@ -889,6 +897,16 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         for (int64_t k = threadIdx.x; k < nd; k += blockDim.x) Dsm[k] = A.Dh[k];
         Dh = Dsm;
     }
+    // work items (destination box, rhs, list chunk), grid-stride: a block's
+    // global scratch slice is reused by its items
+    int64_t nitem = (int64_t)nb * nrhs * nchunk;
+    for (int64_t item = blockIdx.x; item < nitem; item += gridDim.x) {
+    int bx = (int)(item % nb);
+    int rhs = (int)((item / nb) % nrhs);
+    int zc = (int)(item / ((int64_t)nb * nrhs));
+    int b = lo + bx;
+    if (mode == 0 && A.leaf[b]) continue;    // a leaf keeps its P2M expansion
+    __syncthreads();
     for (int k = threadIdx.x; k < Ko; k += blockDim.x) acc[k] = cd{0, 0};
     int qa, qb;
     if (mode == 0) {
@@ -899,7 +917,7 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         qb = A.loff[b + 1];
         if (part) {
             // chunked List 2: this block takes entries [qa + z chunk, qa + (z+1) chunk)
-            qa += blockIdx.z * chunk;
+            qa += zc * chunk;
             qb = min(qb, qa + chunk);
         }
     } else {
@@ -1033,14 +1051,15 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     }
     __syncthreads();
     if (part) {
-        cd* o = part + (((size_t)blockIdx.z * gridDim.y + rhs) * nb + blockIdx.x) * Ko;
+        cd* o = part + (((size_t)zc * nrhs + rhs) * nb + bx) * Ko;
         for (int k = threadIdx.x; k < Ko; k += blockDim.x) o[k] = acc[k];
-        return;
+        continue;
     }
     cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
     for (int k = threadIdx.x; k < Ko; k += blockDim.x) {
         if (mode == 2) o[k] += acc[k];
         else o[k] = acc[k];
+    }
     }
 }
 
@@ -1307,7 +1326,7 @@ void helm3d_setup(cfmm_plan_s* P) {
     int maxP = 0;
     for (int l = S->l0; l < T.nlevels; ++l) maxP = std::max(maxP, S->Plev[l]);
     CFMM_REQUIRE(maxP <= kH3MaxP, CFMM_EUNSUPPORTED,
-                 "3D Helmholtz: expansion order above 63 at the top expansion level (raise top_level or eps)");
+                 "3D Helmholtz: expansion order above 57 at the top expansion level (raise top_level or eps)");
     S->maxP = maxP;
     S->tab = tables(maxP);
     S->dPlev.alloc(T.nlevels);
@@ -1398,7 +1417,7 @@ void helm3d_setup(cfmm_plan_s* P) {
         CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
-    for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp, (const void*)k_eval3h, (const void*)k_tr3h})
+    for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp<false>, (const void*)k_eval3h, (const void*)k_tr3h})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
 }
 
@@ -1454,8 +1473,9 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         CFMM_LAUNCHED();
         size_t smem = sizeof(cd) * (size_t)(kH3Threads / 32) * (PL + 1) * (PL + 1);
         dim3 g((unsigned)cnt, nrhs);
-        k_p2x3h_slp<<<g, kH3Threads, smem, st>>>(A, boxes, sing ? T.loff[3].get() : nullptr,
-                                                 sing ? T.lent[3].get() : nullptr, sing, roff, S->rad.get(), dst);
+        k_p2x3h_slp<false><<<g, kH3Threads, smem, st>>>(A, boxes, sing ? T.loff[3].get() : nullptr,
+                                                        sing ? T.lent[3].get() : nullptr, sing, roff, S->rad.get(),
+                                                        dst, nullptr);
         CFMM_LAUNCHED();
     };
     // (1) P2M, one launch per level (shared memory sized by that level's P)
@@ -1477,7 +1497,10 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                 TB->inv2n1.get(), TB->al.get(), TB->be.get(), TB->ibe.get(), TB->mu.get(), TB->nu.get(),
                 TB->knm.get(), P->kappa, T.cbeg.get(), T.cend.get(),
                 T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get(), S->qbox.get()};
-    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk) {
+    int nsm = 0;
+    CFMM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device));
+    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
+                         int chunk) {
         if (nb <= 0) return;
         size_t smem = tr3h_smem(Pi, Po, true);
         int dsm = 1;
@@ -1486,13 +1509,19 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             smem = tr3h_smem(Pi, Po, false);
             dsm = 0;
         }
+        int64_t nitem = (int64_t)nb * nrhs * nchunk, G = nitem;
         if (smem > (size_t)kH3Smem) {
+            // coaxial work arrays in global scratch: one slice per resident
+            // block, the blocks stride over the work items
             smem = tr3h_smem(Pi, Po, false, false);
-            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)nb * nrhs * nchunk);
+            int per_sm = 0;
+            CFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tr3h, kH3Threads, smem));
+            G = std::min<int64_t>(nitem, (int64_t)std::max(1, per_sm) * nsm);
+            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)G);
             gs = S->gscr.get();
         }
         CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Helmholtz translation exceeds shared memory");
-        dim3 g(nb, nrhs, nchunk);
+        dim3 g((unsigned)G);
         size_t Ko = (size_t)(Po + 1) * (Po + 1);
         cd* pp = nullptr;
         if (nchunk > 1) {
@@ -1520,8 +1549,8 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                                                            S->pre_fl.get());
             CFMM_LAUNCHED();
         }
-        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, kM2LChunk3, pp,
-                                            qfirst, S->pre_sc.get(), S->pre_fl.get());
+        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
+                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
             k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,
@@ -1533,15 +1562,20 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     // from an empty child range)
     for (int l = T.nlevels - 2; l >= S->l0; --l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp, 1);
+        launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp, 1, 1);
     }
     rec(3);
     // (4) M2L per level (overwrites L at levels >= l0)
     for (int l = S->l0; l < T.nlevels; ++l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        // long lists (the all-pairs top level) are split over several blocks
+        // long lists (the all-pairs top level) are split over several blocks,
+        // as far as the launch needs more blocks (many right-hand sides already
+        // give enough, and then no partials are written)
         int nchunk = S->l2max[l] > 2 * kM2LChunk3 ? (S->l2max[l] + kM2LChunk3 - 1) / kM2LChunk3 : 1;
-        launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc, nchunk);
+        int64_t want = (int64_t)16 * nsm, base = (int64_t)std::max(1, nb) * nrhs;
+        if (nchunk > 1 && base * nchunk > want) nchunk = (int)std::max<int64_t>(1, (want + base - 1) / base);
+        int chunk = nchunk > 1 ? (S->l2max[l] + nchunk - 1) / nchunk : std::max(1, S->l2max[l]);
+        launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc, nchunk, chunk);
     }
     rec(4);
     // (6) P2L, per level
@@ -1564,7 +1598,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     // (7) L2L
     for (int l = S->l0 + 1; l < T.nlevels; ++l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
-        launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc, 1);
+        launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc, 1, 1);
     }
     rec(6);
     // (3) P2P
@@ -1586,6 +1620,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
 // ---------------------------------------------------------------------------
 struct Lap3Tr {
     H3Tables* tab = nullptr;
+    int Pord = 0;
     std::vector<int> l2off, level_off;
     DevBuf<int> qbox;
     DevBuf<cd> sc, tt;
@@ -1608,7 +1643,29 @@ Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord) {
     CFMM_CUDA(cudaMemcpyAsync(L->qbox.get(), qb.data(), sizeof(int) * qb.size(), cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     CFMM_CUDA(cudaFuncSetAttribute((const void*)k_tr3l, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
+    CFMM_CUDA(cudaFuncSetAttribute((const void*)k_p2x3h_slp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kH3Smem));
+    L->Pord = Pord;
     return L;
+}
+
+bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                  const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs) {
+    size_t smem = sizeof(cd) * (size_t)(kH3Threads / 32) * (maxP + 1) * (maxP + 1);
+    if (smem > (size_t)kH3Smem || maxP > L->Pord) return false;
+    if (cnt <= 0) return true;
+    TreeDev& T = P->tree;
+    H3Tables* TB = L->tab;
+    ZCoef zc{TB->zA.get(), TB->zB.get(), TB->dg.get(), TB->s21.get(), TB->knm.get(),
+             TB->g3.get(), TB->gp.get(), TB->gm.get()};
+    Exp3hArgs A{P->xr.get(), P->xi.get(), nullptr, nullptr, P->n, sigma, nullptr, dstride, true, false,
+                T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(), dPlev, eoff, ncoef,
+                0.0, zc};
+    dim3 g((unsigned)cnt, nrhs);
+    k_p2x3h_slp<true><<<g, kH3Threads, smem, P->stream>>>(A, leaves, nullptr, nullptr, 0, nullptr, nullptr, out,
+                                                          TB->lsd.get());
+    CFMM_LAUNCHED();
+    return true;
 }
 
 void lap3_tr_destroy(Lap3Tr* L) { delete L; }

@@ -53,9 +53,16 @@ void helm3d_release(cfmm_plan_s* P);
 void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 int nterms_helm3d(int k, double eps, double kappa, double w);
 // 3D Laplace point-and-shoot translations (helm3d.cu, used by fmm3d.cu)
+// largest 3D Helmholtz expansion order: the translation kernel's work arrays
+// (4 (P+1)^2 + 10 P + 5 complex values) fill a block's 220 KB of shared memory
+constexpr int kMaxP3Top = 57;
 struct Lap3Tr;
 Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord);
 void lap3_tr_destroy(Lap3Tr* L);
+// single-layer 3D Laplace P2M over `leaves` (one column per lane); false when
+// the order does not fit the kernel (the caller then uses the general P2M)
+bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                  const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs);
 void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const int64_t* eoff, int64_t ncoef,
                     const cd* in, cd* out, int nrhs);
 

@@ -1234,14 +1234,15 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         if (top_level_opt > 0) {
             l0 = top_level_opt;
         } else if (helm) {
-            // tau = c_d ln(eps / 2^-52), c_2 = 1/4, c_3 = 1 (calibrated on the 3D
-            // surface workload); 3D also needs P_l <= 63 (translation kernel limit)
-            double tau = (dim == 2 ? 0.25 : 1.0) * std::log(P->eps / std::ldexp(1.0, -52));
+            // tau = c_d ln(eps / 2^-52), c_2 = 1, c_3 = 2 (calibrated on the 2D curve
+            // and 3D surface workloads); 3D also needs P_l <= kMaxP3Top (the
+            // translation kernel's work arrays fill a block's shared memory)
+            double tau = (dim == 2 ? 1.0 : 2.0) * std::log(P->eps / std::ldexp(1.0, -52));
             int maxl = P->tree.nlevels - 1;
             l0 = maxl < 1 ? 1 : maxl;
             bool found = false;
             auto p_fits = [&](int m) {
-                return dim != 3 || nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -m)) <= 63;
+                return dim != 3 || nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -m)) <= kMaxP3Top;
             };
             for (int m = 1; m <= maxl; ++m) {
                 if (!p_fits(m)) continue;
