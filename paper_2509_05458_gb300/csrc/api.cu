@@ -281,6 +281,20 @@ static void record(cfmm_plan_s* P, int i) {
     if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev[i], P->stream));
 }
 
+cudaStream_t near_fork(cfmm_plan_s* P) {
+    CFMM_CUDA(cudaEventRecord(P->ev_fork, P->stream));
+    CFMM_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev_p2p[0], P->side));
+    P->p2p_side = true;
+    return P->side;
+}
+
+void near_join(cfmm_plan_s* P) {
+    if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev_p2p[1], P->side));
+    CFMM_CUDA(cudaEventRecord(P->ev_join, P->side));
+    CFMM_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+}
+
 // the full apply on device buffers (densities [nrhs][ncomp][n], out [nrhs][n])
 static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     cudaStream_t st = P->stream;
@@ -293,6 +307,7 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     }
     cd* sg = P->slp ? P->dens_s.get() : nullptr;
     cd* ta = P->dlp ? P->dens_s.get() + (P->slp ? (int64_t)n * nrhs : 0) : nullptr;
+    P->p2p_side = false;
     record(P, 0);
     dim3 g((unsigned)((n + 255) / 256), nrhs);
     int comp = 0;
@@ -320,6 +335,12 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
             CFMM_CUDA(cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]));
             P->step_ms[i] = ms;
         }
+        if (P->p2p_side) {
+            // the near field ran beside the far field: its own duration
+            float ms = 0.f;
+            CFMM_CUDA(cudaEventElapsedTime(&ms, P->ev_p2p[0], P->ev_p2p[1]));
+            P->step_ms[6] = ms;
+        }
     }
 }
 
@@ -334,6 +355,14 @@ static void destroy_plan(cfmm_plan_s* P) {
     helm3d_release(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : P->ev_p2p)
+        if (e) cudaEventDestroy(e);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->side) {
+        cudaStreamSynchronize(P->side);
+        cudaStreamDestroy(P->side);
+    }
     delete P;
 }
 
@@ -408,6 +437,10 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         CFMM_CUDA(cudaGetDevice(&P->device));
         ensure_device_tables();
         for (auto& e : P->ev) CFMM_CUDA(cudaEventCreate(&e));
+        for (auto& e : P->ev_p2p) CFMM_CUDA(cudaEventCreate(&e));
+        CFMM_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+        CFMM_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+        CFMM_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
         Scratch& scr = plan_scratch();
         scr.rewind();
         size_t cnt = (size_t)n * dim;

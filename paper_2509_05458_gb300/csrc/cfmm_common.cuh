@@ -181,6 +181,7 @@ struct TreeDev {
     DevBuf<uint64_t> prefix;
     DevBuf<double> cen_re, cen_im;  // [nboxes][dim]
     DevBuf<int> loff[4];            // CSR offsets [nboxes+1]
+    std::vector<int> hloff[4];      // host copies of the offsets
     DevBuf<int> lent[4];            // CSR entries
     int64_t llen[4] = {0, 0, 0, 0};
     std::vector<int> leaf_boxes;    // host: box index of every leaf, Morton order
@@ -220,6 +221,12 @@ struct cfmm_plan_s {
     bool timing = false;
     double step_ms[9] = {0};
     cudaEvent_t ev[10] = {};
+    // near field (List 1) on a second stream, concurrent with the far field:
+    // fork after the permuted densities, join before the expansions are
+    // evaluated into the same output
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p2p[2] = {};
+    bool p2p_side = false;           // the last apply ran the near field on `side`
     // captured apply
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

@@ -62,6 +62,7 @@ struct Fmm2dState {
     // work lists
     std::vector<int> leaves_l0;            // leaves at level >= l0
     DevBuf<int> d_leaves_l0;
+    int maxP_leaf = 0;                     // largest order at a leaf level (P2M)
     int n_p2l = 0;                         // boxes with a non-empty List 4
     DevBuf<int> d_p2l_boxes;
     // Helmholtz M2L work split: chunks of at most kM2LChunk List-2 entries
@@ -115,19 +116,6 @@ __device__ void cyl_row(int kind, cd zeta, cd eta, double kappa, int P, cd* row)
         pos[m] = f * up;
         up = up * u;
         vp = vp * v;
-    }
-}
-
-// In place: row (holding T_m, m=-P-1..P+1) -> term_n at row[P - n], n = P..-P:
-//   term_n = s T_{-n} - (kappa/2)(nu T_{-n-1} - nut T_{-n+1}) t
-__device__ void cyl_terms(cd* row, int P, cd s, cd t, cd nu, cd nut, double kappa, bool slp, bool dlp) {
-    double hk = 0.5 * kappa;
-    for (int n = P; n >= -P; --n) {
-        int p = P - n;
-        cd v = {0.0, 0.0};
-        if (slp) v = s * row[p + 1];
-        if (dlp) v -= (hk * (nu * row[p] - nut * row[p + 2])) * t;
-        row[p] = v;
     }
 }
 
@@ -215,6 +203,7 @@ __global__ void k_point_to_exp(ExpArgs A, const int* __restrict__ boxes, const i
     int R = KER == CFMM_LAPLACE ? nc : nc + 2;
     cd* acc = sm;
     cd* rows = sm + nc;
+    cd* wts = rows + (size_t)chunk * R;        // Helmholtz: per source (s, -k/2 nu t, k/2 nu~ t)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) acc[c] = cd{0, 0};
     cd cen0 = {A.cre[2 * b], A.cim[2 * b]}, cen1 = {A.cre[2 * b + 1], A.cim[2 * b + 1]};
     int qa = loff ? loff[b] : 0, qb = loff ? loff[b + 1] : 1;
@@ -243,14 +232,32 @@ __global__ void k_point_to_exp(ExpArgs A, const int* __restrict__ boxes, const i
                 } else {
                     zeta_eta(cen0 - y0, cen1 - y1, z, e);   // D = c - y
                     cyl_row(sing ? 1 : 0, z, e, A.kappa, P, row);
-                    cyl_terms(row, P, s, t, nu, nut, A.kappa, A.slp, A.dlp);
+                    double hk = 0.5 * A.kappa;
+                    cd* w = wts + 3 * threadIdx.x;
+                    w[0] = s;
+                    w[1] = (-hk) * (nu * t);
+                    w[2] = hk * (nut * t);
                 }
             }
             __syncthreads();
             for (int c = threadIdx.x; c < nc; c += blockDim.x) {
                 cd a = acc[c];
-                int col = KER == CFMM_LAPLACE ? c : 2 * P - c;
-                for (int tt = 0; tt < cn; ++tt) a += rows[(size_t)tt * R + col];
+                if (KER == CFMM_LAPLACE) {
+                    for (int tt = 0; tt < cn; ++tt) a += rows[(size_t)tt * R + c];
+                } else {
+                    // coefficient n = c - P: s T_{-n} - (k/2)(nu T_{-n-1} - nu~ T_{-n+1}) t,
+                    // T_k at row index k + P + 1
+                    int i0 = 2 * P + 1 - c;
+                    if (A.dlp) {
+                        for (int tt = 0; tt < cn; ++tt) {
+                            const cd* r = rows + (size_t)tt * R + i0;
+                            const cd* w = wts + 3 * tt;
+                            a += w[0] * r[0] + w[1] * r[-1] + w[2] * r[1];
+                        }
+                    } else {
+                        for (int tt = 0; tt < cn; ++tt) a += wts[3 * tt] * rows[(size_t)tt * R + i0];
+                    }
+                }
                 acc[c] = a;
             }
         }
@@ -949,21 +956,26 @@ void fmm2d_setup(cfmm_plan_s* P) {
     P->ncoef = tot;
     S->exp_off.alloc(T.nboxes);
     CFMM_CUDA(cudaMemcpyAsync(S->exp_off.get(), off.data(), sizeof(int64_t) * T.nboxes, cudaMemcpyHostToDevice, st));
-    // leaves at level >= l0 (all leaves when the tree has more than one box)
-    std::vector<int> lvl(T.nboxes), leaf(T.nboxes);
-    CFMM_CUDA(cudaMemcpyAsync(lvl.data(), T.level.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
-    CFMM_CUDA(cudaMemcpyAsync(leaf.data(), T.leaf.get(), sizeof(int) * T.nboxes, cudaMemcpyDeviceToHost, st));
-    CFMM_CUDA(cudaStreamSynchronize(st));
-    for (int b : T.leaf_boxes)
-        if (lvl[b] >= S->l0) S->leaves_l0.push_back(b);
+    // leaves at level >= l0 (all leaves when the tree has more than one box);
+    // boxes are level-major, so a box's level follows from the level offsets
+    auto level_of = [&](int b) {
+        return (int)(std::upper_bound(T.level_off.begin(), T.level_off.end(), b) - T.level_off.begin()) - 1;
+    };
+    S->maxP_leaf = 0;
+    for (int b : T.leaf_boxes) {
+        int lb = level_of(b);
+        if (lb >= S->l0) {
+            S->leaves_l0.push_back(b);
+            S->maxP_leaf = std::max(S->maxP_leaf, S->Plev[lb]);
+        }
+    }
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
                               cudaMemcpyHostToDevice, st));
     // boxes that receive P2L contributions
     {
-        std::vector<int> l4(T.nboxes + 1), boxes;
-        CFMM_CUDA(cudaMemcpyAsync(l4.data(), T.loff[3].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost, st));
-        CFMM_CUDA(cudaStreamSynchronize(st));
+        const std::vector<int>& l4 = T.hloff[3];
+        std::vector<int> boxes;
         for (int b = T.level_off[S->l0]; b < T.nboxes; ++b)
             if (l4[b + 1] > l4[b]) boxes.push_back(b);
         S->n_p2l = (int)boxes.size();
@@ -983,14 +995,12 @@ void fmm2d_setup(cfmm_plan_s* P) {
                 bt[(size_t)n * (NB + 1) + k] = bt[(size_t)(n - 1) * (NB + 1) + k - 1] + (k <= n - 1 ? bt[(size_t)(n - 1) * (NB + 1) + k] : 0.0);
         }
         S->binom.alloc(bt.size());
+        // (a copy from pageable memory returns once the source is staged)
         CFMM_CUDA(cudaMemcpyAsync(S->binom.get(), bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaStreamSynchronize(st));
     }
     if (P->kernel == CFMM_HELMHOLTZ) {
         // M2L tables, level-major like List 2 itself
-        std::vector<int> loff(T.nboxes + 1);
-        CFMM_CUDA(cudaMemcpyAsync(loff.data(), T.loff[1].get(), sizeof(int) * (T.nboxes + 1), cudaMemcpyDeviceToHost, st));
-        CFMM_CUDA(cudaStreamSynchronize(st));
+        const std::vector<int>& loff = T.hloff[1];
         S->m2l_base.assign(T.nlevels, 0);
         S->m2l_q0.assign(T.nlevels, 0);
         int64_t base = 0;
@@ -1018,7 +1028,6 @@ void fmm2d_setup(cfmm_plan_s* P) {
                                                        S->d_m2l_base.get(), S->d_m2l_q0.get(), T.cen_re.get(),
                                                        T.cen_im.get(), P->kappa, S->t_m2l.get(), qf);
             CFMM_LAUNCHED();
-            CFMM_CUDA(cudaStreamSynchronize(st));
         }
         // List-2 chunks per box (levels >= l0)
         {
@@ -1054,7 +1063,6 @@ void fmm2d_setup(cfmm_plan_s* P) {
                 CFMM_CUDA(cudaMemcpyAsync(S->chunk_q1.get(), c1v.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
             }
             CFMM_CUDA(cudaMemcpyAsync(S->box_chunk0.get(), bc0.data(), sizeof(int) * (T.nboxes + 1), cudaMemcpyHostToDevice, st));
-            CFMM_CUDA(cudaStreamSynchronize(st));
         }
         // shift tables for boxes at levels > l0
         std::vector<int64_t> so(T.nboxes, -1);
@@ -1074,7 +1082,6 @@ void fmm2d_setup(cfmm_plan_s* P) {
                                                            P->kappa, S->t_shift.get());
             CFMM_LAUNCHED();
         }
-        CFMM_CUDA(cudaStreamSynchronize(st));
     }
     for (auto f : {(const void*)k_point_to_exp<CFMM_LAPLACE>, (const void*)k_point_to_exp<CFMM_HELMHOLTZ>,
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,
@@ -1112,11 +1119,15 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
               P->kappa, T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(),
               S->dPlev.get(), S->exp_off.get(), S->ncoef};
     int maxP = S->maxP;
-    // (1) P2M
+    // (3) P2P over List 1 (writes u) on the side stream, beside the far field
+    launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), P->precision == CFMM_MIXED);
+    // (1) P2M (shared memory sized by the leaves' orders)
     {
-        int R = KER == CFMM_LAPLACE ? 2 * maxP + 1 : 2 * maxP + 3;
-        int chunk = std::max(1, std::min(kExpThreads, (int)((96 * 1024) / (R * sizeof(cd)))));
-        size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)chunk * R);
+        int PL = S->maxP_leaf;
+        int R = KER == CFMM_LAPLACE ? 2 * PL + 1 : 2 * PL + 3;
+        int chunk = std::max(1, std::min(kExpThreads, (int)((96 * 1024) / ((R + 3) * sizeof(cd)))));
+        size_t smem = sizeof(cd) * ((size_t)(2 * PL + 1) + (size_t)chunk * (R + 3));
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
         if (g.x) {
             k_point_to_exp<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), nullptr, nullptr, 0, mp, chunk);
@@ -1179,8 +1190,8 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     // (6) P2L over List 4
     {
         int R = KER == CFMM_LAPLACE ? 2 * maxP + 1 : 2 * maxP + 3;
-        int chunk = std::max(1, std::min(kExpThreads, (int)((96 * 1024) / (R * sizeof(cd)))));
-        size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)chunk * R);
+        int chunk = std::max(1, std::min(kExpThreads, (int)((96 * 1024) / ((R + 3) * sizeof(cd)))));
+        size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)chunk * (R + 3));
         if (S->n_p2l > 0) {
             dim3 g(S->n_p2l, nrhs);
             k_point_to_exp<KER><<<g, kExpThreads, smem, st>>>(A, S->d_p2l_boxes.get(), T.loff[3].get(),
@@ -1199,10 +1210,8 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
         CFMM_LAUNCHED();
     }
     rec(6);
-    // (3) P2P over List 1 (writes u)
-    launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, st, P->precision == CFMM_MIXED);
     rec(7);
+    near_join(P);   // the near field has written u
     // (5) M2P and (8) L2P (add to u)
     {
         size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)kExpThreads * (maxP + 2));

@@ -1452,6 +1452,9 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                 T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(), S->dPlev.get(),
                 S->exp_off.get(), S->ncoef, P->kappa, zc};
     int maxP = S->maxP;
+    // (3) P2P (writes u) on the side stream, beside the far field
+    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     auto p2x_smem = [&](int PL, int& chunk) {
         size_t nc = (size_t)(PL + 1) * (PL + 1);
         size_t per = nc + (PL + 2) + 6;
@@ -1601,10 +1604,8 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         launch_tr(2, lo, nb, S->Plev[l - 1], S->Plev[l], 0, lc, lc, 1, 1);
     }
     rec(6);
-    // (3) P2P
-    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, st, mixed);
     rec(7);
+    near_join(P);   // the near field has written u
     // (5) M2P, (8) L2P
     {
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);

@@ -654,10 +654,14 @@ static void balance(LeafArrays& L, const uint64_t* keys, int dim, int B, int k, 
 // ---------------------------------------------------------------------------
 // boxes from leaves
 // ---------------------------------------------------------------------------
-__global__ void k_box_flags(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre, int dim,
-                            int m, int* __restrict__ head) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nl) return;
+// head flags of every level at once: entry m nl + i says whether leaf i
+// starts a box of level m (thread per (level, leaf))
+__global__ void k_box_flags(int nl, int nlev, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                            int dim, int* __restrict__ head) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)nl * nlev) return;
+    int m = (int)(k / nl), i = (int)(k - (int64_t)m * nl);
+    head += (int64_t)m * nl;
     int l = lev[i];
     bool q = l >= m;
     bool h = false;
@@ -672,18 +676,22 @@ __global__ void k_box_flags(int nl, const int* __restrict__ lev, const uint64_t*
     head[i] = h ? 1 : 0;
 }
 
-__global__ void k_box_emit(int nl, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
-                           const int* __restrict__ st, const int* __restrict__ en, int dim, int m, int base,
+// boxes of every level at once (thread per (level, leaf)); idx is the exclusive
+// scan of all levels' head flags, level-major, so it counts the boxes of the
+// coarser levels too and is the box index itself
+__global__ void k_box_emit(int nl, int nlev, const int* __restrict__ lev, const uint64_t* __restrict__ pre,
+                           const int* __restrict__ st, const int* __restrict__ en, int dim,
                            const int* __restrict__ head, const int* __restrict__ idx,
                            int* __restrict__ blevel, uint64_t* __restrict__ bpre, int* __restrict__ bst,
                            int* __restrict__ ben, int* __restrict__ bleaf, int* __restrict__ leaf_box) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nl) return;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)nl * nlev) return;
+    int m = (int)(k / nl), i = (int)(k - (int64_t)m * nl);
     int l = lev[i];
     if (l < m) return;
     uint64_t pm = pre[i] >> (dim * (l - m));
-    int b = base + idx[i] + head[i] - 1;
-    if (head[i]) {
+    int b = idx[k] + head[k] - 1;
+    if (head[k]) {
         blevel[b] = m;
         bpre[b] = pm;
         bst[b] = st[i];
@@ -979,6 +987,7 @@ __global__ void k_p2p_work(int nb, const int* __restrict__ off, const int* __res
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
+// boxes at levels <= m (cumulative over the level-major scan)
 __global__ void k_level_totals(int nlev, int nl, const int* __restrict__ head, const int* __restrict__ idx,
                                int* __restrict__ tot) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -996,20 +1005,19 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
     int* idx = scr.take_n<int>((size_t)nlev * nl);
     int* leaf_box = scr.take_n<int>(nl);
     int* tot = scr.take_n<int>(nlev);
-    // head flags and their scans for every level, then all totals in one read
-    for (int m = 0; m <= maxl; ++m) {
-        k_box_flags<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, dim, m, head + (size_t)m * nl);
-        CFMM_LAUNCHED();
-        scan_exclusive_async(head + (size_t)m * nl, idx + (size_t)m * nl, nl, st);
-    }
+    // head flags of every level, one level-major scan, then all totals in one read
+    int64_t nall = (int64_t)nlev * nl;
+    k_box_flags<<<(unsigned)((nall + 255) / 256), 256, 0, st>>>(nl, nlev, L.lev, L.pre, dim, head);
+    CFMM_LAUNCHED();
+    scan_exclusive_async(head, idx, (int)nall, st);
     k_level_totals<<<blocks_for(nlev, 64), 64, 0, st>>>(nlev, nl, head, idx, tot);
     CFMM_LAUNCHED();
-    std::vector<int> counts(nlev);
-    CFMM_CUDA(cudaMemcpyAsync(counts.data(), tot, sizeof(int) * nlev, cudaMemcpyDeviceToHost, st));
+    std::vector<int> cum(nlev);
+    CFMM_CUDA(cudaMemcpyAsync(cum.data(), tot, sizeof(int) * nlev, cudaMemcpyDeviceToHost, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     T.nlevels = nlev;
     T.level_off.assign(T.nlevels + 1, 0);
-    for (int m = 0; m <= maxl; ++m) T.level_off[m + 1] = T.level_off[m] + counts[m];
+    for (int m = 0; m <= maxl; ++m) T.level_off[m + 1] = cum[m];
     T.nboxes = T.level_off[T.nlevels];
     T.nleaves = nl;
     int nb = T.nboxes;
@@ -1021,13 +1029,10 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
     T.parent.alloc(nb);
     T.cbeg.alloc(nb);
     T.cend.alloc(nb);
-    for (int m = 0; m <= maxl; ++m) {
-        k_box_emit<<<blocks_for(nl, 256), 256, 0, st>>>(nl, L.lev, L.pre, L.st, L.en, dim, m, T.level_off[m],
-                                                       head + (size_t)m * nl, idx + (size_t)m * nl, T.level.get(),
-                                                       T.prefix.get(), T.start.get(), T.end.get(), T.leaf.get(),
-                                                       leaf_box);
-        CFMM_LAUNCHED();
-    }
+    k_box_emit<<<(unsigned)((nall + 255) / 256), 256, 0, st>>>(nl, nlev, L.lev, L.pre, L.st, L.en, dim, head, idx,
+                                                               T.level.get(), T.prefix.get(), T.start.get(),
+                                                               T.end.get(), T.leaf.get(), leaf_box);
+    CFMM_LAUNCHED();
     T.d_level_off.alloc(T.nlevels + 1);
     CFMM_CUDA(cudaMemcpyAsync(T.d_level_off.get(), T.level_off.data(), sizeof(int) * (T.nlevels + 1),
                               cudaMemcpyHostToDevice, st));
@@ -1099,11 +1104,17 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
         T.loff[w].alloc(nb + 1);
         scan_exclusive_async(cw, T.loff[w].get(), nb + 1, st);   // loff[nb] = total
     }
+    // the four offset arrays come back to the host in one read (the setup of
+    // the expansions walks them there)
     int tot[4];
-    for (int w = 0; w < 4; ++w)
-        CFMM_CUDA(cudaMemcpyAsync(&tot[w], T.loff[w].get() + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int w = 0; w < 4; ++w) {
+        T.hloff[w].resize(nb + 1);
+        CFMM_CUDA(cudaMemcpyAsync(T.hloff[w].data(), T.loff[w].get(), sizeof(int) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, st));
+    }
     CFMM_CUDA(cudaStreamSynchronize(st));
     for (int w = 0; w < 4; ++w) {
+        tot[w] = T.hloff[w][nb];
         CFMM_REQUIRE(tot[w] >= 0, CFMM_EUNSUPPORTED, "interaction list longer than 2^31 entries");
         T.llen[w] = tot[w];
         T.lent[w].alloc(tot[w] > 0 ? tot[w] : 1);
@@ -1260,7 +1271,16 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
                 l0 = std::max(l0, m);
             }
         }
-        if (l0 > 1) {
+        // boxes are stored level-major, so the leaf with the smallest box index
+        // is the coarsest; when no leaf lies above l0 the forced refinement
+        // and the re-balancing change nothing and are skipped
+        int min_leaf_level = P->tree.nlevels;
+        if (!P->tree.leaf_boxes.empty()) {
+            int bmin = *std::min_element(P->tree.leaf_boxes.begin(), P->tree.leaf_boxes.end());
+            min_leaf_level = (int)(std::upper_bound(P->tree.level_off.begin(), P->tree.level_off.end(), bmin) -
+                                   P->tree.level_off.begin()) - 1;
+        }
+        if (l0 > 1 && min_leaf_level < l0) {
             refine_onepass(L, P->keys.get(), n, dim, B, Ns, l0, true, st);
             balance(L, P->keys.get(), dim, B, P->sep, st);
             build_boxes(P, L, st);
