@@ -726,6 +726,8 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serve: requests in flight")
     ap.add_argument("--n", type=int, default=0,
                     help="override the point count (small cases for profiler captures; not a bench line)")
+    ap.add_argument("--sep", type=int, default=0, help="override the separation k (parameter sweeps)")
+    ap.add_argument("--leaf", type=int, default=0, help="override the leaf size of both passes (parameter sweeps)")
     args = ap.parse_args()
     if args.workload == "helm3d":
         globals().update(W3D)
@@ -735,6 +737,10 @@ def main():
         globals().update(W4)
     if args.n > 0:
         globals()["N_POINTS"] = args.n
+    if args.sep > 0:
+        globals()["SEP"] = args.sep
+    if args.leaf > 0:
+        globals()["LEAF"] = globals()["LEAF_FP64"] = args.leaf
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))
         args.steps = max(1, min(args.steps, 2))

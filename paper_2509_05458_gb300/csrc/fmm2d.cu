@@ -58,6 +58,11 @@ struct Fmm2dState {
     DevBuf<int64_t> d_m2l_base;
     DevBuf<int> d_m2l_q0;
     DevBuf<cd> t_shift;                    // per child box: G_j(c_parent - c_child), j = -(Pc+Pp)..(Pc+Pp)
+    // Helmholtz: per point, the regular row T_m(c - y), m = -P-1..P+1 (P of
+    // the point's leaf, index m + P + 1, stride RL), c its leaf's centre; P2M
+    // of the leaf and L2P at the point both use it (geometry only)
+    DevBuf<cd> lrow;
+    int RL = 0;
     DevBuf<int64_t> shift_off;             // per box, -1 when none
     // work lists
     std::vector<int> leaves_l0;            // leaves at level >= l0
@@ -116,6 +121,24 @@ __device__ void cyl_row(int kind, cd zeta, cd eta, double kappa, int P, cd* row)
         pos[m] = f * up;
         up = up * u;
         vp = vp * v;
+    }
+}
+
+// Regular rows of every point about its leaf's centre (plan time): block per
+// leaf, thread per point.
+__global__ void k_leaf_rows(const int* __restrict__ leaves, const int* __restrict__ blevel,
+                            const int* __restrict__ bst, const int* __restrict__ ben, const int* __restrict__ Plev,
+                            const double* __restrict__ xr, const double* __restrict__ xi, int64_t n,
+                            const double* __restrict__ cre, const double* __restrict__ cim, double kappa, int RL,
+                            cd* __restrict__ lrow) {
+    int b = leaves[blockIdx.x];
+    int P = Plev[blevel[b]];
+    cd cen0 = {cre[2 * b], cim[2 * b]}, cen1 = {cre[2 * b + 1], cim[2 * b + 1]};
+    for (int j = bst[b] + threadIdx.x; j < ben[b]; j += blockDim.x) {
+        cd y0 = {xr[j], xi[j]}, y1 = {xr[n + j], xi[n + j]};
+        cd z, e;
+        zeta_eta(cen0 - y0, cen1 - y1, z, e);   // D = c - y
+        cyl_row(0, z, e, kappa, P, lrow + (int64_t)j * RL);
     }
 }
 
@@ -194,7 +217,8 @@ __device__ void lap_terms(bool sing, cd zeta, cd eta, cd s, cd t, cd nu, cd nut,
 // in (P2M) out[rhs][eoff[b] + c].
 template <int KER>
 __global__ void k_point_to_exp(ExpArgs A, const int* __restrict__ boxes, const int* __restrict__ loff,
-                               const int* __restrict__ lent, int sing, cd* __restrict__ out, int chunk) {
+                               const int* __restrict__ lent, int sing, cd* __restrict__ out, int chunk,
+                               const cd* __restrict__ lrow, int RL) {
     extern __shared__ cd sm[];
     int b = boxes[blockIdx.x];
     int rhs = blockIdx.y;
@@ -230,8 +254,14 @@ __global__ void k_point_to_exp(ExpArgs A, const int* __restrict__ boxes, const i
                     zeta_eta(y0 - cen0, y1 - cen1, z, e);   // d = y - c
                     lap_terms(sing != 0, z, e, s, t, nu, nut, P, A.slp, A.dlp, row);
                 } else {
-                    zeta_eta(cen0 - y0, cen1 - y1, z, e);   // D = c - y
-                    cyl_row(sing ? 1 : 0, z, e, A.kappa, P, row);
+                    if (lrow && !sing) {
+                        // the plan's row of this point about its own leaf (this box)
+                        const cd* src = lrow + j * RL;
+                        for (int q = 0; q < R; ++q) row[q] = src[q];
+                    } else {
+                        zeta_eta(cen0 - y0, cen1 - y1, z, e);   // D = c - y
+                        cyl_row(sing ? 1 : 0, z, e, A.kappa, P, row);
+                    }
                     double hk = 0.5 * A.kappa;
                     cd* w = wts + 3 * threadIdx.x;
                     w[0] = s;
@@ -660,7 +690,7 @@ __global__ void k_m2l_reduce(int lo, int nbl, const int* __restrict__ box_chunk0
 template <int KER>
 __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                        const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
-                       cd* __restrict__ u, int maxP) {
+                       cd* __restrict__ u, int maxP, const cd* __restrict__ lrow, int RL) {
     extern __shared__ cd sm[];
     int b = leaves[blockIdx.x];
     int rhs = blockIdx.y;
@@ -733,6 +763,18 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
                     acc += coef[nn] * zp + coef[P + nn] * ep;
                     zp = zp * z;
                     ep = ep * e;
+                }
+            } else if (lrow) {
+                // T_k(x - c) = (-1)^k T_k(c - x), the plan's row of this point
+                const cd* t = lrow + (int64_t)i * RL + (P + 1);
+                acc += coef[P] * t[0];
+                for (int nn = 1; nn <= P; ++nn) {
+                    cd tp = t[nn], tm = t[-nn];
+                    if (nn & 1) {
+                        tp = -tp;
+                        tm = -tm;
+                    }
+                    acc += coef[P + nn] * tp + coef[P - nn] * tm;
                 }
             } else {
                 cd* row = rows + (size_t)threadIdx.x * (maxP + 2);
@@ -972,6 +1014,14 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
                               cudaMemcpyHostToDevice, st));
+    if (P->kernel == CFMM_HELMHOLTZ && !S->leaves_l0.empty()) {
+        S->RL = 2 * S->maxP_leaf + 3;
+        S->lrow.alloc((size_t)P->n * S->RL);
+        k_leaf_rows<<<(unsigned)S->leaves_l0.size(), 64, 0, st>>>(
+            S->d_leaves_l0.get(), T.level.get(), T.start.get(), T.end.get(), S->dPlev.get(), P->xr.get(),
+            P->xi.get(), P->n, T.cen_re.get(), T.cen_im.get(), P->kappa, S->RL, S->lrow.get());
+        CFMM_LAUNCHED();
+    }
     // boxes that receive P2L contributions
     {
         const std::vector<int>& l4 = T.hloff[3];
@@ -1130,7 +1180,8 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
         size_t smem = sizeof(cd) * ((size_t)(2 * PL + 1) + (size_t)chunk * (R + 3));
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
         if (g.x) {
-            k_point_to_exp<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), nullptr, nullptr, 0, mp, chunk);
+            k_point_to_exp<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), nullptr, nullptr, 0, mp, chunk,
+                                                             S->lrow.get(), S->RL);
             CFMM_LAUNCHED();
         }
     }
@@ -1195,7 +1246,7 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
         if (S->n_p2l > 0) {
             dim3 g(S->n_p2l, nrhs);
             k_point_to_exp<KER><<<g, kExpThreads, smem, st>>>(A, S->d_p2l_boxes.get(), T.loff[3].get(),
-                                                             T.lent[3].get(), 1, lc, chunk);
+                                                             T.lent[3].get(), 1, lc, chunk, nullptr, 0);
             CFMM_LAUNCHED();
         }
     }
@@ -1214,10 +1265,11 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     near_join(P);   // the near field has written u
     // (5) M2P and (8) L2P (add to u)
     {
-        size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)kExpThreads * (maxP + 2));
+        // with the plan's rows, L2P needs no per-thread row space
+        size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (S->lrow.get() ? 0 : (size_t)kExpThreads * (maxP + 2)));
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
         k_eval<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc,
-                                                 u, maxP);
+                                                 u, maxP, S->lrow.get(), S->RL);
         CFMM_LAUNCHED();
     }
     rec(8);
