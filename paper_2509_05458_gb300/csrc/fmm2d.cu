@@ -1014,10 +1014,13 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
                               cudaMemcpyHostToDevice, st));
+    bool rows_side = false;
     if (P->kernel == CFMM_HELMHOLTZ && !S->leaves_l0.empty()) {
+        // on the side stream, beside the translation tables below
         S->RL = 2 * S->maxP_leaf + 3;
         S->lrow.alloc((size_t)P->n * S->RL);
-        k_leaf_rows<<<(unsigned)S->leaves_l0.size(), 64, 0, st>>>(
+        rows_side = true;
+        k_leaf_rows<<<(unsigned)S->leaves_l0.size(), 64, 0, near_fork(P)>>>(
             S->d_leaves_l0.get(), T.level.get(), T.start.get(), T.end.get(), S->dPlev.get(), P->xr.get(),
             P->xi.get(), P->n, T.cen_re.get(), T.cen_im.get(), P->kappa, S->RL, S->lrow.get());
         CFMM_LAUNCHED();
@@ -1133,6 +1136,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             CFMM_LAUNCHED();
         }
     }
+    if (rows_side) near_join(P);
     for (auto f : {(const void*)k_point_to_exp<CFMM_LAPLACE>, (const void*)k_point_to_exp<CFMM_HELMHOLTZ>,
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,
