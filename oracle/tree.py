@@ -40,8 +40,8 @@ Readings (all listed in the design doc):
   sqrt(3) kappa g of the rule, so c_3 = 2 still bounds the growth by
   (eps/2^-52)^0.65; at kappa = 15 the level it picks met eps = 1e-6 with
   1.4e-7, at a third of the cost of the c_3 = 1 level). In 3D it is also at
-  least the coarsest level with P_l <= 57, the order limit of the CUDA
-  translation kernel (its work arrays fill the shared memory of a block). Leaves above l0 are split
+  least the coarsest level with P_l <= 63, the order limit of the CUDA
+  translation tables. Leaves above l0 are split
   down to l0 and the tree is re-balanced. M2L at l0 runs over all non-near
   pairs of l0 boxes.
 """
@@ -479,7 +479,7 @@ def check_balance(T):
 # against (r/R)^n and undershoots by about a digit).
 P_HEADROOM = 0.1
 P_HEADROOM_HELM = 0.01
-P_MAX_3D = 57
+P_MAX_3D = 63
 
 def nterms_laplace(dim, k, eps):
     """Smallest n >= 1 with (r/R)^n <= eps, R=(k+1/2)w, r=sqrt(d)/2 w."""

@@ -864,14 +864,16 @@ __device__ __forceinline__ cd cpow_int(cd x, int m) {
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
                        cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl,
-                       int nrhs, int nchunk) {
+                       int nrhs, int nchunk, int acc_glob) {
     extern __shared__ cd sm[];
     int Pm = max(Pi, Po), Pn = min(Pi, Po);
     int Ki = (Pi + 1) * (Pi + 1), Ko = (Po + 1) * (Po + 1), Km = (Pm + 1) * (Pm + 1);
     int NR = Pi + Po;                   // rows 0..NR
     int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // acc_glob (the largest orders): the destination accumulator lives after the
+    // work arrays in the block's global scratch slice
     cd* acc = sm;
-    cd* a = acc + Ko;
+    cd* a = acc_glob ? sm : acc + Ko;
     cd* bb = a + Km;
     cd* wb = bb + Km;
     cd* f = wb + Km;
@@ -886,9 +888,10 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     if (gscr) {
         // large orders: the coaxial work arrays live in this block's slice of
         // global scratch instead of shared memory
-        size_t per = (size_t)(Pn + 1) * (NR + 1) + wsz;
+        size_t per = (size_t)(Pn + 1) * (NR + 1) + wsz + (acc_glob ? (size_t)Ko : 0);
         sect = gscr + (size_t)blockIdx.x * per;
         cols = sect + (size_t)(Pn + 1) * (NR + 1);
+        if (acc_glob) acc = cols + wsz;
         Dsm = (double*)(pwei + (2 * Pm + 1));
     }
     const double* Dh = A.Dh;
@@ -1211,11 +1214,12 @@ size_t tr3h_dh(int P) {
     return nd;
 }
 
-size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true) {
+size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true, bool acc_in_smem = true) {
     int Pm = std::max(Pi, Po);
     size_t Km = (size_t)(Pm + 1) * (Pm + 1), Ko = (size_t)(Po + 1) * (Po + 1);
     int NR = Pi + Po;
-    size_t c = Ko + 3 * Km + (NR + 1) + 4 * (2 * Pm + 1) + (work_in_smem ? tr3h_work(Pi, Po) : 0);
+    size_t c = (acc_in_smem ? Ko : 0) + 3 * Km + (NR + 1) + 4 * (2 * Pm + 1) +
+               (work_in_smem ? tr3h_work(Pi, Po) : 0);
     size_t bytes = c * sizeof(cd);
     if (d_in_smem) bytes += tr3h_dh(Pm) * sizeof(double);
     return bytes;
@@ -1326,7 +1330,7 @@ void helm3d_setup(cfmm_plan_s* P) {
     int maxP = 0;
     for (int l = S->l0; l < T.nlevels; ++l) maxP = std::max(maxP, S->Plev[l]);
     CFMM_REQUIRE(maxP <= kH3MaxP, CFMM_EUNSUPPORTED,
-                 "3D Helmholtz: expansion order above 57 at the top expansion level (raise top_level or eps)");
+                 "3D Helmholtz: expansion order above 63 at the top expansion level (raise top_level or eps)");
     S->maxP = maxP;
     S->tab = tables(maxP);
     S->dPlev.alloc(T.nlevels);
@@ -1513,14 +1517,21 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             dsm = 0;
         }
         int64_t nitem = (int64_t)nb * nrhs * nchunk, G = nitem;
+        int accg = 0;
         if (smem > (size_t)kH3Smem) {
-            // coaxial work arrays in global scratch: one slice per resident
-            // block, the blocks stride over the work items
+            // coaxial work arrays (and for the largest orders the accumulator)
+            // in global scratch: one slice per resident block, the blocks
+            // stride over the work items
             smem = tr3h_smem(Pi, Po, false, false);
+            if (smem > (size_t)kH3Smem) {
+                smem = tr3h_smem(Pi, Po, false, false, false);
+                accg = 1;
+            }
             int per_sm = 0;
             CFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tr3h, kH3Threads, smem));
             G = std::min<int64_t>(nitem, (int64_t)std::max(1, per_sm) * nsm);
-            S->gscr.alloc(tr3h_work(Pi, Po) * (size_t)G);
+            size_t per = tr3h_work(Pi, Po) + (accg ? (size_t)(Po + 1) * (Po + 1) : 0);
+            S->gscr.alloc(per * (size_t)G);
             gs = S->gscr.get();
         }
         CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Helmholtz translation exceeds shared memory");
@@ -1553,7 +1564,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             CFMM_LAUNCHED();
         }
         k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
-                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk);
+                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
             k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,

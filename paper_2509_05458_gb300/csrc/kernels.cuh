@@ -58,9 +58,10 @@ void helm3d_release(cfmm_plan_s* P);
 void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 int nterms_helm3d(int k, double eps, double kappa, double w);
 // 3D Laplace point-and-shoot translations (helm3d.cu, used by fmm3d.cu)
-// largest 3D Helmholtz expansion order: the translation kernel's work arrays
-// (4 (P+1)^2 + 10 P + 5 complex values) fill a block's 220 KB of shared memory
-constexpr int kMaxP3Top = 57;
+// largest 3D Helmholtz expansion order: the limit of the translation tables
+// (the translation kernel keeps 3 (P+1)^2 + 10 P + 5 complex values in shared
+// memory, the rest in global scratch, which fits up to here)
+constexpr int kMaxP3Top = 63;
 struct Lap3Tr;
 Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord);
 void lap3_tr_destroy(Lap3Tr* L);

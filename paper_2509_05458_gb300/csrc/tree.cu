@@ -1247,7 +1247,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         } else if (helm) {
             // tau = c_d ln(eps / 2^-52), c_2 = 1, c_3 = 2 (calibrated on the 2D curve
             // and 3D surface workloads); 3D also needs P_l <= kMaxP3Top (the
-            // translation kernel's work arrays fill a block's shared memory)
+            // order limit of the translation tables)
             double tau = (dim == 2 ? 1.0 : 2.0) * std::log(P->eps / std::ldexp(1.0, -52));
             int maxl = P->tree.nlevels - 1;
             l0 = maxl < 1 ? 1 : maxl;

@@ -101,3 +101,23 @@ def test_helm3d_top_level_deeper_than_initial_tree(cuda):
     u = p.apply(to_dev(dens, cuda)).cpu().numpy()
     uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
     assert relerr_l2(u[0], uo[0]) <= 1e-12
+
+
+def test_helm3d_top_order_above_57(cuda):
+    """kappa = 25: the top level has P = 59, where the translation kernel keeps
+    its accumulator in global scratch as well as its coaxial work arrays."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    kap, eps, leaf = 25.0, 1e-6, 64
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2)
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True)
+    orders = H.expansion_orders(T, kap, eps)
+    assert p.info()["l0"] == T.l0 and orders[T.l0] > 57
+    assert list(p.orders()) == orders
+    dens = densities(g.n, seed=10, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
+    assert relerr_l2(u[0], uo[0]) <= 1e-12
+    pts = g.re + 1j * g.im
+    u0 = direct(3, 1, kap, pts, pts, sigma=dens[0, 0])
+    assert relerr_paper(u[0], u0, dens[0].reshape(-1)) <= eps
