@@ -32,6 +32,11 @@ CFMM_HD cd operator*(cd a, cd b) { return cd{a.x * b.x - a.y * b.y, a.x * b.y + 
 CFMM_HD cd operator*(double s, cd a) { return cd{s * a.x, s * a.y}; }
 CFMM_HD cd operator*(cd a, double s) { return cd{s * a.x, s * a.y}; }
 CFMM_HD cd& operator+=(cd& a, cd b) { a.x += b.x; a.y += b.y; return a; }
+// acc + a b as four fused multiply-adds (the operators above cost two more
+// FP64 instructions: the product is rounded before it is added)
+CFMM_HD cd cmac(cd acc, cd a, cd b) {
+    return cd{fma(-a.y, b.y, fma(a.x, b.x, acc.x)), fma(a.y, b.x, fma(a.x, b.y, acc.y))};
+}
 CFMM_HD cd& operator-=(cd& a, cd b) { a.x -= b.x; a.y -= b.y; return a; }
 CFMM_HD double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
 CFMM_HD cd conjg(cd a) { return cd{a.x, -a.y}; }

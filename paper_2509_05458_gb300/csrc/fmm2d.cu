@@ -282,10 +282,10 @@ __global__ void k_point_to_exp(ExpArgs A, const int* __restrict__ boxes, const i
                         for (int tt = 0; tt < cn; ++tt) {
                             const cd* r = rows + (size_t)tt * R + i0;
                             const cd* w = wts + 3 * tt;
-                            a += w[0] * r[0] + w[1] * r[-1] + w[2] * r[1];
+                            a = cmac(cmac(cmac(a, w[0], r[0]), w[1], r[-1]), w[2], r[1]);
                         }
                     } else {
-                        for (int tt = 0; tt < cn; ++tt) a += wts[3 * tt] * rows[(size_t)tt * R + i0];
+                        for (int tt = 0; tt < cn; ++tt) a = cmac(a, wts[3 * tt], rows[(size_t)tt * R + i0]);
                     }
                 }
                 acc[c] = a;
@@ -380,7 +380,7 @@ __global__ void k_m2m(TransArgs T, int lo, const cd* __restrict__ mp_in, cd* __r
             } else {
                 int m = c - Pp;
                 int off = Pc + Pp;
-                for (int nn = -Pc; nn <= Pc; ++nn) a += pw[nn - m + off] * src[nn + Pc];
+                for (int nn = -Pc; nn <= Pc; ++nn) a = cmac(a, pw[nn - m + off], src[nn + Pc]);
             }
             acc[c] = a;
         }
@@ -449,7 +449,7 @@ __global__ void k_l2l(TransArgs T, int lo, cd* __restrict__ loc) {
         } else {
             int m = c - Pc;
             int off = Pc + Pp;
-            for (int nn = -Pp; nn <= Pp; ++nn) a += pw[nn - m + off] * src[nn + Pp];
+            for (int nn = -Pp; nn <= Pp; ++nn) a = cmac(a, pw[nn - m + off], src[nn + Pp]);
         }
         o[c] += a;
     }
@@ -546,7 +546,7 @@ __global__ void k_m2l(M2LArgs A, int first_box, const cd* __restrict__ mp, cd* _
                 }
             } else {
                 int j = c - P;
-                for (int nn = -P; nn <= P; ++nn) a += tb[nn - j + 2 * P] * src[nn + P];
+                for (int nn = -P; nn <= P; ++nn) a = cmac(a, tb[nn - j + 2 * P], src[nn + P]);
             }
             acc[c] = a;
         }
@@ -654,7 +654,7 @@ __global__ void k_m2l_chunk(M2LArgs A, int ch0, const int* __restrict__ chunk_bo
             const cd* ms = msrc + (size_t)sl * nc;
             const cd* tb = mtab + (size_t)sl * nt + (nc - 1 - c);   // T[n - c + 2P] = tb[n]
             cd a = acc;
-            for (int nn = 0; nn < nc; ++nn) a += tb[nn] * ms[nn];
+            for (int nn = 0; nn < nc; ++nn) a = cmac(a, tb[nn], ms[nn]);
             acc = a;
         }
     }
@@ -739,7 +739,7 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
                 cd hm = h0, hn = h1, up = uu, vp = vv;
                 for (int nn = 1; nn <= Ps; ++nn) {
                     cd neg = (nn & 1) ? -hn : hn;
-                    acc += coef[Ps + nn] * (hn * up) + coef[Ps - nn] * (neg * vp);
+                    acc = cmac(cmac(acc, coef[Ps + nn], hn * up), coef[Ps - nn], neg * vp);
                     cd hp = (2.0 * nn) * (zi * hn) - hm;
                     hm = hn;
                     hn = hp;
@@ -774,7 +774,7 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
                         tp = -tp;
                         tm = -tm;
                     }
-                    acc += coef[P + nn] * tp + coef[P - nn] * tm;
+                    acc = cmac(cmac(acc, coef[P + nn], tp), coef[P - nn], tm);
                 }
             } else {
                 cd* row = rows + (size_t)threadIdx.x * (maxP + 2);

@@ -520,14 +520,14 @@ __device__ __forceinline__ void p2x_column(const ZCoef& zc, int P, int col, cd x
     cd xs = neg ? xm : xp;
     cd d = sg;
     for (int i = 1; i <= am; ++i) d = (-__ldg(zc.dg + i)) * (xs * d);
-    acc[nmi(am, m)] += LAP ? d : F[am] * d;
+    acc[nmi(am, m)] = LAP ? acc[nmi(am, m)] + d : cmac(acc[nmi(am, m)], F[am], d);
     if (am + 1 > P) return;
     cd p2 = d, p1 = __ldg(zc.s21 + am) * (z * d);
-    acc[nmi(am + 1, m)] += LAP ? p1 : F[am + 1] * p1;
+    acc[nmi(am + 1, m)] = LAP ? acc[nmi(am + 1, m)] + p1 : cmac(acc[nmi(am + 1, m)], F[am + 1], p1);
     for (int n = am + 2; n <= P; ++n) {
         int k = nmi(n, am);
         cd cur = __ldg(zc.A + k) * (z * p1) - __ldg(zc.B + k) * (r2 * p2);
-        acc[nmi(n, m)] += LAP ? cur : F[n] * cur;
+        acc[nmi(n, m)] = LAP ? acc[nmi(n, m)] + cur : cmac(acc[nmi(n, m)], F[n], cur);
         p2 = p1;
         p1 = cur;
     }
@@ -624,14 +624,14 @@ __device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const
             if (m > 0) d = (-__ldg(zc.dg + m)) * (xs * d);
             if (sgn == 1 && m == 0) continue;
             int mi = sgn ? -m : m;
-            acc += F[m] * (d * coef[nmi(m, mi)]);
+            acc = cmac(acc, F[m], d * coef[nmi(m, mi)]);
             if (m + 1 > P) continue;
             cd p2 = d, p1 = __ldg(zc.s21 + m) * (z * d);
-            acc += F[m + 1] * (p1 * coef[nmi(m + 1, mi)]);
+            acc = cmac(acc, F[m + 1], p1 * coef[nmi(m + 1, mi)]);
             for (int n = m + 2; n <= P; ++n) {
                 int k = nmi(n, m);
                 cd cur = zc.A[k] * (z * p1) - zc.B[k] * (r2 * p2);
-                acc += F[n] * (cur * coef[nmi(n, mi)]);
+                acc = cmac(acc, F[n], cur * coef[nmi(n, mi)]);
                 p2 = p1;
                 p1 = cur;
             }
@@ -1032,10 +1032,10 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
                 cd sp = {0, 0};
                 int ce = min(n, Pi);
                 const cd* Tr = Tm + n * (Pn + 1);
-                for (int c = m; c <= ce; ++c) sp += Tr[c] * a[nmi(c, mm)];
+                for (int c = m; c <= ce; ++c) sp = cmac(sp, Tr[c], a[nmi(c, mm)]);
                 if (n < Pi) {
                     cd up = {0, 0};
-                    for (int r = n + 1; r <= Pi; ++r) up += Tm[r * (Pn + 1) + n] * wb[nmi(r, mm)];
+                    for (int r = n + 1; r <= Pi; ++r) up = cmac(up, Tm[r * (Pn + 1) + n], wb[nmi(r, mm)]);
                     double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
                     sp += g * up;
                 }
@@ -1171,12 +1171,12 @@ __global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const
             int am = m < 0 ? -m : m;
             cd v = {0, 0};
             if (mode == 0) {
-                for (int kk = 0; kk <= n - am; ++kk) v += g[kk] * a[nmi(n - kk, m)];
+                for (int kk = 0; kk <= n - am; ++kk) v = cmac(v, g[kk], a[nmi(n - kk, m)]);
             } else if (mode == 1) {
-                for (int nn = am; nn <= P; ++nn) v += g[nn + n] * a[nmi(nn, m)];
+                for (int nn = am; nn <= P; ++nn) v = cmac(v, g[nn + n], a[nmi(nn, m)]);
                 if ((n + m) & 1) v = -v;
             } else {
-                for (int nn = n; nn <= P; ++nn) v += g[nn - n] * a[nmi(nn, m)];
+                for (int nn = n; nn <= P; ++nn) v = cmac(v, g[nn - n], a[nmi(nn, m)]);
             }
             bb[k] = (out_local ? __ldg(lsd + k) : __ldg(lsm + k)) * v;
         }
@@ -1202,10 +1202,10 @@ __global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const
 
 // coaxial work arrays of one block (complex entries): sectorial columns and,
 // per warp, three recurrence columns and the lower triangle of T^m
-size_t tr3h_work(int Pi, int Po) {
+size_t tr3h_work(int Pi, int Po, int threads = kH3Threads) {
     int Pn = std::min(Pi, Po), Pm = std::max(Pi, Po), NR = Pi + Po;
     return (size_t)(Pn + 1) * (NR + 1) +
-           (size_t)(kH3Threads / 32) * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
+           (size_t)(threads / 32) * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
 }
 
 size_t tr3h_dh(int P) {
@@ -1517,20 +1517,22 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             dsm = 0;
         }
         int64_t nitem = (int64_t)nb * nrhs * nchunk, G = nitem;
-        int accg = 0;
+        int accg = 0, threads = kH3Threads;
         if (smem > (size_t)kH3Smem) {
             // coaxial work arrays (and for the largest orders the accumulator)
             // in global scratch: one slice per resident block, the blocks
             // stride over the work items
             smem = tr3h_smem(Pi, Po, false, false);
             if (smem > (size_t)kH3Smem) {
+                // one block per SM fits: twice the threads keep the FP64 pipe fed
                 smem = tr3h_smem(Pi, Po, false, false, false);
                 accg = 1;
+                threads = 2 * kH3Threads;
             }
             int per_sm = 0;
-            CFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tr3h, kH3Threads, smem));
+            CFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tr3h, threads, smem));
             G = std::min<int64_t>(nitem, (int64_t)std::max(1, per_sm) * nsm);
-            size_t per = tr3h_work(Pi, Po) + (accg ? (size_t)(Po + 1) * (Po + 1) : 0);
+            size_t per = tr3h_work(Pi, Po, threads) + (accg ? (size_t)(Po + 1) * (Po + 1) : 0);
             S->gscr.alloc(per * (size_t)G);
             gs = S->gscr.get();
         }
@@ -1563,7 +1565,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                                                            S->pre_fl.get());
             CFMM_LAUNCHED();
         }
-        k_tr3h<<<g, kH3Threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
+        k_tr3h<<<g, threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
                                             qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
@@ -1588,6 +1590,10 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         int nchunk = S->l2max[l] > 2 * kM2LChunk3 ? (S->l2max[l] + kM2LChunk3 - 1) / kM2LChunk3 : 1;
         int64_t want = (int64_t)16 * nsm, base = (int64_t)std::max(1, nb) * nrhs;
         if (nchunk > 1 && base * nchunk > want) nchunk = (int)std::max<int64_t>(1, (want + base - 1) / base);
+        // few boxes (a coarse top level): split their lists down to 4 entries
+        // so that every SM gets work
+        if (base * nchunk < want && S->l2max[l] > 4)
+            nchunk = (int)std::max<int64_t>(nchunk, std::min<int64_t>((S->l2max[l] + 3) / 4, (want + base - 1) / base));
         int chunk = nchunk > 1 ? (S->l2max[l] + nchunk - 1) / nchunk : std::max(1, S->l2max[l]);
         launch_tr(1, lo, nb, S->Plev[l], S->Plev[l], 1, mp, lc, nchunk, chunk);
     }
