@@ -37,6 +37,8 @@ CFMM_HD cd& operator+=(cd& a, cd b) { a.x += b.x; a.y += b.y; return a; }
 CFMM_HD cd cmac(cd acc, cd a, cd b) {
     return cd{fma(-a.y, b.y, fma(a.x, b.x, acc.x)), fma(a.y, b.x, fma(a.x, b.y, acc.y))};
 }
+// acc + s z for real s (two fused multiply-adds)
+CFMM_HD cd rmac(cd acc, double s, cd z) { return cd{fma(s, z.x, acc.x), fma(s, z.y, acc.y)}; }
 CFMM_HD cd& operator-=(cd& a, cd b) { a.x -= b.x; a.y -= b.y; return a; }
 CFMM_HD double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
 CFMM_HD cd conjg(cd a) { return cd{a.x, -a.y}; }

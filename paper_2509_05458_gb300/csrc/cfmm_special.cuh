@@ -141,8 +141,9 @@ CFMM_HD void bessel_j_seq(cd z, int nmax, cd* out) {
         int r = n & 3;
         if (up) w = (r == 0) ? f : (r == 1) ? cd{f.y, -f.x} : (r == 2) ? -f : cd{-f.y, f.x};
         else    w = (r == 0) ? f : (r == 1) ? cd{-f.y, f.x} : (r == 2) ? -f : cd{f.y, -f.x};
-        S += 2.0 * w;
-        cd fm = (2.0 * n) * (zi * f) - fp;
+        S = cd{fma(2.0, w.x, S.x), fma(2.0, w.y, S.y)};
+        cd t = zi * f;
+        cd fm = {fma(2.0 * n, t.x, -fp.x), fma(2.0 * n, t.y, -fp.y)};
         fp = f;
         f = fm;
         if (cabs2(f) > 1e300) {
@@ -168,7 +169,7 @@ CFMM_HD void sph_h_seq(cd z, int nmax, cd* out) {
     out[0] = -mul_i(e * zi);
     if (nmax < 1) return;
     out[1] = -(e * (z + cd{0.0, 1.0})) * (zi * zi);
-    for (int n = 1; n < nmax; ++n) out[n + 1] = (2.0 * n + 1.0) * (zi * out[n]) - out[n - 1];
+    for (int n = 1; n < nmax; ++n) out[n + 1] = rmac(-out[n - 1], 2.0 * n + 1.0, zi * out[n]);
 }
 
 // j_n(z), n = 0..nmax, complex z
@@ -193,8 +194,10 @@ CFMM_HD void sph_j_seq(cd z, int nmax, cd* out) {
         int r = n & 3;
         if (up) w = (r == 0) ? f : (r == 1) ? cd{f.y, -f.x} : (r == 2) ? -f : cd{-f.y, f.x};
         else    w = (r == 0) ? f : (r == 1) ? cd{-f.y, f.x} : (r == 2) ? -f : cd{f.y, -f.x};
-        S += (2.0 * n + 1.0) * w;
-        cd fm = (2.0 * n + 1.0) * (zi * f) - fp;   // j_{n-1} = ((2n+1)/z) j_n - j_{n+1}
+        double c2 = 2.0 * n + 1.0;
+        S = cd{fma(c2, w.x, S.x), fma(c2, w.y, S.y)};
+        cd t = zi * f;
+        cd fm = {fma(c2, t.x, -fp.x), fma(c2, t.y, -fp.y)};   // j_{n-1} = ((2n+1)/z) j_n - j_{n+1}
         fp = f;
         f = fm;
         if (cabs2(f) > 1e300) {

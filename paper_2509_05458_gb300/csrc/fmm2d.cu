@@ -109,7 +109,7 @@ __device__ void cyl_row(int kind, cd zeta, cd eta, double kappa, int P, cd* row)
         pos[0] = h0;
         if (M >= 1) pos[1] = h1;
         cd zi = cinv(z);
-        for (int m = 1; m < M; ++m) pos[m + 1] = (2.0 * m) * (zi * pos[m]) - pos[m - 1];
+        for (int m = 1; m < M; ++m) pos[m + 1] = rmac(-pos[m - 1], 2.0 * m, zi * pos[m]);
     }
     cd ir = cinv(r);
     cd u = zeta * ir, v = eta * ir;
@@ -740,7 +740,7 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
                 for (int nn = 1; nn <= Ps; ++nn) {
                     cd neg = (nn & 1) ? -hn : hn;
                     acc = cmac(cmac(acc, coef[Ps + nn], hn * up), coef[Ps - nn], neg * vp);
-                    cd hp = (2.0 * nn) * (zi * hn) - hm;
+                    cd hp = rmac(-hm, 2.0 * nn, zi * hn);
                     hm = hn;
                     hn = hp;
                     up = up * uu;

@@ -779,8 +779,8 @@ __device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, c
         for (int mp = 1; mp <= n; ++mp) {
             double d = Dn[mp * N1 + m];
             cd wq = odd ? wv[-mp] : wv[mp];
-            if (mp & 1) O += d * wq;
-            else E += d * wq;
+            if (mp & 1) O = rmac(O, d, wq);
+            else E = rmac(E, d, wq);
         }
         cd yp, ym;
         if (odd) {
@@ -794,6 +794,10 @@ __device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, c
         auto emit = [&](int mm, cd y) {
             y = mul_ipow(op * mm, y);
             if (sgn_out && (mm & 1)) y = -y;
+            if (accum && pwo) {
+                out[nmi(n, mm)] = cmac(out[nmi(n, mm)], y, pwo[mm + Pm]);
+                return;
+            }
             if (pwo) y = y * pwo[mm + Pm];
             if (accum) out[nmi(n, mm)] += y;
             else out[nmi(n, mm)] = y;
@@ -1011,8 +1015,8 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
                 // next column c + 1, rows c + 1 .. NR - c - 1
                 double ac = __ldg(A.al + nmi(c, m)), ib = __ldg(A.ibe + nmi(c, m));
                 for (int r = c + 1 + lane; r <= NR - c - 1; r += 32) {
-                    cd v = ac * cm1[r] - __ldg(A.al + nmi(r + 1, m)) * c0[r + 1];
-                    if (r - 1 >= m) v += __ldg(A.be + nmi(r - 1, m)) * c0[r - 1];
+                    cd v = rmac(ac * cm1[r], -__ldg(A.al + nmi(r + 1, m)), c0[r + 1]);
+                    if (r - 1 >= m) v = rmac(v, __ldg(A.be + nmi(r - 1, m)), c0[r - 1]);
                     c1[r] = ib * v;
                 }
                 __syncwarp();
