@@ -279,6 +279,9 @@ def run_gpu(args):
     fp64_peak = 1250.0   # GFLOP/s: nominal dense FP64 of GB300 (no measured FP64 peak is provided)
     roof = dominant_roofline("M2L", kt[3], work, fp64_peak)
     roof["longest_step"] = {"step": STEP_NAMES[dom], "ms": float(kt[dom])}
+    if M2L_TRAFFIC_BYTES is not None and DIM == 2 and N_POINTS == 100_000 and LEAF == 64:
+        roof["traffic"] = M2L_TRAFFIC_BYTES
+        roof["traffic_source"] = "profiles/ncu_m2l_helm2d_k20_n1e5.txt (k_m2l_chunk, one apply, DRAM read+write)"
     info = mixed["info"]
     line = {
         "metric": METRIC,
@@ -640,6 +643,9 @@ def dominant_roofline(name, ms, work, fp64_peak_gflops):
 
 # FP64 operations of one near-field pair (2D Helmholtz SLP+DLP); 0 = not yet counted
 P2P_FLOPS_PER_PAIR = 0
+# DRAM bytes of the 2D Helmholtz M2L launches of one apply on the headline workload,
+# from one ncu capture (profiles/ncu_m2l_helm2d_k20_n1e5.txt); None once the kernel changes
+M2L_TRAFFIC_BYTES = 27_990_784
 
 
 def cpu_baseline(args):
