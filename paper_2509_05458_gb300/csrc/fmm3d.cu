@@ -415,6 +415,9 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
         chunk = (int)std::max<size_t>(1, std::min<size_t>(16, (96 * 1024) / (nt * sizeof(cd))));
         return sizeof(cd) * ((size_t)(maxP + 1) * (maxP + 1) + (size_t)chunk * nt + (size_t)chunk * 6);
     };
+    // (3) P2P (writes u) on the side stream, beside the far field
+    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     // (1) P2M (single layer: one lane per harmonic column)
     if (!(P->slp && !P->dlp &&
           lap3_p2m_slp(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
@@ -433,9 +436,6 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     for (int l = T.nlevels - 2; l >= S->l0; --l)
         lap3_tr_launch(S->tr, P, 0, l, Pu, S->exp_off.get(), S->ncoef, mp, mp, nrhs);
     rec(3);
-    // (3) P2P (writes u) on the side stream, beside the translations
-    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     // (4) M2L
     for (int l = S->l0; l < T.nlevels; ++l)
         lap3_tr_launch(S->tr, P, 1, l, Pu, S->exp_off.get(), S->ncoef, mp, lc, nrhs);

@@ -1460,6 +1460,9 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                 T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(), T.cen_im.get(), S->dPlev.get(),
                 S->exp_off.get(), S->ncoef, P->kappa, zc};
     int maxP = S->maxP;
+    // (3) P2P (writes u) on the side stream, beside the far field
+    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     auto p2x_smem = [&](int PL, int& chunk) {
         size_t nc = (size_t)(PL + 1) * (PL + 1);
         size_t per = nc + (PL + 2) + 6;
@@ -1582,11 +1585,6 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         launch_tr(0, lo, nb, S->Plev[l + 1], S->Plev[l], 0, mp, mp, 1, 1);
     }
     rec(3);
-    // (3) P2P (writes u) on the side stream, beside the translations: the
-    // FP32 near field then shares the SMs with the FP64-bound M2L rather than
-    // with P2M, which the translations wait for
-    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     // (4) M2L per level (overwrites L at levels >= l0)
     for (int l = S->l0; l < T.nlevels; ++l) {
         int lo = T.level_off[l], nb = T.level_off[l + 1] - lo;
