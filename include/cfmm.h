@@ -219,7 +219,8 @@ typedef struct cfmm_plan_info {
 /* cfmm_plan_get_info: fills *info. */
 int cfmm_plan_get_info(cfmm_plan_t plan, cfmm_plan_info* info);
 
-/* cfmm_plan_get_orders: P per level into p[0..nlevels-1] (host array). */
+/* cfmm_plan_get_orders: P per level into p[0..nlevels-1] (host array); 2D Helmholtz
+ * levels above the top expansion level (no expansions there) read 0. */
 int cfmm_plan_get_orders(cfmm_plan_t plan, int* p, int nlevels);
 
 /*

@@ -975,7 +975,10 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->Plev.assign(T.nlevels, 0);
     for (int l = 0; l < T.nlevels; ++l) {
         if (P->kernel == CFMM_LAPLACE) S->Plev[l] = nterms_laplace(2, P->sep, P->eps * kPHeadroom);
-        else S->Plev[l] = nterms_helm2d(P->sep, P->eps * kPHeadroomHelm, P->kappa, std::ldexp(P->W, -l));
+        // Helmholtz levels above the top expansion level carry no expansions:
+        // their (large, host-evaluated) orders are not computed and read 0
+        else if (l >= S->l0 || T.nboxes <= 1)
+            S->Plev[l] = nterms_helm2d(P->sep, P->eps * kPHeadroomHelm, P->kappa, std::ldexp(P->W, -l));
     }
     P->P = S->Plev;
     if (T.nboxes <= 1) return;   // single leaf: near field only
