@@ -137,27 +137,32 @@ static constexpr int kSortThreads = 256;
 static constexpr int kSortItems = 8;                 // chunks per tile
 static constexpr int kSortTile = kSortThreads * kSortItems;
 
+static constexpr int kRadixBits = 8;                // digit width of one pass
+static constexpr int kRadix = 1 << kRadixBits;
+
 __global__ void k_sort_hist(const uint64_t* __restrict__ keys, int n, int shift,
                             int* __restrict__ hist, int ntiles) {
-    __shared__ int h[16];
-    if (threadIdx.x < 16) h[threadIdx.x] = 0;
+    __shared__ int h[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) h[d] = 0;
     __syncthreads();
     int base = blockIdx.x * kSortTile;
     for (int c = 0; c < kSortItems; ++c) {
         int i = base + c * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 15u], 1);
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1);
     }
     __syncthreads();
-    if (threadIdx.x < 16) hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[d * ntiles + blockIdx.x] = h[d];
 }
 
+// stable scatter of one digit: within a tile, items keep their order (chunk
+// by chunk, warp by warp, and by lane rank among equal digits in a warp)
 __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int* __restrict__ vin,
                                uint64_t* __restrict__ kout, int* __restrict__ vout, int n,
                                int shift, const int* __restrict__ offs, int ntiles) {
-    __shared__ int run[16];
-    __shared__ int wcnt[kSortThreads / 32][16];
+    __shared__ int run[kRadix];
+    __shared__ int wcnt[kSortThreads / 32][kRadix];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x < 16) run[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] = offs[d * ntiles + blockIdx.x];
     int base = blockIdx.x * kSortTile;
     __syncthreads();
     for (int c = 0; c < kSortItems; ++c) {
@@ -165,11 +170,11 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int* __re
         bool valid = i < n;
         uint64_t key = valid ? kin[i] : 0;
         int val = valid ? vin[i] : 0;
-        unsigned dig = valid ? (unsigned)((key >> shift) & 15u) : 16u;
+        unsigned dig = valid ? (unsigned)((key >> shift) & (kRadix - 1)) : (unsigned)kRadix;
         unsigned same = __match_any_sync(0xffffffffu, dig);
         unsigned lt = (1u << lane) - 1u;
         int rank = __popc(same & lt);
-        if (lane < 16) wcnt[w][lane] = 0;
+        for (int d = lane; d < kRadix; d += 32) wcnt[w][d] = 0;
         __syncwarp();
         if (valid && rank == 0) wcnt[w][dig] = __popc(same);
         __syncthreads();
@@ -181,10 +186,10 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int* __re
             vout[pos] = val;
         }
         __syncthreads();
-        if (threadIdx.x < 16) {
-            int s = 0;
-            for (int ww = 0; ww < kSortThreads / 32; ++ww) s += wcnt[ww][threadIdx.x];
-            run[threadIdx.x] += s;
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+            int s2 = 0;
+            for (int ww = 0; ww < kSortThreads / 32; ++ww) s2 += wcnt[ww][d];
+            run[d] += s2;
         }
         __syncthreads();
     }
@@ -202,16 +207,16 @@ static void radix_sort(DevBuf<uint64_t>& keys, DevBuf<int>& vals, int n, int nbi
     int ntiles = (n + kSortTile - 1) / kSortTile;
     uint64_t* k2 = scr.take_n<uint64_t>(n);
     int* v2 = scr.take_n<int>(n);
-    int* hist = scr.take_n<int>(16 * ntiles);
-    int* offs = scr.take_n<int>(16 * ntiles);
+    int* hist = scr.take_n<int>((size_t)kRadix * ntiles);
+    int* offs = scr.take_n<int>((size_t)kRadix * ntiles);
     uint64_t *ka = keys.get(), *kb = k2;
     int *va = vals.get(), *vb = v2;
-    int passes = (nbits + 3) / 4;
+    int passes = (nbits + kRadixBits - 1) / kRadixBits;
     for (int p = 0; p < passes; ++p) {
-        int shift = 4 * p;
+        int shift = kRadixBits * p;
         k_sort_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles);
         CFMM_LAUNCHED();
-        scan_exclusive_async(hist, offs, 16 * ntiles, st);
+        scan_exclusive_async(hist, offs, kRadix * ntiles, st);
         k_sort_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs, ntiles);
         CFMM_LAUNCHED();
         std::swap(ka, kb);
