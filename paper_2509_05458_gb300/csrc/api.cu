@@ -124,6 +124,42 @@ Scratch::~Scratch() {
     for (auto& c : chunks_) cudaFree(c.p);
 }
 
+void* HostStage::take(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (cur_ < chunks_.size()) {
+        if (off_ + bytes <= chunks_[cur_].size) {
+            void* p = chunks_[cur_].p + off_;
+            off_ += bytes;
+            return p;
+        }
+        ++cur_;
+        off_ = 0;
+    }
+    size_t sz = std::max(bytes, (size_t)4 << 20);
+    char* p = nullptr;
+    CFMM_CUDA(cudaHostAlloc((void**)&p, sz, cudaHostAllocDefault));
+    chunks_.push_back(Chunk{p, sz});
+    cur_ = chunks_.size() - 1;
+    off_ = bytes;
+    return p;
+}
+
+HostStage::~HostStage() {
+    for (auto& c : chunks_) cudaFreeHost(c.p);
+}
+
+HostStage& plan_host_stage() {
+    thread_local HostStage stage;
+    return stage;
+}
+
+void upload(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return;
+    void* h = plan_host_stage().take(bytes);
+    std::memcpy(h, src, bytes);
+    CFMM_CUDA(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, st));
+}
+
 Scratch& plan_scratch() {
     thread_local std::vector<std::unique_ptr<Scratch>> per_dev;
     int dev = 0;
@@ -443,6 +479,7 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         CFMM_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
         Scratch& scr = plan_scratch();
         scr.rewind();
+        plan_host_stage().rewind();
         size_t cnt = (size_t)n * dim;
         const double* re = stage_in(pts_re, cnt, P->stream);
         const double* im = stage_in(pts_im, cnt, P->stream);
@@ -454,6 +491,7 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         else fmm3d_setup(P);
         CFMM_CUDA(cudaStreamSynchronize(P->stream));
         scr.rewind();
+        plan_host_stage().rewind();
     });
     if (rc != 0) {
         destroy_plan(P);

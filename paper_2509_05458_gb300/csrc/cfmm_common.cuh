@@ -162,6 +162,31 @@ class Scratch {
 };
 Scratch& plan_scratch();
 
+// Pinned host staging for the small uploads of plan construction: a copy from
+// pinned memory is asynchronous, one from pageable memory costs the host a
+// staging copy each time. Bump-allocated like Scratch and rewound with it,
+// after the plan's stream has been synchronised.
+class HostStage {
+   public:
+    void* take(size_t bytes);
+    void rewind() {
+        cur_ = 0;
+        off_ = 0;
+    }
+    ~HostStage();
+
+   private:
+    struct Chunk {
+        char* p;
+        size_t size;
+    };
+    std::vector<Chunk> chunks_;
+    size_t cur_ = 0, off_ = 0;
+};
+HostStage& plan_host_stage();
+// host -> device copy of `bytes` on `st` through the plan's pinned staging
+void upload(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // constants shared by host and device code of this library
 // ---------------------------------------------------------------------------

@@ -988,7 +988,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->maxP = maxP;
     P->maxP = maxP;
     S->dPlev.alloc(T.nlevels);
-    CFMM_CUDA(cudaMemcpyAsync(S->dPlev.get(), S->Plev.data(), sizeof(int) * T.nlevels, cudaMemcpyHostToDevice, st));
+    upload(S->dPlev.get(), S->Plev.data(), sizeof(int) * T.nlevels, st);
     // coefficient offsets
     std::vector<int64_t> off(T.nboxes, -1);
     int64_t tot = 0;
@@ -1000,7 +1000,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->ncoef = tot;
     P->ncoef = tot;
     S->exp_off.alloc(T.nboxes);
-    CFMM_CUDA(cudaMemcpyAsync(S->exp_off.get(), off.data(), sizeof(int64_t) * T.nboxes, cudaMemcpyHostToDevice, st));
+    upload(S->exp_off.get(), off.data(), sizeof(int64_t) * T.nboxes, st);
     // leaves at level >= l0 (all leaves when the tree has more than one box);
     // boxes are level-major, so a box's level follows from the level offsets
     auto level_of = [&](int b) {
@@ -1015,8 +1015,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         }
     }
     S->d_leaves_l0.alloc(S->leaves_l0.size());
-    CFMM_CUDA(cudaMemcpyAsync(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(),
-                              cudaMemcpyHostToDevice, st));
+    upload(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(), st);
     bool rows_side = false;
     if (P->kernel == CFMM_HELMHOLTZ && !S->leaves_l0.empty()) {
         // on the side stream, beside the translation tables below
@@ -1037,8 +1036,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         S->n_p2l = (int)boxes.size();
         S->d_p2l_boxes.alloc(boxes.size());
         if (!boxes.empty())
-            CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
-                                      cudaMemcpyHostToDevice, st));
+            upload(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(), st);
     }
     // binomials C(n, k), n, k <= 2 maxP + 1 (exact integers up to 2^53, then rounded)
     S->NB = 2 * maxP + 2;
@@ -1052,7 +1050,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         }
         S->binom.alloc(bt.size());
         // (a copy from pageable memory returns once the source is staged)
-        CFMM_CUDA(cudaMemcpyAsync(S->binom.get(), bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, st));
+        upload(S->binom.get(), bt.data(), sizeof(double) * bt.size(), st);
     }
     if (P->kernel == CFMM_HELMHOLTZ) {
         // M2L tables, level-major like List 2 itself
@@ -1069,8 +1067,8 @@ void fmm2d_setup(cfmm_plan_s* P) {
         S->t_m2l.alloc(base > 0 ? base : 1);
         S->d_m2l_base.alloc(T.nlevels);
         S->d_m2l_q0.alloc(T.nlevels);
-        CFMM_CUDA(cudaMemcpyAsync(S->d_m2l_base.get(), S->m2l_base.data(), sizeof(int64_t) * T.nlevels, cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(S->d_m2l_q0.get(), S->m2l_q0.data(), sizeof(int) * T.nlevels, cudaMemcpyHostToDevice, st));
+        upload(S->d_m2l_base.get(), S->m2l_base.data(), sizeof(int64_t) * T.nlevels, st);
+        upload(S->d_m2l_q0.get(), S->m2l_q0.data(), sizeof(int) * T.nlevels, st);
         // owner box of every List-2 entry at levels >= l0
         int qf = loff[T.level_off[S->l0]], ql = loff[T.nboxes];
         if (ql > qf) {
@@ -1078,7 +1076,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             for (int b = T.level_off[S->l0]; b < T.nboxes; ++b)
                 for (int q = loff[b]; q < loff[b + 1]; ++q) qbox[q - qf] = b;
             int* dq = plan_scratch().take_n<int>(qbox.size());
-            CFMM_CUDA(cudaMemcpyAsync(dq, qbox.data(), sizeof(int) * qbox.size(), cudaMemcpyHostToDevice, st));
+            upload(dq, qbox.data(), sizeof(int) * qbox.size(), st);
             int nq = ql - qf;
             k_tab_m2l<<<(nq + 127) / 128, 128, 0, st>>>(nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
                                                        S->d_m2l_base.get(), S->d_m2l_q0.get(), T.cen_re.get(),
@@ -1114,11 +1112,11 @@ void fmm2d_setup(cfmm_plan_s* P) {
             S->chunk_q1.alloc(cb.size());
             S->box_chunk0.alloc(T.nboxes + 1);
             if (!cb.empty()) {
-                CFMM_CUDA(cudaMemcpyAsync(S->chunk_box.get(), cb.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
-                CFMM_CUDA(cudaMemcpyAsync(S->chunk_q0.get(), c0v.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
-                CFMM_CUDA(cudaMemcpyAsync(S->chunk_q1.get(), c1v.data(), sizeof(int) * cb.size(), cudaMemcpyHostToDevice, st));
+                upload(S->chunk_box.get(), cb.data(), sizeof(int) * cb.size(), st);
+                upload(S->chunk_q0.get(), c0v.data(), sizeof(int) * cb.size(), st);
+                upload(S->chunk_q1.get(), c1v.data(), sizeof(int) * cb.size(), st);
             }
-            CFMM_CUDA(cudaMemcpyAsync(S->box_chunk0.get(), bc0.data(), sizeof(int) * (T.nboxes + 1), cudaMemcpyHostToDevice, st));
+            upload(S->box_chunk0.get(), bc0.data(), sizeof(int) * (T.nboxes + 1), st);
         }
         // shift tables for boxes at levels > l0
         std::vector<int64_t> so(T.nboxes, -1);
@@ -1130,7 +1128,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             }
         S->t_shift.alloc(sb > 0 ? sb : 1);
         S->shift_off.alloc(T.nboxes);
-        CFMM_CUDA(cudaMemcpyAsync(S->shift_off.get(), so.data(), sizeof(int64_t) * T.nboxes, cudaMemcpyHostToDevice, st));
+        upload(S->shift_off.get(), so.data(), sizeof(int64_t) * T.nboxes, st);
         int lo = T.level_off[std::min(S->l0 + 1, T.nlevels)], hi = T.nboxes;
         if (hi > lo) {
             k_tab_shift<<<(hi - lo + 63) / 64, 64, 0, st>>>(lo, hi, T.parent.get(), T.level.get(), S->dPlev.get(),

@@ -1039,8 +1039,7 @@ static void build_boxes(cfmm_plan_s* P, LeafArrays& L, cudaStream_t st) {
                                                                T.end.get(), T.leaf.get(), leaf_box);
     CFMM_LAUNCHED();
     T.d_level_off.alloc(T.nlevels + 1);
-    CFMM_CUDA(cudaMemcpyAsync(T.d_level_off.get(), T.level_off.data(), sizeof(int) * (T.nlevels + 1),
-                              cudaMemcpyHostToDevice, st));
+    upload(T.d_level_off.get(), T.level_off.data(), sizeof(int) * (T.nlevels + 1), st);
     k_box_links<<<blocks_for(nb, 256), 256, 0, st>>>(nb, T.level.get(), T.prefix.get(), T.d_level_off.get(),
                                                     T.nlevels, dim, T.parent.get(), T.cbeg.get(), T.cend.get());
     CFMM_LAUNCHED();
@@ -1226,13 +1225,13 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     LeafArrays L;
     L.take(1);
     {
+        // the root leaf: level 0, prefix 0, points [0, n)
         int z = 0, nn = (int)n;
         uint64_t zp = 0;
-        CFMM_CUDA(cudaMemcpyAsync(L.lev, &z, sizeof(int), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.pre, &zp, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.st, &z, sizeof(int), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaMemcpyAsync(L.en, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
-        CFMM_CUDA(cudaStreamSynchronize(st));
+        upload(L.lev, &z, sizeof(int), st);
+        upload(L.pre, &zp, sizeof(uint64_t), st);
+        upload(L.st, &z, sizeof(int), st);
+        upload(L.en, &nn, sizeof(int), st);
     }
     int Ns = P->leaf_size;
     refine_onepass(L, P->keys.get(), n, dim, B, Ns, 0, false, st);
