@@ -8,6 +8,9 @@
 
 #include <atomic>
 #include <string>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/cfmm.h"
@@ -184,6 +187,28 @@ class HostStage {
     size_t cur_ = 0, off_ = 0;
 };
 HostStage& plan_host_stage();
+
+// Phase times of plan construction on stderr when CFMM_PLAN_PROFILE=1 (each
+// mark synchronises the stream first; off otherwise)
+struct PhaseTimer {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t;
+    explicit PhaseTimer(cudaStream_t s) : st(s) {
+        const char* e = getenv("CFMM_PLAN_PROFILE");
+        on = e && e[0] == '1';
+        t = std::chrono::steady_clock::now();
+    }
+    void mark(const char* name) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[cfmm plan] %-14s %8.3f ms\n", name,
+                std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 // host -> device copy of `bytes` on `st` through the plan's pinned staging
 void upload(void* dst, const void* src, size_t bytes, cudaStream_t st);
 

@@ -950,20 +950,7 @@ constexpr double kPHeadroomHelm = 0.01;
 void fmm2d_setup(cfmm_plan_s* P) {
     TreeDev& T = P->tree;
     cudaStream_t st = P->stream;
-    const char* prof = getenv("CFMM_PLAN_PROFILE");
-    auto t_start = std::chrono::steady_clock::now();
-    struct Done {
-        const char* prof;
-        cudaStream_t st;
-        std::chrono::steady_clock::time_point t0;
-        ~Done() {
-            if (prof && prof[0] == '1') {
-                cudaStreamSynchronize(st);
-                fprintf(stderr, "[cfmm plan] %-14s %8.3f ms\n", "setup2d",
-                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
-            }
-        }
-    } done{prof, st, t_start};
+    PhaseTimer pt(st);
     Fmm2dState* S = new Fmm2dState();
     {
         std::lock_guard<std::mutex> lk(g_ext_mu);
@@ -981,6 +968,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             S->Plev[l] = nterms_helm2d(P->sep, P->eps * kPHeadroomHelm, P->kappa, std::ldexp(P->W, -l));
     }
     P->P = S->Plev;
+    pt.mark("setup:orders");
     if (T.nboxes <= 1) return;   // single leaf: near field only
     int maxP = 0;
     for (int l = S->l0; l < T.nlevels; ++l) maxP = std::max(maxP, S->Plev[l]);
@@ -1016,6 +1004,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
     }
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     upload(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(), st);
+    pt.mark("setup:leaves");
     bool rows_side = false;
     if (P->kernel == CFMM_HELMHOLTZ && !S->leaves_l0.empty()) {
         // on the side stream, beside the translation tables below
@@ -1038,6 +1027,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         if (!boxes.empty())
             upload(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(), st);
     }
+    pt.mark("setup:p2l+rows");
     // binomials C(n, k), n, k <= 2 maxP + 1 (exact integers up to 2^53, then rounded)
     S->NB = 2 * maxP + 2;
     {
@@ -1083,6 +1073,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
                                                        T.cen_im.get(), P->kappa, S->t_m2l.get(), qf);
             CFMM_LAUNCHED();
         }
+        pt.mark("setup:m2ltab");
         // List-2 chunks per box (levels >= l0)
         {
             std::vector<int> cb, c0v, c1v, bc0(T.nboxes + 1, 0);
@@ -1118,6 +1109,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             }
             upload(S->box_chunk0.get(), bc0.data(), sizeof(int) * (T.nboxes + 1), st);
         }
+        pt.mark("setup:chunks");
         // shift tables for boxes at levels > l0
         std::vector<int64_t> so(T.nboxes, -1);
         int64_t sb = 0;
@@ -1137,7 +1129,9 @@ void fmm2d_setup(cfmm_plan_s* P) {
             CFMM_LAUNCHED();
         }
     }
+    pt.mark("setup:shift");
     if (rows_side) near_join(P);
+    pt.mark("setup:rowsjoin");
     for (auto f : {(const void*)k_point_to_exp<CFMM_LAPLACE>, (const void*)k_point_to_exp<CFMM_HELMHOLTZ>,
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,

@@ -28,24 +28,6 @@ namespace cfmm {
 
 // Optional host-side phase timing of plan construction (CFMM_PLAN_PROFILE=1):
 // each phase is synchronised and its wall time printed to stderr.
-struct PhaseTimer {
-    bool on;
-    cudaStream_t st;
-    std::chrono::steady_clock::time_point t;
-    explicit PhaseTimer(cudaStream_t s) : st(s) {
-        const char* e = getenv("CFMM_PLAN_PROFILE");
-        on = e && e[0] == '1';
-        t = std::chrono::steady_clock::now();
-    }
-    void mark(const char* name) {
-        if (!on) return;
-        cudaStreamSynchronize(st);
-        auto now = std::chrono::steady_clock::now();
-        fprintf(stderr, "[cfmm plan] %-14s %8.3f ms\n", name,
-                std::chrono::duration<double, std::milli>(now - t).count());
-        t = now;
-    }
-};
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 (any length), returns the total
