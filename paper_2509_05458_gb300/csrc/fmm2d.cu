@@ -800,77 +800,38 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
 }
 
 // table kernels (plan time)
-// S_j(c_t - c_s), j = -2P..2P (stored at j + 2P), of every List-2 pair at
-// levels >= l0: one lane per pair runs the Hankel recurrence; each warp stages
-// kTabChunk orders of its 32 pairs in shared memory and writes them out
-// row-contiguously (8 lanes per pair), so the stores coalesce.
-constexpr int kTabChunk = 8;
-constexpr int kTabWarps = 4;
 __global__ void k_tab_m2l(int nq, const int* __restrict__ qbox, const int* __restrict__ lent,
                           const int* __restrict__ blevel, const int* __restrict__ Plev, const int64_t* __restrict__ tbase,
                           const int* __restrict__ tq0, const double* __restrict__ cre, const double* __restrict__ cim,
                           double kappa, cd* __restrict__ tab, int q_first) {
-    __shared__ cd tp[kTabWarps][32][kTabChunk], tn[kTabWarps][32][kTabChunk];
-    __shared__ int64_t rbase[kTabWarps][32];
-    __shared__ int rM[kTabWarps][32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = qi < nq;
-    int M = 0;
-    int64_t base = 0;
-    cd hm = {0, 0}, hn = {0, 0}, up = {0, 0}, vp = {0, 0}, uu = {0, 0}, vv = {0, 0}, zi = {0, 0};
-    if (valid) {
-        int q = q_first + qi;
-        int b = qbox[qi], s = lent[q];
-        int l = blevel[b];
-        int P = Plev[l];
-        M = 2 * P;
-        base = tbase[l] + (int64_t)(q - tq0[l]) * (4 * P + 1);
-        cd z, e;
-        zeta_eta(cd{cre[2 * b] - cre[2 * s], cim[2 * b] - cim[2 * s]},
-                 cd{cre[2 * b + 1] - cre[2 * s + 1], cim[2 * b + 1] - cim[2 * s + 1]}, z, e);
-        cd r = csqrt_p(z * e);
-        cd zz = kappa * r;
-        cd h0, h1;
-        hankel01(zz, &h0, &h1);
-        cd ir = cinv(r);
-        uu = z * ir;
-        vv = e * ir;
-        zi = cinv(zz);
-        tab[base + M] = h0;
-        hm = h0;
-        hn = h1;
-        up = uu;
-        vp = vv;
-    }
-    rbase[w][lane] = base;
-    rM[w][lane] = M;
-    int Mmax = __reduce_max_sync(0xffffffffu, M);
-    for (int j0 = 1; j0 <= Mmax; j0 += kTabChunk) {
-        for (int jj = 0; jj < kTabChunk; ++jj) {
-            int jx = j0 + jj;
-            if (jx <= M) {
-                cd neg = (jx & 1) ? -hn : hn;
-                tp[w][lane][jj] = hn * up;
-                tn[w][lane][jj] = neg * vp;
-                cd hp = rmac(-hm, 2.0 * jx, zi * hn);
-                hm = hn;
-                hn = hp;
-                up = up * uu;
-                vp = vp * vv;
-            }
-        }
-        __syncwarp();
-        for (int k = lane; k < 32 * kTabChunk; k += 32) {
-            int pp = k / kTabChunk, jj = k - pp * kTabChunk;
-            int jx = j0 + jj, Mp = rM[w][pp];
-            if (jx <= Mp) {
-                cd* t = tab + rbase[w][pp];
-                t[Mp + jx] = tp[w][pp][jj];
-                t[Mp - jx] = tn[w][pp][jj];
-            }
-        }
-        __syncwarp();
+    if (qi >= nq) return;
+    int q = q_first + qi;
+    int b = qbox[qi], s = lent[q];
+    int l = blevel[b];
+    int P = Plev[l];
+    cd* t = tab + tbase[l] + (int64_t)(q - tq0[l]) * (4 * P + 1);
+    // S_j(c_t - c_s), j = -2P..2P, stored at j + 2P
+    cd z, e;
+    zeta_eta(cd{cre[2 * b] - cre[2 * s], cim[2 * b] - cim[2 * s]},
+             cd{cre[2 * b + 1] - cre[2 * s + 1], cim[2 * b + 1] - cim[2 * s + 1]}, z, e);
+    cd r = csqrt_p(z * e);
+    cd zz = kappa * r;
+    cd h0, h1;
+    hankel01(zz, &h0, &h1);
+    cd ir = cinv(r), uu = z * ir, vv = e * ir, zi = cinv(zz);
+    int M = 2 * P;
+    t[M] = h0;
+    cd hm = h0, hn = h1, up = uu, vp = vv;
+    for (int j = 1; j <= M; ++j) {
+        cd neg = (j & 1) ? -hn : hn;
+        t[M + j] = hn * up;
+        t[M - j] = neg * vp;
+        cd hp = (2.0 * j) * (zi * hn) - hm;
+        hm = hn;
+        hn = hp;
+        up = up * uu;
+        vp = vp * vv;
     }
 }
 
@@ -1107,8 +1068,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
             int* dq = plan_scratch().take_n<int>(qbox.size());
             upload(dq, qbox.data(), sizeof(int) * qbox.size(), st);
             int nq = ql - qf;
-            k_tab_m2l<<<(nq + 32 * kTabWarps - 1) / (32 * kTabWarps), 32 * kTabWarps, 0, st>>>(
-                nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
+            k_tab_m2l<<<(nq + 127) / 128, 128, 0, st>>>(nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
                                                        S->d_m2l_base.get(), S->d_m2l_q0.get(), T.cen_re.get(),
                                                        T.cen_im.get(), P->kappa, S->t_m2l.get(), qf);
             CFMM_LAUNCHED();
