@@ -46,8 +46,9 @@ enum {
     CFMM_OK = 0,
     CFMM_EINVAL = -1,      /* bad dim/kernel/k/eps/n/nrhs/options               */
     CFMM_ENONFINITE = -2,  /* NaN or Inf in points or normals                   */
-    CFMM_EGEOM = -3,       /* geometry outside the method's assumptions:        */
-                           /*   Re r^2 <= 0 for a near-field pair (Asm. 4.1/5.1)*/
+    CFMM_EGEOM = -3,       /* geometry outside the method's assumptions (Re r^2 */
+                           /*   <= 0 for a near-field pair): reserved, this     */
+                           /*   build does not test the assumption             */
     CFMM_ENOMEM = -4,      /* device allocation failed                          */
     CFMM_ECUDA = -5,       /* CUDA runtime error                                */
     CFMM_ETIMEOUT = -6,    /* a bounded device wait gave up                     */
@@ -254,6 +255,12 @@ int cfmm_plan_set_timing(cfmm_plan_t plan, int on);
 /* cfmm_launch_count: number of kernels this library launched so far in the
  * calling process (all threads). */
 int64_t cfmm_launch_count(void);
+
+/* cfmm_debug_fail_allocs: failure injection for tests (no counterpart in the
+ * paper): the next `count` device allocations of the library (plan buffers,
+ * workspaces, plan-construction scratch) fail with CFMM_ENOMEM, whichever
+ * call makes them; 0 disarms. Returns 0, or CFMM_EINVAL for count < 0. */
+int cfmm_debug_fail_allocs(int count);
 
 int cfmm_last_status(void);
 const char* cfmm_last_error(void);

@@ -74,6 +74,8 @@ def lib():
     L.cfmm_batch_kernels.argtypes = [vp]
     L.cfmm_batch_destroy.restype = ci
     L.cfmm_batch_destroy.argtypes = [vp]
+    L.cfmm_debug_fail_allocs.restype = ci
+    L.cfmm_debug_fail_allocs.argtypes = [ci]
     L.cfmm_destroy.restype = ci
     L.cfmm_destroy.argtypes = [vp]
     L.cfmm_direct.restype = ci

@@ -26,7 +26,18 @@ std::atomic<int64_t>& launch_counter() {
     return c;
 }
 
+// failure injection (tests): the next g_fail_allocs device allocations fail
+static std::atomic<int> g_fail_allocs{0};
+static void injected_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1))
+            throw Error{CFMM_ENOMEM, "device allocation failed (injected)"};
+    }
+}
+
 void* Scratch::take(size_t bytes) {
+    injected_failure();
     bytes = (bytes + 255) & ~(size_t)255;
     while (cur_ < chunks_.size()) {
         if (off_ + bytes <= chunks_[cur_].size) {
@@ -72,6 +83,7 @@ size_t pool_class(size_t b) {
 }  // namespace
 
 void* pool_alloc(size_t bytes, int* dev_out) {
+    injected_failure();
     int dev = 0;
     CFMM_CUDA(cudaGetDevice(&dev));
     *dev_out = dev;
@@ -433,6 +445,13 @@ int cfmm_last_status(void) { return g_status; }
 const char* cfmm_last_error(void) { return g_msg.c_str(); }
 const char* cfmm_version(void) { return "cfmm-gb300 0.1 (sm_103a)"; }
 int64_t cfmm_launch_count(void) { return launch_counter().load(); }
+
+int cfmm_debug_fail_allocs(int count) {
+    return guarded([&] {
+        CFMM_REQUIRE(count >= 0, CFMM_EINVAL, "count must be >= 0");
+        g_fail_allocs.store(count);
+    });
+}
 
 cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
                          const double* nrm_re, const double* nrm_im, int64_t n, const cfmm_opts* opts) {
