@@ -505,6 +505,8 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         const double* nre = dlp ? stage_in(nrm_re, cnt, P->stream) : nullptr;
         const double* nim = dlp ? stage_in(nrm_im, cnt, P->stream) : nullptr;
         build_tree(P, re, im, nre, nim, o.top_level);
+        if (dim == 2) fmm2d_presetup(P);   // its row table overlaps the lists
+        build_plan_lists(P);
         if (dim == 2) fmm2d_setup(P);
         else if (P->kernel == CFMM_HELMHOLTZ) helm3d_setup(P);
         else fmm3d_setup(P);

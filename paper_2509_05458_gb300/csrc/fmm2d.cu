@@ -68,6 +68,7 @@ struct Fmm2dState {
     std::vector<int> leaves_l0;            // leaves at level >= l0
     DevBuf<int> d_leaves_l0;
     int maxP_leaf = 0;                     // largest order at a leaf level (P2M)
+    bool rows_side = false;                // the row table is being built on the side stream
     int n_p2l = 0;                         // boxes with a non-empty List 4
     DevBuf<int> d_p2l_boxes;
     // Helmholtz M2L work split: chunks of at most kM2LChunk List-2 entries
@@ -947,7 +948,10 @@ static int nterms_helm2d(int k, double eps, double kappa, double w) {
 constexpr double kPHeadroom = 0.1;
 constexpr double kPHeadroomHelm = 0.01;
 
-void fmm2d_setup(cfmm_plan_s* P) {
+// First part of the setup, run before the lists are built: orders, offsets,
+// the leaves and (Helmholtz) the per-point row table, launched on the side
+// stream so that it overlaps the construction of the lists.
+void fmm2d_presetup(cfmm_plan_s* P) {
     TreeDev& T = P->tree;
     cudaStream_t st = P->stream;
     PhaseTimer pt(st);
@@ -1005,17 +1009,28 @@ void fmm2d_setup(cfmm_plan_s* P) {
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     upload(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(), st);
     pt.mark("setup:leaves");
-    bool rows_side = false;
     if (P->kernel == CFMM_HELMHOLTZ && !S->leaves_l0.empty()) {
-        // on the side stream, beside the translation tables below
+        // on the side stream, beside the lists and the translation tables
         S->RL = 2 * S->maxP_leaf + 3;
         S->lrow.alloc((size_t)P->n * S->RL);
-        rows_side = true;
+        S->rows_side = true;
         k_leaf_rows<<<(unsigned)S->leaves_l0.size(), 64, 0, near_fork(P)>>>(
             S->d_leaves_l0.get(), T.level.get(), T.start.get(), T.end.get(), S->dPlev.get(), P->xr.get(),
             P->xi.get(), P->n, T.cen_re.get(), T.cen_im.get(), P->kappa, S->RL, S->lrow.get());
         CFMM_LAUNCHED();
     }
+}
+
+// The rest of the setup, once the lists exist: P2L boxes, translation tables,
+// List-2 chunks; joins the side stream's row table at the end.
+void fmm2d_setup(cfmm_plan_s* P) {
+    TreeDev& T = P->tree;
+    cudaStream_t st = P->stream;
+    if (!state(P)) fmm2d_presetup(P);
+    Fmm2dState* S = state(P);
+    PhaseTimer pt(st);
+    if (T.nboxes <= 1) return;   // single leaf: near field only
+    int maxP = S->maxP;
     // boxes that receive P2L contributions
     {
         const std::vector<int>& l4 = T.hloff[3];
@@ -1130,7 +1145,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         }
     }
     pt.mark("setup:shift");
-    if (rows_side) near_join(P);
+    if (S->rows_side) near_join(P);
     pt.mark("setup:rowsjoin");
     for (auto f : {(const void*)k_point_to_exp<CFMM_LAPLACE>, (const void*)k_point_to_exp<CFMM_HELMHOLTZ>,
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,

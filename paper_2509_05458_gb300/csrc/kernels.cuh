@@ -36,8 +36,13 @@ void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaSt
 // tree construction (tree.cu)
 void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,
                 int top_level_opt);
+// Lists 1-4 of the plan's tree (after build_tree)
+void build_plan_lists(cfmm_plan_s* P);
 
 // 2D expansions (fmm2d.cu)
+// 2D expansions: fmm2d_presetup before the lists (orders, leaves, the per-point
+// row table on the side stream), fmm2d_setup after them
+void fmm2d_presetup(cfmm_plan_s* P);
 void fmm2d_setup(cfmm_plan_s* P);
 void fmm2d_release(cfmm_plan_s* P);
 void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);

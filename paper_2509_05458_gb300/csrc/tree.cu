@@ -1275,8 +1275,12 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     }
     P->tree.l0 = l0;
     pt.mark("centres+l0");
-    // a5: lists
-    build_lists(P, st);
+}
+
+// a5: Lists 1-4 of the plan's tree (after build_tree)
+void build_plan_lists(cfmm_plan_s* P) {
+    PhaseTimer pt(P->stream);
+    build_lists(P, P->stream);
     pt.mark("lists");
 }
 
