@@ -626,7 +626,7 @@ def m2l_flops_pair_lap3d(P):
 
 def dominant_roofline(name, ms, work, fp64_peak_gflops):
     """Roofline of the dominant kernel of the apply, FP64-ALU bound:
-    M2L: work["m2l_flops"]; P2P: List-1 pairs x FP64 flops per pair (DESIGN.md)."""
+    M2L: work["m2l_flops"]; P2P: List-1 pairs x FP64 flops per pair."""
     flops = None
     if name == "M2L":
         flops = work["m2l_flops"]

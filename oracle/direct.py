@@ -6,7 +6,7 @@ constant-free sums Eq. lap_2d_pot (2D Laplace, kernel log r), Eq. helm_2d_pot
 (2D Helmholtz, H_0^(1)(kappa r)), Eq. lap_3d_pot (3D Laplace, 1/rho) and the
 3D Helmholtz sum of Sec. 5.3 (exp(i kappa rho)/rho).
 
-Readings taken here (each is listed in the design doc):
+Readings taken here:
 
 * the complex distance is r = sqrt((x-y).(x-y)) on the principal branch
   (Sec. 2.1, Def. 3.1); log r is evaluated as Log(r^2)/2, which equals

@@ -234,7 +234,8 @@ class Expansions2D:
 
 
 def expansion_orders(T, kernel, kappa, eps):
-    """P per level (Sec. 6.3, reading #13)."""
+    """P per level: the Sec. 6.3 criteria with the prefactors dropped and the
+    eps headroom factors of tree.P_HEADROOM / P_HEADROOM_HELM."""
     nl = T.nlevels
     if kernel == LAPLACE:
         return [tr.nterms_laplace(2, T.k, eps * tr.P_HEADROOM)] * nl

@@ -41,7 +41,7 @@ Translations ("point and shoot", Sec. 5.3 translation operators with the
 rotations of Sec. 5.2): for a shift d = c_new - c_old,
   1. rotate about z: s = sqrt(d1^2 + d2^2), e^{i beta} = (d1 + i d2)/s, the
      frame x' = R_z(-beta) x carries d to (s, 0, d3); coefficients are
-     multiplied by e^{i m beta}. If s^2 = 0 then beta = 0 (reading #16);
+     multiplied by e^{i m beta}. If s^2 = 0 (a shift along z) then beta = 0;
   2. rotate about y by alpha, cos alpha = d3/t, sin alpha = s/t,
      t = sqrt(d.d): d goes to (0, 0, t). The rotated coefficients are
      computed by projection (Eq. mp_y_rot): the order-n part F_n and its
@@ -57,7 +57,7 @@ rotations of Sec. 5.2): for a shift d = c_new - c_old,
      results) with the weight pair (conj w_n, kappa conj w_n'), which equals
      the paper's (j_n, kappa j_n') for real j_n and never divides by zero;
   4. undo step 2 (projection) and step 1 (diagonal).
-Sampling radius rho_s (reading #15): the radius sqrt(3)/2 w of the box the
+Sampling radius rho_s (the paper leaves it open): the radius sqrt(3)/2 w of the box the
 result is centred on (target box for M2L and L2L, parent box for M2M).
 """
 from __future__ import annotations
@@ -446,7 +446,8 @@ class Helmholtz3D:
 
 
 def expansion_orders(T, kappa, eps):
-    """P per level (Sec. 6.3, Eq. nterms_criteria_3d, reading #13)."""
+    """P per level (Sec. 6.3, Eq. nterms_criteria_3d, prefactors dropped, with the
+    Helmholtz eps headroom of tree.P_HEADROOM_HELM)."""
     e = eps * tr.P_HEADROOM_HELM
     return [tr.nterms_helmholtz(3, T.k, e, kappa, T.width(l), tr.helm3d_pair)
             for l in range(T.nlevels)]

@@ -6,7 +6,7 @@ Sec. 6.2 (k-colleagues, Lists 1-4) and Sec. 6.3 (number of terms per level,
 Eqs. nterms_criteria / nterms_criteria_2d / nterms_criteria_3d with the
 prefactors ignored as the paper does in practice).
 
-Readings (all listed in the design doc):
+Readings:
 
 * root box: centre = (min+max)/2 of Re x per axis, width W = max extent *
   (1 + 2^-20); integer coordinates q = floor((x - lo)/W * 2^B) clamped to
@@ -494,7 +494,8 @@ def nterms_laplace(dim, k, eps):
 
 
 def nterms_helmholtz(dim, k, eps, kappa, w, fn_pair, pmax=2000):
-    """Smallest n with |f_n(kappa R) g_n(kappa r)| <= eps for n..n+3 (reading #13)."""
+    """Smallest n with |f_n(kappa R) g_n(kappa r)| <= eps for n..n+3 (the Sec. 6.3
+    criterion with its prefactor dropped, four consecutive orders for safety)."""
     R = (k + 0.5) * w
     r = math.sqrt(dim) * 0.5 * w
     vals = fn_pair(np.arange(pmax + 4), kappa * R, kappa * r)

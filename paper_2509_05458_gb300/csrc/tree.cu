@@ -8,7 +8,7 @@
 // expansion level are all "split these leaves" passes. Boxes of every level
 // are then the distinct level-l prefixes of the leaves at level >= l.
 //
-// Conventions shared with the specification of the method (see DESIGN.md):
+// Conventions shared with the specification of the method:
 //   root square: centre (min+max)/2, width W = max extent * (1 + 2^-20);
 //   q = floor((x - lo)/W * 2^B) clamped, B = 31 (2D) / 21 (3D), computed
 //   with explicitly rounded operations (no contraction);
