@@ -5,7 +5,7 @@ Workload (the 2D Helmholtz configuration): k = 20, N = 100,000 points on the
 complexified bump curve t in [-40, 40] (bump height drawn in [0.3, 1.0],
 imaginary part 0.5*sign(t)*max(|t|-4, 0)), single + double layer with the
 curve's analytic normals, complex Gaussian densities, eps = 1e-6, leaf size
-64. Inputs are synthetic (seeded, cfmm_inputs.config2). The headline runs in
+64. Inputs are synthetic (seeded, cfmm_inputs.curve2d_long). The headline runs in
 MIXED precision (near field in complex64 arithmetic, translations FP64); the
 same pass in FP64 is reported beside it, and both are checked against the
 direct sum on 100 sampled targets.
@@ -151,7 +151,7 @@ def run_gpu(args):
     import torch
 
     import paper_2509_05458_gb300 as cf
-    from cfmm_inputs import config2, config3, densities
+    from cfmm_inputs import curve2d_long, plane3d, densities
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -159,7 +159,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    g = config2(N_POINTS, seed=0) if DIM == 2 else config3(N_POINTS, seed=0)
+    g = curve2d_long(N_POINTS, seed=0) if DIM == 2 else plane3d(N_POINTS, seed=0)
     dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2 if DLP else 1)
     re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
     nre = torch.from_numpy(g.nrm_re).to(dev) if DLP else None
@@ -335,7 +335,7 @@ def run_batch(args):
 
     import paper_2509_05458_gb300 as cf
     from paper_2509_05458_gb300.autotune import tune_leaf_size
-    from cfmm_inputs import config3, config4_uneven, densities
+    from cfmm_inputs import plane3d, plane3d_uneven, densities
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -343,7 +343,7 @@ def run_batch(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    geoms = [config3(N_POINTS, seed=0)] + config4_uneven()
+    geoms = [plane3d(N_POINTS, seed=0)] + plane3d_uneven()
     nrhs = [64] + [1] * (len(geoms) - 1)
     kernel = cf.HELMHOLTZ | cf.SLP
     main = torch.cuda.Stream(device=dev)
@@ -657,9 +657,9 @@ def cpu_baseline(args):
     if DIM == 3:
         code = ("import sys,time,json; sys.path.insert(0, %r)\n"
                 "import numpy as np\n"
-                "from cfmm_inputs import config3, densities\n"
+                "from cfmm_inputs import plane3d, densities\n"
                 "from oracle.direct import direct\n"
-                "g = config3(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=1)\n"
+                "g = plane3d(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=1)\n"
                 "pts = g.re + 1j * g.im; idx = np.arange(200)\n"
                 "t=time.perf_counter(); direct(3, %d, %r, pts, pts[idx], sigma=d[0,0]); t=time.perf_counter()-t\n"
                 "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, N_POINTS, KERNEL, KAPPA)
@@ -672,9 +672,9 @@ def cpu_baseline(args):
                 "sample": f"oracle direct sum (numpy), 200 targets against all {o['n']} sources: {o['s']:.1f} s; "
                           "points/s = targets evaluated per second"}
     code = ("import sys,time,json; sys.path.insert(0, %r)\n"
-            "from cfmm_inputs import config2, densities\n"
+            "from cfmm_inputs import curve2d_long, densities\n"
             "from oracle import fmm2d\n"
-            "g = config2(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=2)\n"
+            "g = curve2d_long(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=2)\n"
             "t=time.perf_counter(); fmm2d.apply(g.re, g.im, 1, %r, %r, %d, sigma=d[0,0], tau=d[0,1], "
             "nrm_re=g.nrm_re, nrm_im=g.nrm_im); t=time.perf_counter()-t\n"
             "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, args.cpu_n, KAPPA, EPS, LEAF)

@@ -24,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["curve2d", "surface3d", "densities", "halton", "Geometry",
-           "config1", "config2", "config3", "config4_uneven"]
+           "curve2d_short", "curve2d_long", "plane3d", "plane3d_uneven"]
 
 
 class Geometry:
@@ -126,23 +126,26 @@ def densities(n, seed=0, nrhs=1, ncomp=1):
 
 # ---- the named workloads -------------------------------------------------
 
-def config1(n=4000, seed=0):
-    """2D Laplace SLP workload: t in [-10, 10], bump 0.3, slope 0.5."""
+def curve2d_short(n=4000, seed=0):
+    """The 2D Laplace SLP workload: N = 4000 on t in [-10, 10], bump height 0.3,
+    imaginary slope 0.5 beyond |t| = 4."""
     return curve2d(n, seed=seed, t_half=10.0, height=0.3, slope=0.5, t_flat=4.0)
 
 
-def config2(n=100000, seed=0):
-    """2D Helmholtz SLP+DLP workload: t in [-40, 40], bump height ~ U[0.3, 1]."""
+def curve2d_long(n=100000, seed=0):
+    """The 2D Helmholtz SLP+DLP workload: N = 1e5 on t in [-40, 40], bump
+    height ~ U[0.3, 1], imaginary slope 0.5 beyond |t| = 4."""
     return curve2d(n, seed=seed, t_half=40.0, slope=0.5, t_flat=4.0,
                    random_height=(0.3, 1.0))
 
 
-def config3(n=1000000, seed=0):
-    """3D workload: complexified plane with bump, Halton points in [-20, 20]^2."""
+def plane3d(n=1000000, seed=0):
+    """The 3D workload: N = 1e6 Halton points of the complexified plane with a
+    bump over [-20, 20]^2, imaginary slope 0.4 beyond rho = 6."""
     return surface3d(n, seed=seed, half=20.0, amp=0.5, width=1.0, slope=0.4, rho0=6.0)
 
 
-def config4_uneven(count=32, seed0=100, nmin=10_000, nmax=200_000):
+def plane3d_uneven(count=32, seed0=100, nmin=10_000, nmax=200_000):
     """The uneven batch of the batched 3D Helmholtz workload: `count` surfaces
     of the ``surface3d`` family ([-20, 20]^2, bump 0.5, rho0 = 6), geometry i
     with N log-uniform in [nmin, nmax] (drawn from seed0) and its width ~

@@ -4,7 +4,7 @@ the oracle FMM, and the direct sum within eps (Eq. relerr)."""
 import numpy as np
 import pytest
 
-from cfmm_inputs import config1, config2, curve2d, densities
+from cfmm_inputs import curve2d_short, curve2d_long, curve2d, densities
 from oracle import fmm2d, tree as tr
 from oracle.direct import direct, relerr_paper, relerr_l2
 from tests.gpu_util import gpu_plan, to_dev
@@ -22,8 +22,8 @@ def _run(cuda, g, ker, kap, eps, leaf, dlp, nrhs=1, sep=1, seed=0):
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
-def test_laplace_config1_vs_oracle_fmm(cuda, eps):
-    g = config1()
+def test_laplace_short_curve_vs_oracle_fmm(cuda, eps):
+    g = curve2d_short()
     p, dens, u = _run(cuda, g, 0, 0.0, eps, 32, False)
     uo, T = fmm2d.apply(g.re, g.im, 0, 0.0, eps, 32, sigma=dens[0, 0])
     assert list(p.orders()) == fmm2d.expansion_orders(T, 0, 0.0, eps)
@@ -73,9 +73,9 @@ def test_repeat_apply_bitwise_identical(cuda):
     assert np.array_equal(a, b)
 
 
-def test_config2_full_size_sampled(cuda):
+def test_long_curve_full_size_sampled(cuda):
     """2D Helmholtz k=20, N=1e5, SLP+DLP, leaf 64, eps 1e-6: sampled targets vs direct."""
-    g = config2()
+    g = curve2d_long()
     eps = 1e-6
     p, dens, u = _run(cuda, g, 1, 20.0, eps, 64, True)
     rng = np.random.default_rng(1)
@@ -105,10 +105,10 @@ def test_mixed_precision_fmm(cuda, ker, kap):
     assert relerr_paper(u, u0, dens[0].reshape(-1)) <= eps
 
 
-def test_config2_mixed_full_size_sampled(cuda):
+def test_long_curve_mixed_full_size_sampled(cuda):
     """The benchmark workload in MIXED precision meets eps = 1e-6 on sampled targets."""
     import paper_2509_05458_gb300 as cf
-    g = config2()
+    g = curve2d_long()
     eps = 1e-6
     p = gpu_plan(cf, g, 1, 20.0, eps, cuda, 64, dlp=True, precision=cf.MIXED)
     dens = densities(g.n, seed=0, nrhs=1, ncomp=2)

@@ -1,11 +1,11 @@
 """GPU 3D Laplace FMM (Sec. 5.2 operators, Sec. 6.4 steps) against the oracle:
 same tree and P, element-by-element relative l2 <= 1e-12 against the oracle
-FMM; within eps of the direct sum; the config-3 surface family at N = 1e5 on
+FMM; within eps of the direct sum; the plane-with-bump surface family at N = 1e5 on
 sampled targets."""
 import numpy as np
 import pytest
 
-from cfmm_inputs import surface3d, config3, densities
+from cfmm_inputs import surface3d, plane3d, densities
 from oracle import fmm3d
 from oracle.direct import direct, relerr_paper, relerr_l2
 from tests.gpu_util import gpu_plan, to_dev
@@ -33,7 +33,7 @@ def test_laplace3d_vs_oracle_fmm(cuda, eps):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_laplace3d_surface_1e5_sampled(cuda, precision):
     import paper_2509_05458_gb300 as cf
-    g = config3(100_000)
+    g = plane3d(100_000)
     eps = 1e-3
     p = gpu_plan(cf, g, 0, 0.0, eps, cuda, 64, precision=precision)
     dens = densities(g.n, seed=4, nrhs=1, ncomp=1)

@@ -4,14 +4,14 @@ rounding (Eq. complexify_center_average)."""
 import numpy as np
 import pytest
 
-from cfmm_inputs import config1, curve2d, surface3d
+from cfmm_inputs import curve2d_short, curve2d, surface3d
 from oracle import tree as tr
 from tests.gpu_util import gpu_plan, compare_tree
 
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    ("2d-lap-cfg1", lambda: config1(), 2, 0, 0.0, 32, 1),
+    ("2d-lap-short-curve", lambda: curve2d_short(), 2, 0, 0.0, 32, 1),
     ("2d-lap-sep2", lambda: curve2d(3000, seed=2, t_half=10.0, height=0.6), 2, 0, 0.0, 16, 2),
     ("2d-helm-k20", lambda: curve2d(3000, seed=3, t_half=10.0, height=0.5), 2, 1, 20.0, 32, 1),
     ("2d-ragged", lambda: curve2d(1237, seed=9, t_half=3.0, height=1.5), 2, 0, 0.0, 7, 1),

@@ -14,14 +14,14 @@ import math
 import numpy as np
 import pytest
 
-from cfmm_inputs import config1, curve2d, densities
+from cfmm_inputs import curve2d_short, curve2d, densities
 from oracle import fmm2d, tree as tr
 from oracle.direct import direct, relerr_paper, relerr_l2, LAPLACE, HELMHOLTZ
 
 
 @pytest.fixture(scope="module")
-def cfg1():
-    g = config1()
+def short_curve():
+    g = curve2d_short()
     pts = g.re + 1j * g.im
     s = densities(g.n, seed=0)[0, 0]
     u0 = direct(2, LAPLACE, 0.0, pts, pts, sigma=s)
@@ -29,8 +29,8 @@ def cfg1():
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
-def test_laplace_config1_meets_eps(cfg1, eps):
-    g, s, u0 = cfg1
+def test_laplace_short_curve_meets_eps(short_curve, eps):
+    g, s, u0 = short_curve
     u, T = fmm2d.apply(g.re, g.im, LAPLACE, 0.0, eps, 32, sigma=s)
     assert relerr_paper(u, u0, s) <= eps
     assert T.nlevels >= 5
