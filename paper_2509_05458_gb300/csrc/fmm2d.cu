@@ -557,63 +557,6 @@ __global__ void k_m2l(M2LArgs A, int first_box, const cd* __restrict__ mp, cd* _
     for (int c = threadIdx.x; c < nc; c += blockDim.x) o[c] = acc[c];
 }
 
-// Helmholtz M2L, warp-parallel over sources: each of the 4 warps of a CTA
-// takes every 4th List-2 source of the box; a lane owns outputs
-// j = lane + 32 o (o < kM2LOut) and accumulates the Toeplitz sums
-// L_j += sum_n T_{n-j} M_n in registers; the four warps' partial sums are
-// combined in a fixed order at the end (bitwise reproducible).
-constexpr int kM2LWarps = 4;
-
-template <int kM2LOut>   // outputs per lane: 2P+1 <= 32 kM2LOut
-__global__ void __launch_bounds__(kM2LWarps * 32) k_m2l_helm(M2LArgs A, int first_box, const cd* __restrict__ mp,
-                                                               cd* __restrict__ loc) {
-    extern __shared__ cd sm[];
-    int b = first_box + blockIdx.x;
-    int rhs = blockIdx.y;
-    int l = A.blevel[b];
-    int P = A.Plev[l];
-    int nc = 2 * P + 1, nt = 4 * P + 1;
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    cd* my_src = sm + (size_t)w * (nc + nt);
-    cd* my_tab = my_src + nc;
-    cd acc[kM2LOut];
-#pragma unroll
-    for (int o = 0; o < kM2LOut; ++o) acc[o] = cd{0, 0};
-    int q0 = A.loff[b], q1 = A.loff[b + 1];
-    for (int q = q0 + w; q < q1; q += kM2LWarps) {
-        int s = A.lent[q];
-        const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
-        const cd* t = A.tab + A.tbase[l] + (int64_t)(q - A.tq0[l]) * nt;
-        __syncwarp();
-        for (int c = lane; c < nc; c += 32) my_src[c] = m[c];
-        for (int c = lane; c < nt; c += 32) my_tab[c] = t[c];
-        __syncwarp();
-        // L_j += sum_n T[n - j + 2P] M[n + P],  j = lane + 32 o - P
-        for (int nn = 0; nn < nc; ++nn) {
-            cd mv = my_src[nn];
-#pragma unroll
-            for (int o = 0; o < kM2LOut; ++o) {
-                int c = lane + 32 * o;
-                if (c < nc) acc[o] += my_tab[nn - c + nc - 1] * mv;
-            }
-        }
-    }
-    __syncthreads();
-    cd* red = sm;                    // reuse: [warp][nc]
-#pragma unroll
-    for (int o = 0; o < kM2LOut; ++o) {
-        int c = lane + 32 * o;
-        if (c < nc) red[(size_t)w * nc + c] = acc[o];
-    }
-    __syncthreads();
-    cd* out = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        cd v = red[c];
-        for (int ww = 1; ww < kM2LWarps; ++ww) v += red[(size_t)ww * nc + c];
-        out[c] = v;
-    }
-}
-
 // Helmholtz M2L split into chunks of List-2 entries: one CTA per chunk, thread
 // (c, s) owns output c for source lane s; the S lanes' sums are combined in a
 // fixed order into one partial sum per chunk, and k_m2l_reduce adds the chunks
@@ -1151,8 +1094,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
                    (const void*)k_m2m<CFMM_LAPLACE>, (const void*)k_m2m<CFMM_HELMHOLTZ>,
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l<CFMM_LAPLACE>, (const void*)k_m2l<CFMM_HELMHOLTZ>,
-                   (const void*)k_m2l_helm<1>, (const void*)k_m2l_helm<2>, (const void*)k_m2l_helm<4>,
-                   (const void*)k_m2l_helm<8>, (const void*)k_m2l_chunk,
+                   (const void*)k_m2l_chunk,
                    (const void*)k_eval<CFMM_LAPLACE>, (const void*)k_eval<CFMM_HELMHOLTZ>})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
 }

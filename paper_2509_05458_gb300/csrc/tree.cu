@@ -177,11 +177,6 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int* __re
     }
 }
 
-__global__ void k_iota(int* v, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = i;
-}
-
 // sorts keys (in place, via ping-pong) with payload; nbits = significant bits
 static void radix_sort(DevBuf<uint64_t>& keys, DevBuf<int>& vals, int n, int nbits, cudaStream_t st) {
     if (n <= 1) return;
