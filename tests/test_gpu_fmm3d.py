@@ -42,3 +42,17 @@ def test_laplace3d_surface_1e5_sampled(cuda, precision):
     pts = g.re + 1j * g.im
     u0 = direct(3, 0, 0.0, pts, pts[idx], sigma=dens[0, 0])
     assert np.linalg.norm(u[idx] - u0) / np.linalg.norm(u0) <= eps
+
+
+def test_laplace3d_single_layer_vs_oracle_fmm(cuda):
+    """The single-layer column P2M (one lane per harmonic column, scaled into the
+    solid-harmonic basis) at separation 2, against the oracle FMM."""
+    import paper_2509_05458_gb300 as cf
+    g = surface3d(1500, seed=2, half=4.0, amp=0.5, width=1.0, slope=0.3, rho0=1.0)
+    eps = 1e-6
+    p = gpu_plan(cf, g, 0, 0.0, eps, cuda, 48, sep=2)
+    dens = densities(g.n, seed=6, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    uo, T = fmm3d.apply(g.re, g.im, eps, 48, k=2, sigma=dens[0, 0])
+    assert list(p.orders()) == fmm3d.expansion_orders(T, eps)
+    assert relerr_l2(u[0], uo) <= 1e-12
