@@ -17,7 +17,14 @@ centres, Lists 1-4, expansion orders, translation tables) + cfmm_apply
 value = points per second of that pass; apply_only = the same for the apply
 alone on a resident plan (the GMRES matvec).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Other lines (--workload): helm3d / lap3d, the 3D Helmholtz (k=10) and Laplace
+surface workloads at N = 1e6; batch3d, one 3D Helmholtz surface (k=15, N=2e5)
+with 64 right-hand sides plus 32 uneven surfaces, replayed as one CUDA graph;
+serve, the serving loop on a Poisson stream of 2D and 3D requests (points/s
+with p50/p99 latency). --n, --sep and --leaf override the workload for
+profiler captures and parameter sweeps (not bench lines).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Multi-GPU: replicas (each rank runs its own copy of the workload), weak scaling.
 """
 from __future__ import annotations
