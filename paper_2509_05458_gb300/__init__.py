@@ -58,6 +58,8 @@ def lib():
                           "`python -c 'import __graft_entry__ as g; g.build()'`")
     L = C.CDLL(library_path)
     vp, i64, dbl, ci = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    L.cfmm_plan.restype = vp
+    L.cfmm_plan.argtypes = [ci, ci, dbl, dbl, vp, vp, i64]
     L.cfmm_plan_ex.restype = vp
     L.cfmm_plan_ex.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, C.POINTER(_Opts)]
     L.cfmm_apply.restype = ci

@@ -46,3 +46,14 @@ def test_binding_rejects_bad_arguments_without_gpu(libpath):
         cf.plan(2, cf.HELMHOLTZ, -1.0, 1e-6, z, z)       # k <= 0
     with pytest.raises(cf.CfmmError):
         cf.plan(2, cf.LAPLACE, 0.0, 1.0, z, z)           # eps out of range
+
+
+def test_binding_declares_every_entry_point(libpath):
+    """The ctypes binding sets a result type for every function of the header
+    (a missing one would silently truncate 64-bit pointers or sizes)."""
+    import paper_2509_05458_gb300 as cf
+    src = open(os.path.join(ROOT, "paper_2509_05458_gb300", "__init__.py")).read()
+    bound = set(re.findall(r"L\.(cfmm_[a-z0-9_]+)\.restype", src))
+    missing = [n for n in _declared() if n not in bound]
+    assert not missing, missing
+    cf.lib()
