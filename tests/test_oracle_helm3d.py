@@ -242,3 +242,23 @@ def test_top_level_deeper_than_initial_tree():
     assert T.l0 == 2 and T.nlevels == 3
     assert P[T.l0] <= tr.P_MAX_3D and all(P[l] > tr.P_MAX_3D for l in range(T.l0))
     assert min(T.box_level[b] for b in range(T.nboxes) if T.box_leaf[b]) >= T.l0
+
+
+def test_laplace_multipole_from_schmidt_harmonics():
+    """The identity the CUDA path's single-layer 3D Laplace P2M uses: with
+    Z_n^m = e_m s_n^m U_n^m (s = sqrt((n-|m|)!(n+|m|)!), e_m = (-1)^m for
+    m < 0, else 1), the solid-harmonic multipole (-1)^m sum sigma U_n^{-m}(y)
+    equals (e_m / s_n^m) sum sigma Z_n^{-m}(y)."""
+    rng = np.random.default_rng(11)
+    P = 14
+    y = rng.normal(size=(25, 3)) * 0.4 + 0.05j * rng.normal(size=(25, 3))
+    sig = rng.normal(size=(1, 25)) + 1j * rng.normal(size=(1, 25))
+    M = fmm3d.Laplace3D.p2m(P, y, sig)[0]
+    Z = H.ylm(P, y)
+    for n in range(P + 1):
+        for m in range(-n, n + 1):
+            am = abs(m)
+            s = math.sqrt(math.factorial(n - am) * math.factorial(n + am))
+            e = (-1.0) ** m if m < 0 else 1.0
+            ref = e / s * (sig[0] @ Z[idx(n, -m)])
+            assert abs(M[idx(n, m)] - ref) <= 1e-12 * max(1.0, abs(ref))
