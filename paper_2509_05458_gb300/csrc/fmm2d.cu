@@ -985,7 +985,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         if (!boxes.empty())
             upload(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(), st);
     }
-    pt.mark("setup:p2l+rows");
+    pt.mark("setup:p2l");
     // binomials C(n, k), n, k <= 2 maxP + 1 (exact integers up to 2^53, then rounded)
     S->NB = 2 * maxP + 2;
     {
@@ -1026,7 +1026,9 @@ void fmm2d_setup(cfmm_plan_s* P) {
             int* dq = plan_scratch().take_n<int>(qbox.size());
             upload(dq, qbox.data(), sizeof(int) * qbox.size(), st);
             int nq = ql - qf;
-            k_tab_m2l<<<(nq + 127) / 128, 128, 0, st>>>(nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
+            // one warp per block: the few thousand pairs (one thread each) spread over
+            // every SM instead of filling a fraction of them with larger blocks
+            k_tab_m2l<<<(nq + 31) / 32, 32, 0, st>>>(nq, dq, T.lent[1].get(), T.level.get(), S->dPlev.get(),
                                                        S->d_m2l_base.get(), S->d_m2l_q0.get(), T.cen_re.get(),
                                                        T.cen_im.get(), P->kappa, S->t_m2l.get(), qf);
             CFMM_LAUNCHED();
@@ -1081,7 +1083,7 @@ void fmm2d_setup(cfmm_plan_s* P) {
         upload(S->shift_off.get(), so.data(), sizeof(int64_t) * T.nboxes, st);
         int lo = T.level_off[std::min(S->l0 + 1, T.nlevels)], hi = T.nboxes;
         if (hi > lo) {
-            k_tab_shift<<<(hi - lo + 63) / 64, 64, 0, st>>>(lo, hi, T.parent.get(), T.level.get(), S->dPlev.get(),
+            k_tab_shift<<<(hi - lo + 31) / 32, 32, 0, st>>>(lo, hi, T.parent.get(), T.level.get(), S->dPlev.get(),
                                                            S->shift_off.get(), T.cen_re.get(), T.cen_im.get(),
                                                            P->kappa, S->t_shift.get());
             CFMM_LAUNCHED();
