@@ -39,9 +39,11 @@ Readings:
   grows with the top level like exp(0.56 kappa g), a third of the exponent
   sqrt(3) kappa g of the rule, so c_3 = 2 still bounds the growth by
   (eps/2^-52)^0.65; at kappa = 15 the level it picks met eps = 1e-6 with
-  1.4e-7, at a third of the cost of the c_3 = 1 level). In 3D it is also at
-  least the coarsest level with P_l <= 63, the order limit of the CUDA
-  translation tables. Leaves above l0 are split
+  1.4e-7, at a third of the cost of the c_3 = 1 level). When no level of the
+  tree qualifies (a shallow tree), the spread below the deepest level is
+  taken to halve with each further level (Im x is Lipschitz in Re x, so a
+  box's spread scales with its width), and l0 is the first level where that
+  extrapolated spread meets the bound. Leaves above l0 are split
   down to l0 and the tree is re-balanced. M2L at l0 runs over all non-near
   pairs of l0 boxes.
 """
@@ -315,26 +317,21 @@ def choose_l0(T, im_sorted, kappa, eps, helmholtz):
     if maxl < 1:
         return 1
     sq = math.sqrt(T.dim)
+    gm = 0.0
     for m in range(1, maxl + 1):
         gm = 0.0
         for b in range(T.nboxes):
             lv = T.box_level[b]
             if lv == m or (lv < m and T.box_leaf[b]):
                 gm = max(gm, g[b])
-        if T.dim == 3 and nterms_helmholtz(3, T.k, eps * P_HEADROOM_HELM, kappa, T.width(m),
-                                           helm3d_pair) > P_MAX_3D:
-            continue
         if kappa * sq * gm <= tau:
             return m
-    if T.dim == 3:
-        # no level of the tree qualifies: take at least the coarsest level whose
-        # order fits, which the forced refinement of build_tree then reaches
-        m = 1
-        while m < T.B and nterms_helmholtz(3, T.k, eps * P_HEADROOM_HELM, kappa, T.width(m),
-                                           helm3d_pair) > P_MAX_3D:
-            m += 1
-        return max(maxl, m)
-    return maxl
+    # below the deepest level: the spread halves per level
+    m = maxl
+    while m < T.B and kappa * sq * gm > tau:
+        m += 1
+        gm *= 0.5
+    return m
 
 
 def build_tree(re, im, N_s, k=1, kappa=0.0, eps=1e-6, helmholtz=False, top_level=0):
@@ -479,7 +476,6 @@ def check_balance(T):
 # against (r/R)^n and undershoots by about a digit).
 P_HEADROOM = 0.1
 P_HEADROOM_HELM = 0.01
-P_MAX_3D = 63
 
 def nterms_laplace(dim, k, eps):
     """Smallest n >= 1 with (r/R)^n <= eps, R=(k+1/2)w, r=sqrt(d)/2 w."""

@@ -22,6 +22,8 @@ __all__ = ["LAPLACE", "HELMHOLTZ", "SLP", "DLP", "GREEN_SCALE", "FP64", "MIXED",
 LAPLACE, HELMHOLTZ = 0, 1
 SLP, DLP, GREEN_SCALE = 1 << 4, 1 << 5, 1 << 6
 FP64, MIXED, AUTO = 0, 1, 2
+# status codes (include/cfmm.h)
+OK, EINVAL, ENONFINITE, EGEOM, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libcfmm.so")

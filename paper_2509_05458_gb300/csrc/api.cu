@@ -266,7 +266,7 @@ void ensure_device_tables() {
     done[dev] = 1;
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -316,13 +316,6 @@ __global__ void k_unpermute(const cd* __restrict__ us, const int* __restrict__ p
     if (i >= n) return;
     cd v = us[(int64_t)r * n + i];
     out[(int64_t)r * n + perm[i]] = v * scale;
-}
-
-static cd green_scale(int dim, int ker) {
-    const double pi = 3.14159265358979323846;
-    if (dim == 2 && ker == CFMM_LAPLACE) return cd{-1.0 / (2.0 * pi), 0.0};
-    if (dim == 2) return cd{0.0, 0.25};
-    return cd{1.0 / (4.0 * pi), 0.0};
 }
 
 static void record(cfmm_plan_s* P, int i) {
@@ -734,20 +727,7 @@ int cfmm_direct(int dim, int kernel, double k, const double* src_re, const doubl
         KParams K{sr.get(), si.get(), dlp ? nr.get() : nullptr, dlp ? ni.get() : nullptr, tr.get(), ti.get(), m, n,
                   slp ? d : nullptr, dlp ? d + (slp ? m : 0) : nullptr, ncomp * m, slp, dlp, k};
         launch_direct(dim, ker, K, reinterpret_cast<cd*>(out), nrhs, st, precision == CFMM_MIXED);
-        if (kernel & CFMM_GREEN_SCALE) {
-            DevBuf<int> id;
-            std::vector<int> h(n);
-            for (int64_t i = 0; i < n; ++i) h[i] = (int)i;
-            id.alloc(n);
-            CFMM_CUDA(cudaMemcpyAsync(id.get(), h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-            DevBuf<cd> tmp;
-            tmp.alloc((size_t)n * nrhs);
-            CFMM_CUDA(cudaMemcpyAsync(tmp.get(), out, sizeof(cd) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-            dim3 g((unsigned)((n + 255) / 256), nrhs);
-            k_unpermute<<<g, 256, 0, st>>>(tmp.get(), id.get(), n, green_scale(dim, ker), reinterpret_cast<cd*>(out));
-            CFMM_LAUNCHED();
-            CFMM_CUDA(cudaStreamSynchronize(st));
-        }
+        if (kernel & CFMM_GREEN_SCALE) launch_scale_inplace(reinterpret_cast<cd*>(out), n * nrhs, green_scale(dim, ker), st);
         CFMM_CUDA(cudaStreamSynchronize(st));
     });
 }
@@ -757,9 +737,6 @@ int cfmm_direct_noalloc(int dim, int kernel, double k, const double* src_re, con
                         const double* trg_im, int64_t n, const double* densities, int nrhs, double* out,
                         void* stream) {
     return guarded([&] {
-        CFMM_REQUIRE(is_device_ptr(src_re) && is_device_ptr(trg_re) && is_device_ptr(densities) &&
-                         is_device_ptr(out),
-                     CFMM_EINVAL, "cfmm_direct_noalloc takes device pointers");
         direct_noalloc(dim, kernel, k, src_re, src_im, nrm_re, nrm_im, m, trg_re, trg_im, n, densities, nrhs, out,
                        stream);
     });

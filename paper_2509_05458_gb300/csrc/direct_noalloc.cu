@@ -46,6 +46,12 @@ __global__ void k_scale_inplace(cd* __restrict__ v, int64_t cnt, cd s) {
     if (i < cnt) v[i] = v[i] * s;
 }
 
+void launch_scale_inplace(cd* v, int64_t cnt, cd s, cudaStream_t st) {
+    if (cnt <= 0) return;
+    k_scale_inplace<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(v, cnt, s);
+    CFMM_LAUNCHED();
+}
+
 // device address of the scratch array, looked up once per device
 static double* scratch_address() {
     static std::mutex mu;
@@ -79,6 +85,9 @@ int direct_noalloc(int dim, int kernel, double k, const double* src_re, const do
     bool dlp = (kernel & CFMM_DLP) != 0;
     bool slp = (kernel & CFMM_SLP) != 0 || !dlp;
     CFMM_REQUIRE(!dlp || (nrm_re && nrm_im), CFMM_EINVAL, "double layer needs normals");
+    // the first CUDA call of this entry point: everything above is host-only
+    CFMM_REQUIRE(is_device_ptr(src_re) && is_device_ptr(trg_re) && is_device_ptr(densities) && is_device_ptr(out),
+                 CFMM_EINVAL, "cfmm_direct_noalloc takes device pointers");
     ensure_device_tables();
     double* base = scratch_address();
     cudaStream_t st = (cudaStream_t)stream;
@@ -105,14 +114,7 @@ int direct_noalloc(int dim, int kernel, double k, const double* src_re, const do
     KParams K{sr, si, dlp ? nr : nullptr, dlp ? ni : nullptr, tr, ti, m, n,
               slp ? d : nullptr, dlp ? d + (slp ? m : 0) : nullptr, ncomp * m, slp, dlp, k};
     launch_direct(dim, ker, K, reinterpret_cast<cd*>(out), nrhs, st);
-    if (kernel & CFMM_GREEN_SCALE) {
-        const double pi = 3.14159265358979323846;
-        cd s = dim == 2 ? (ker == CFMM_LAPLACE ? cd{-1.0 / (2.0 * pi), 0.0} : cd{0.0, 0.25})
-                        : cd{1.0 / (4.0 * pi), 0.0};
-        int64_t cnt = n * nrhs;
-        k_scale_inplace<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(reinterpret_cast<cd*>(out), cnt, s);
-        CFMM_LAUNCHED();
-    }
+    if (kernel & CFMM_GREEN_SCALE) launch_scale_inplace(reinterpret_cast<cd*>(out), n * nrhs, green_scale(dim, ker), st);
     return 0;
 }
 

@@ -47,7 +47,21 @@ void fmm2d_setup(cfmm_plan_s* P);
 void fmm2d_release(cfmm_plan_s* P);
 void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
 
-// direct sum with library-owned fixed scratch (direct_noalloc.cu)
+// Green's function constants of CFMM_GREEN_SCALE: -1/(2 pi) (2D Laplace),
+// i/4 (2D Helmholtz), 1/(4 pi) (3D Laplace and Helmholtz)
+inline cd green_scale(int dim, int ker) {
+    const double pi = 3.14159265358979323846;
+    if (dim == 2 && ker == CFMM_LAPLACE) return cd{-1.0 / (2.0 * pi), 0.0};
+    if (dim == 2) return cd{0.0, 0.25};
+    return cd{1.0 / (4.0 * pi), 0.0};
+}
+// true for device (or managed) memory (api.cu); a CUDA call
+bool is_device_ptr(const void* p);
+// v[i] *= s for i < cnt (direct_noalloc.cu)
+void launch_scale_inplace(cd* v, int64_t cnt, cd s, cudaStream_t st);
+
+// direct sum with library-owned fixed scratch (direct_noalloc.cu); validates
+// every argument it can without a CUDA call before touching the GPU
 int direct_noalloc(int dim, int kernel, double k, const double* src_re, const double* src_im, const double* nrm_re,
                    const double* nrm_im, int64_t m, const double* trg_re, const double* trg_im, int64_t n,
                    const double* densities, int nrhs, double* out, void* stream);

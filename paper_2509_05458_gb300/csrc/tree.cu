@@ -1227,29 +1227,26 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
             l0 = top_level_opt;
         } else if (helm) {
             // tau = c_d ln(eps / 2^-52), c_2 = 1, c_3 = 2 (calibrated on the 2D curve
-            // and 3D surface workloads); 3D also needs P_l <= kMaxP3Top (the
-            // order limit of the translation tables)
+            // and 3D surface workloads): the coarsest level whose boxes (and coarser
+            // leaves) have kappa sqrt(d) g <= tau; below the deepest level the spread
+            // is taken to halve per level (Im x Lipschitz in Re x)
             double tau = (dim == 2 ? 1.0 : 2.0) * std::log(P->eps / std::ldexp(1.0, -52));
             int maxl = P->tree.nlevels - 1;
-            l0 = maxl < 1 ? 1 : maxl;
-            bool found = false;
-            auto p_fits = [&](int m) {
-                return dim != 3 || nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -m)) <= kMaxP3Top;
-            };
-            for (int m = 1; m <= maxl; ++m) {
-                if (!p_fits(m)) continue;
-                if (P->kappa * std::sqrt((double)dim) * spread[m] <= tau) {
+            double sq = std::sqrt((double)dim);
+            l0 = 0;
+            for (int m = 1; m <= maxl; ++m)
+                if (P->kappa * sq * spread[m] <= tau) {
                     l0 = m;
-                    found = true;
                     break;
                 }
-            }
-            if (!found && dim == 3 && maxl >= 1) {
-                // no level of the tree qualifies: take at least the coarsest level
-                // whose order fits; the forced refinement below reaches it
-                int m = 1;
-                while (m < B && !p_fits(m)) ++m;
-                l0 = std::max(l0, m);
+            if (l0 == 0) {
+                int m = maxl < 1 ? 1 : maxl;
+                double gm = maxl < 1 ? 0.0 : spread[maxl];
+                while (m < B && P->kappa * sq * gm > tau) {
+                    ++m;
+                    gm *= 0.5;
+                }
+                l0 = m;
             }
         }
         // boxes are stored level-major, so the leaf with the smallest box index

@@ -32,3 +32,23 @@ def compare_tree(T, tr_gpu, lists_gpu):
         for b in range(T.nboxes):
             got = list(ent[off[b]:off[b + 1]])
             assert got == ref[b], (w + 1, b, got, ref[b])
+
+
+def _direct_chunk(args):
+    from oracle.direct import direct
+    dim, ker, kap, pts, trg, sigma, tau, nrm, green = args
+    return direct(dim, ker, kap, pts, trg, sigma=sigma, tau=tau, nrm=nrm, green_scale=green)
+
+
+def direct_sampled(dim, ker, kap, pts, idx, sigma=None, tau=None, nrm=None, green=False, workers=None):
+    """The oracle's direct sum at the targets pts[idx] against all points, split
+    over a process pool started with `spawn` (safe after CUDA is initialised)."""
+    import concurrent.futures as fut
+    import multiprocessing as mp
+    import os
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    parts = np.array_split(np.asarray(idx), workers)
+    jobs = [(dim, ker, kap, pts, pts[p], sigma, tau, nrm, green) for p in parts if len(p)]
+    with fut.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_direct_chunk, jobs))
+    return np.concatenate(res, axis=-1)

@@ -86,6 +86,24 @@ def test_other_calls_reject_bad_arguments_without_gpu():
     assert L.cfmm_destroy(None) == 0
 
 
+def test_direct_noalloc_rejects_oversized_without_gpu():
+    """cfmm_direct_noalloc checks its sizes and arguments on the host before its
+    first CUDA call: with host pointers and no GPU the size limit is what it
+    reports."""
+    cf, L = _lib()
+    m = 40000
+    x = np.zeros((m, 2))
+    d = np.zeros(2 * m)
+    h = x.ctypes.data
+    st = L.cfmm_direct_noalloc(2, cf.LAPLACE | cf.SLP, 0.0, h, h, None, None, m, h, h, 8, d.ctypes.data, 1,
+                               d.ctypes.data, None)
+    assert st == EINVAL
+    assert "32768" in L.cfmm_last_error().decode()
+    st = L.cfmm_direct_noalloc(4, cf.LAPLACE | cf.SLP, 0.0, h, h, None, None, 8, h, h, 8, d.ctypes.data, 1,
+                               d.ctypes.data, None)
+    assert st == EINVAL and "dim" in L.cfmm_last_error().decode()
+
+
 def _geom_dev(cuda, n=3000, seed=5):
     import torch
     g = curve2d(n, seed=seed, t_half=10.0, height=0.5)

@@ -88,11 +88,12 @@ def test_helm3d_repeat_bitwise(cuda):
 
 
 def test_helm3d_top_level_deeper_than_initial_tree(cuda):
-    """A shallow initial tree whose levels all need orders above the 3D limit:
-    both sides refine to the coarsest level whose order fits."""
+    """A shallow initial tree (leaf 700 on 1500 points) none of whose levels
+    meets the top-level bound: both sides extrapolate the spread below the
+    deepest level and refine to the level it picks."""
     import paper_2509_05458_gb300 as cf
-    g = _geom()
-    kap, eps, leaf = 20.0, 1e-3, 700
+    g = surface3d(1500, seed=2, half=4.0, amp=0.5, width=1.0, slope=0.8, rho0=1.0)
+    kap, eps, leaf = 15.0, 1e-3, 700
     p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2)
     T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True)
     assert p.info()["l0"] == T.l0 == 2
@@ -103,21 +104,47 @@ def test_helm3d_top_level_deeper_than_initial_tree(cuda):
     assert relerr_l2(u[0], uo[0]) <= 1e-12
 
 
-def test_helm3d_top_order_above_57(cuda):
-    """kappa = 25: the top level has P = 59, where the translation kernel keeps
-    its accumulator in global scratch as well as its coaxial work arrays."""
+# expansion order limit of the CUDA 3D translation kernels (a property of the
+# library, not of the method)
+GPU_MAX_ORDER_3D = 63
+
+
+def test_helm3d_order_above_limit_unsupported(cuda):
+    """Where the top-level rule picks a level whose order exceeds the library's
+    3D limit, the plan fails with CFMM_EUNSUPPORTED (the oracle has no limit)."""
     import paper_2509_05458_gb300 as cf
     g = _geom()
     kap, eps, leaf = 25.0, 1e-6, 64
-    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2)
     T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True)
+    assert H.expansion_orders(T, kap, eps)[T.l0] > GPU_MAX_ORDER_3D
+    with pytest.raises(cf.CfmmError) as e:
+        gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2)
+    assert e.value.status == cf.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kap,eps,leaf", [(20.0, 1e-3, 700), (25.0, 1e-6, 64)])
+def test_helm3d_explicit_top_level(cuda, kap, eps, leaf):
+    """The same explicit top level on both sides where the rule's own level
+    needs an order above the library's limit: a top level below a shallow
+    initial tree (leaf 700), and a top-level order above 57 (kappa = 25, P = 59),
+    where the translation kernel keeps its accumulator in global scratch as
+    well as its coaxial work arrays."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    top = 2
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2, top_level=top)
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True, top_level=top)
     orders = H.expansion_orders(T, kap, eps)
-    assert p.info()["l0"] == T.l0 and orders[T.l0] > 57
+    assert p.info()["l0"] == T.l0 == top
+    assert orders[T.l0] <= GPU_MAX_ORDER_3D
+    assert min(T.box_level[b] for b in range(T.nboxes) if T.box_leaf[b]) >= top
     assert list(p.orders()) == orders
     dens = densities(g.n, seed=10, nrhs=1, ncomp=1)
     u = p.apply(to_dev(dens, cuda)).cpu().numpy()
     uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
     assert relerr_l2(u[0], uo[0]) <= 1e-12
-    pts = g.re + 1j * g.im
-    u0 = direct(3, 1, kap, pts, pts, sigma=dens[0, 0])
-    assert relerr_paper(u[0], u0, dens[0].reshape(-1)) <= eps
+    if kap == 25.0:
+        assert orders[T.l0] > 57
+        pts = g.re + 1j * g.im
+        u0 = direct(3, 1, kap, pts, pts, sigma=dens[0, 0])
+        assert relerr_paper(u[0], u0, dens[0].reshape(-1)) <= eps

@@ -232,15 +232,22 @@ def test_single_leaf_is_direct():
 
 
 def test_top_level_deeper_than_initial_tree():
-    """When no level of the initial tree has an order within the 3D limit (a
-    shallow tree at high kappa), the top level is the coarsest level whose
-    order fits, and the forced refinement makes the tree reach it."""
+    """When no level of the initial tree meets the top-level bound (a shallow
+    tree: leaf 700 on 1500 points), the spread is extrapolated below the
+    deepest level by halving it per level, the top level is the first level
+    where that meets the bound, and the forced refinement reaches it."""
+    import math
     from oracle import tree as tr
-    g = surface3d(1500, seed=2, half=4.0, amp=0.5, width=1.0, slope=0.3, rho0=1.0)
-    T = tr.build_tree(g.re, g.im, 700, k=2, kappa=20.0, eps=1e-3, helmholtz=True)
-    P = H.expansion_orders(T, 20.0, 1e-3)
+    g = surface3d(1500, seed=2, half=4.0, amp=0.5, width=1.0, slope=0.8, rho0=1.0)
+    kap, eps = 15.0, 1e-3
+    T0 = tr.build_tree(g.re, g.im, 700, k=2)
+    assert T0.nlevels == 2
+    # the deepest initial level misses the bound, one level below meets it
+    tau = tr.C_TOP[3] * math.log(eps / tr.EPS_MACH)
+    g1 = float(tr.imag_spread(T0, g.im[T0.perm])[T0.box_level == 1].max())
+    assert kap * math.sqrt(3) * g1 > tau >= kap * math.sqrt(3) * g1 / 2
+    T = tr.build_tree(g.re, g.im, 700, k=2, kappa=kap, eps=eps, helmholtz=True)
     assert T.l0 == 2 and T.nlevels == 3
-    assert P[T.l0] <= tr.P_MAX_3D and all(P[l] > tr.P_MAX_3D for l in range(T.l0))
     assert min(T.box_level[b] for b in range(T.nboxes) if T.box_leaf[b]) >= T.l0
 
 

@@ -172,3 +172,54 @@ def test_top_level_rule_helmholtz():
     assert T.l0 >= 2
     # no leaf above l0
     assert np.all(T.box_level[T.box_leaf] >= T.l0)
+
+
+# ---- the "near" predicate of Sec. 6.2 pinned by counts fixed by the definitions ----
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_near_colleague_count_interior(dim, k):
+    """Same-level boxes are near exactly when they are k-colleagues: an interior
+    box has (2k+1)^d of them (itself included)."""
+    level = 4
+    I = tuple([8] * dim)
+    cnt = sum(tr.near(level, I, level, J, k) for J in np.ndindex(*([1 << level] * dim)))
+    assert cnt == (2 * k + 1) ** dim
+
+
+def test_near_boundary_hand_cases():
+    """Boxes of different levels: near means ||c_a - c_b||_inf <= k/2 (w_a + w_b),
+    with equality (touching boxes at k = 1) counting as near. Level-1 box (0, 0)
+    spans [0, 1/2]^2 (centre 1/4, width 1/2); level-2 box (2, 0) spans
+    [1/2, 3/4] x [0, 1/4] (centre 5/8): distance 3/8 = (1/2)(1/2 + 1/4)."""
+    assert tr.near(1, (0, 0), 2, (2, 0), 1)
+    assert tr.near(2, (2, 0), 1, (0, 0), 1)
+    # level-2 box (3, 0): centre 7/8, distance 5/8 > 3/8, but <= 2/2 (3/4) at k = 2
+    assert not tr.near(1, (0, 0), 2, (3, 0), 1)
+    assert tr.near(1, (0, 0), 2, (3, 0), 2)
+    # level-3 box (6, 0) spans [3/4, 7/8]: centre 13/16, distance 9/16 > (1/2)(1/2 + 1/8)
+    assert not tr.near(1, (0, 0), 3, (6, 0), 1)
+    # level-3 box (4, 5): x touches (distance 5/16 = (1/2)(5/8)), y centre 11/16 is 7/16 away
+    assert not tr.near(1, (0, 0), 3, (4, 5), 1)
+    assert tr.near(1, (0, 0), 3, (4, 3), 1)
+    # a diagonal neighbour at the same level touches at a corner
+    assert tr.near(3, (2, 2, 2), 3, (3, 3, 3), 1)
+    assert not tr.near(3, (2, 2, 2), 3, (4, 3, 3), 1)
+
+
+@pytest.mark.parametrize("dim,per_axis,k,list1,list2", [(2, 16, 1, 9, 27), (2, 16, 2, 25, 75),
+                                                         (3, 8, 1, 27, 189)])
+def test_uniform_tree_list_sizes(dim, per_axis, k, list1, list2):
+    """A complete tree (one point per finest box, leaf size 1): an interior
+    leaf whose parent's colleagues all exist has (2k+1)^d List-1 leaves and
+    (2(2k+1))^d - (2k+1)^d List-2 boxes (27 in 2D and 189 in 3D at k = 1)."""
+    ax = np.arange(per_axis) / (per_axis - 1)
+    grid = np.stack(np.meshgrid(*([ax] * dim), indexing="ij"), axis=-1).reshape(-1, dim)
+    T = tr.build_tree(grid, np.zeros_like(grid), 1, k=k)
+    level = int(round(math.log2(per_axis)))
+    assert T.nlevels == level + 1
+    assert np.sum(T.box_leaf) == per_axis ** dim
+    I = tuple([per_axis // 2 - 1] * dim)
+    b = T._index[(level, tr.encode(I, level, dim))]
+    assert len(T.lists["list1"][b]) == list1
+    assert len(T.lists["list2"][b]) == list2
+    assert T.lists["list3"][b] == [] and T.lists["list4"][b] == []

@@ -3,7 +3,9 @@ memory while they run (their device-memory budget is held by a pool, or they
 sit in a loop where cudaMalloc/cudaFree would synchronise the device). It keeps
 its scratch in a fixed array inside the library. These tests call it through
 the C ABI and check it against cfmm_direct, on two calls in a row, and check
-that an oversized request is refused. This file is collected last on purpose."""
+that an oversized request is refused (the size check comes before any CUDA
+call: tests/test_failures.py checks it without a GPU). This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 
@@ -17,11 +19,14 @@ def _t(a, dev):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
 
-@pytest.mark.parametrize("dim,ker,kap", [(2, 1, 20.0), (3, 1, 6.0), (2, 0, 0.0)])
-def test_noalloc_matches_direct_twice(cuda, dim, ker, kap):
+@pytest.mark.parametrize("green", [False, True])
+@pytest.mark.parametrize("dim,ker,kap", [(2, 1, 20.0), (3, 1, 6.0), (2, 0, 0.0), (3, 0, 0.0)])
+def test_noalloc_matches_direct_twice(cuda, dim, ker, kap, green):
+    """Both layers, with and without the Green's function constants, for all
+    four kernels."""
     import torch
     import paper_2509_05458_gb300 as cf
-    flags = ker | cf.SLP | cf.DLP
+    flags = ker | cf.SLP | cf.DLP | (cf.GREEN_SCALE if green else 0)
     for call, seed in enumerate((1, 2)):          # two calls in a row, different inputs
         g = curve2d(900 + 37 * call, seed=seed, t_half=5.0) if dim == 2 else \
             surface3d(900 + 37 * call, seed=seed, half=3.0, rho0=1.0)
