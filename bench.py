@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the complex-coordinate FMM hot path on GB300.
 
-Workload (the 2D Helmholtz configuration): k = 20, N = 100,000 points on the
-complexified bump curve t in [-40, 40] (bump height drawn in [0.3, 1.0],
-imaginary part 0.5*sign(t)*max(|t|-4, 0)), single + double layer with the
-curve's analytic normals, complex Gaussian densities, eps = 1e-6, leaf size
-64. Inputs are synthetic (seeded, cfmm_inputs.curve2d_long). The headline runs in
-MIXED precision (near field in complex64 arithmetic, translations FP64); the
-same pass in FP64 is reported beside it, and both are checked against the
-direct sum on 100 sampled targets.
+Headline workload (the 3D surface configuration): 3D Helmholtz single layer,
+k = 10, N = 1,000,000 Halton points of the complexified plane with a bump
+((x, y) in [-20, 20]^2, z = 0.5 exp(-(x^2 + y^2)), Im = 0.4 max(rho - 6, 0)
+(x, y)/rho), complex Gaussian densities, eps = 1e-6, separation k = 2, leaf
+256 (MIXED) / 128 (FP64). Inputs are synthetic (seeded, cfmm_inputs.plane3d).
+The headline runs in MIXED precision (near field and L2P in complex64
+arithmetic, translations FP64); the same pass in FP64 is reported beside it.
+Both are checked against the library's FP64 direct sum on 1,000 sampled
+targets, and, when the CPU baseline runs, against the oracle's direct sum on
+its sample.
 
 One step = one pass of the whole hot path on inputs resident in HBM:
 cfmm_plan (bounding box, Morton keys, radix sort, tree, level restriction,
@@ -17,12 +19,16 @@ centres, Lists 1-4, expansion orders, translation tables) + cfmm_apply
 value = points per second of that pass; apply_only = the same for the apply
 alone on a resident plan (the GMRES matvec).
 
-Other lines (--workload): helm3d / lap3d, the 3D Helmholtz (k=10) and Laplace
-surface workloads at N = 1e6; batch3d, one 3D Helmholtz surface (k=15, N=2e5)
-with 64 right-hand sides plus 32 uneven surfaces, replayed as one CUDA graph;
-serve, the serving loop on a Poisson stream of 2D and 3D requests (points/s
-with p50/p99 latency). --n, --sep and --leaf override the workload for
-profiler captures and parameter sweeps (not bench lines).
+Beside the headline, the same line carries the 3D Laplace pass on the same
+surface and the 2D Helmholtz curve configuration (k = 20, N = 1e5, SLP+DLP,
+eps = 1e-6, leaf 64), each MIXED and FP64 (--no-extras skips them).
+
+Other lines (--workload): lap3d / helm2d alone; batch3d, one 3D Helmholtz
+surface (k=15, N=2e5) with 64 right-hand sides plus 32 uneven surfaces,
+replayed as one CUDA graph; serve, the serving loop on a Poisson stream of 2D
+and 3D requests (points/s with p50/p99 latency). --n, --sep and --leaf
+override the workload for profiler captures and parameter sweeps (not bench
+lines).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Multi-GPU: replicas (each rank runs its own copy of the workload), weak scaling.
@@ -30,6 +36,7 @@ Multi-GPU: replicas (each rank runs its own copy of the workload), weak scaling.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -41,34 +48,77 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KAPPA, EPS, LEAF, N_POINTS = 20.0, 1e-6, 64, 100_000
-METRIC = "complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, N=1e5)"
-WORKLOAD = "2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"
-SEP, DIM, DLP = 1, 2, True
-KERNEL = 1            # 1 = Helmholtz, 0 = Laplace
-LEAF_FP64 = 64
-# --workload helm3d: the 3D Helmholtz surface configuration (a second bench line,
-# not the headline)
-W3D = dict(KAPPA=10.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
-           METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Helmholtz SLP, k=10, N=1e6)",
-           WORKLOAD="3D Helmholtz SLP k=10, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
-                    "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / 128 (FP64) "
-                    "as picked by the leaf-size autotuner")
-# --workload batch3d: the batched 3D Helmholtz configuration (one geometry with
-# 64 right-hand sides plus 32 uneven geometries, all replayed as one CUDA graph)
-W4 = dict(KAPPA=15.0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=200_000, SEP=2, DIM=3, DLP=False,
-          METRIC="complex-FMM pts/s at rel.err<=1e-6 (batched 3D Helmholtz SLP, k=15: N=2e5 x 64 RHS "
-                 "+ 32 uneven geometries, one CUDA graph)",
-          WORKLOAD="batched 3D Helmholtz SLP k=15, eps=1e-6: plane-with-bump surface N=2e5 (Halton in "
-                   "[-20,20]^2, slope 0.4) with 64 RHS, plus 32 surfaces of N log-uniform in [1e4, 2e5], "
-                   "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; separation k=2; "
-                   "leaf sizes from the autotuner per geometry")
-# --workload lap3d: the 3D Laplace surface configuration (same surface as helm3d)
-WL3D = dict(KAPPA=0.0, KERNEL=0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3, DLP=False,
-            METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Laplace SLP, N=1e6)",
-            WORKLOAD="3D Laplace SLP, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
-                     "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / 128 (FP64)")
+WORKLOADS = {
+    # the 3D surface configuration (the headline)
+    "helm3d": dict(KAPPA=10.0, KERNEL=1, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3,
+                   DLP=False,
+                   METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Helmholtz SLP, k=10, N=1e6)",
+                   WORKLOAD="3D Helmholtz SLP k=10, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
+                            "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / "
+                            "128 (FP64)"),
+    # the 3D Laplace pass on the same surface
+    "lap3d": dict(KAPPA=0.0, KERNEL=0, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=1_000_000, SEP=2, DIM=3,
+                  DLP=False,
+                  METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 3D Laplace SLP, N=1e6)",
+                  WORKLOAD="3D Laplace SLP, N=1e6 complexified plane with bump (Halton in [-20,20]^2, "
+                           "Im = 0.4 max(rho-6,0) (x,y)/rho), eps=1e-6, separation k=2, leaf 256 (MIXED) / "
+                           "128 (FP64)"),
+    # the 2D curve configuration
+    "helm2d": dict(KAPPA=20.0, KERNEL=1, EPS=1e-6, LEAF=64, LEAF_FP64=64, N_POINTS=100_000, SEP=1, DIM=2,
+                   DLP=True,
+                   METRIC="complex-FMM pts/s at rel.err<=1e-6 (mixed vs FP64 GPU; 2D Helmholtz SLP+DLP, k=20, "
+                          "N=1e5)",
+                   WORKLOAD="2D Helmholtz SLP+DLP k=20, N=1e5 complexified curve t in [-40,40], eps=1e-6, leaf 64"),
+    # the batched 3D Helmholtz configuration (one geometry with 64 right-hand
+    # sides plus 32 uneven geometries, all replayed as one CUDA graph)
+    "batch3d": dict(KAPPA=15.0, KERNEL=1, EPS=1e-6, LEAF=256, LEAF_FP64=128, N_POINTS=200_000, SEP=2, DIM=3,
+                    DLP=False,
+                    METRIC="complex-FMM pts/s at rel.err<=1e-6 (batched 3D Helmholtz SLP, k=15: N=2e5 x 64 RHS "
+                           "+ 32 uneven geometries, one CUDA graph)",
+                    WORKLOAD="batched 3D Helmholtz SLP k=15, eps=1e-6: plane-with-bump surface N=2e5 (Halton in "
+                             "[-20,20]^2, slope 0.4) with 64 RHS, plus 32 surfaces of N log-uniform in [1e4, 2e5], "
+                             "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; separation k=2; "
+                             "leaf sizes from the autotuner per geometry"),
+}
+globals().update(WORKLOADS["helm3d"])
 STEP_NAMES = ["permute", "P2M", "M2M", "M2L", "P2L", "L2L", "P2P", "M2P+L2P", "unpermute"]
+# GB300 ALU peaks derived from unit counts and the maximum SM clock (2.07 GHz):
+# 152 SMs x 2 FP64 FMA/clk x 2 flops, and 152 SMs x 128 FP32 FMA/clk x 2 flops
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+CSRC = os.path.join(ROOT, "paper_2509_05458_gb300", "csrc")
+
+
+def source_hash(files):
+    """sha256 (first 16 hex digits) of the named CUDA sources: the build a
+    profile summary under profiles/ was taken on."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_figures(name, files):
+    """key: value lines of profiles/<name>.txt, or None when the summary is
+    missing or was taken on other sources than the current ones."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    d = {}
+    for l in lines:
+        if ":" in l and not l.startswith(("#", " ")):
+            k, v = l.split(":", 1)
+            d[k.strip()] = v.strip()
+    if d.get("source_sha256") != source_hash(files):
+        return None
+    d["_path"] = "profiles/" + name
+    return d
+
+
+P2P_SOURCES = ("p2p.cu", "cfmm_special.cuh", "cfmm_common.cuh", "kernels.cuh")
+TR3H_SOURCES = ("helm3d.cu", "cfmm_special.cuh", "cfmm_common.cuh", "kernels.cuh")
 
 
 def _peaks():
@@ -153,12 +203,226 @@ def _max_over_ranks(x, ws, dev):
     return float(t.item())
 
 
-def run_gpu(args):
+def _geometry(W, n=None):
+    from cfmm_inputs import curve2d_long, plane3d
+    n = n or W["N_POINTS"]
+    return curve2d_long(n, seed=0) if W["DIM"] == 2 else plane3d(n, seed=0)
+
+
+def measure_workload(args, W, dev, ws, rank, local, steps, warmup, check_targets=1000, e2e=True):
+    """MIXED and FP64 passes of workload W: plan+apply steps (the bench step),
+    the apply alone on a resident plan, per-step kernel times from a serialised
+    apply (near field in line), accuracy against the library's FP64 direct sum
+    on sampled targets, and (e2e) the same pass through the C ABI with host
+    buffers."""
     import numpy as np
     import torch
 
     import paper_2509_05458_gb300 as cf
-    from cfmm_inputs import curve2d_long, plane3d, densities
+    from cfmm_inputs import densities
+
+    DIM, DLP, KAPPA, EPS, SEP = W["DIM"], W["DLP"], W["KAPPA"], W["EPS"], W["SEP"]
+    g = _geometry(W)
+    dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2 if DLP else 1)
+    re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
+    nre = torch.from_numpy(g.nrm_re).to(dev) if DLP else None
+    nim = torch.from_numpy(g.nrm_im).to(dev) if DLP else None
+    dens = torch.from_numpy(dens_np).to(dev)
+    out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
+    kernel = (cf.HELMHOLTZ if W["KERNEL"] else cf.LAPLACE) | cf.SLP | (cf.DLP if DLP else 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # reference values at sampled targets: the library's FP64 direct sum
+    idx = np.sort(np.random.default_rng(1).choice(g.n, min(check_targets, g.n), replace=False))
+    ref = None
+    if check_targets:
+        ti = torch.from_numpy(idx).to(dev)
+        ref = cf.direct(DIM, kernel, KAPPA, re, im, re[ti].contiguous(), im[ti].contiguous(), dens, nre, nim,
+                        precision=cf.FP64, stream=stream).cpu().numpy()[0]
+
+    def plan(precision, leaf):
+        return cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=leaf, sep=SEP, stream=stream,
+                       precision=precision)
+
+    def measure(precision):
+        leaf = W["LEAF"] if precision == cf.MIXED else W["LEAF_FP64"]
+
+        def step():
+            p = plan(precision, leaf)
+            p.apply(dens, out=out)
+            info = p.info()
+            p.destroy()
+            return info
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        n0 = cf.launch_count()
+        step_ms = []
+        _barrier(ws)
+        torch.cuda.synchronize()
+        clocks.start()
+        wall0 = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            info = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize()
+        _barrier(ws)
+        wall = time.perf_counter() - wall0
+        clk = clocks.stop()
+        launches = cf.launch_count() - n0
+        ms = _max_over_ranks(statistics.mean(step_ms), ws, dev)
+        acc = None
+        u_all = out.cpu().numpy()[0].copy()
+        if ref is not None:
+            u = u_all[idx]
+            acc = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+        # the apply alone on a resident plan (the GMRES matvec)
+        p = plan(precision, leaf)
+        for _ in range(3):
+            p.apply(dens, out=out)
+        torch.cuda.synchronize()
+        ap = []
+        for _ in range(max(5, steps)):
+            flush.zero_()
+            ev0.record(stream)
+            p.apply(dens, out=out)
+            ev1.record(stream)
+            ev1.synchronize()
+            ap.append(ev0.elapsed_time(ev1))
+        # per-step kernel times: the near field in line (timing mode 2), so no
+        # step's events absorb the other stream's kernels; median of 3
+        p.set_timing(2)
+        kts = []
+        for _ in range(3):
+            flush.zero_()
+            p.apply(dens, out=out)
+            kts.append(p.timings())
+        p.set_timing(0)
+        kt = np.median(np.array(kts), axis=0)
+        work = work_model(p, W)
+        p.destroy()
+        return dict(ms=ms, apply_ms=statistics.median(ap), kt=kt, acc=acc, clk=clk, wall=wall,
+                    launches=launches // max(1, steps), info=info, work=work, leaf=leaf, u=u_all)
+
+    if args.precision == "fp64":
+        mixed = fp64 = measure(cf.FP64)
+    elif args.precision == "mixed":
+        mixed = fp64 = measure(cf.MIXED)
+    else:
+        mixed = measure(cf.MIXED)
+        fp64 = measure(cf.FP64)
+
+    e2e_line = None
+    if e2e:
+        # end to end through the C ABI with host buffers (copies inside the timed region), MIXED
+        hre, him = g.re, g.im
+        hnre, hnim = (g.nrm_re, g.nrm_im) if DLP else (None, None)
+        hd = np.ascontiguousarray(dens_np)
+        ho = np.empty((1, g.n), dtype=np.complex128)
+        e2e_t = []
+        for i in range(max(3, steps) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ph = cf.plan(DIM, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=W["LEAF"], sep=SEP,
+                         precision=cf.MIXED)
+            ph.apply(hd, out=ho)
+            ph.destroy()
+            t1 = time.perf_counter()
+            if i > 0:
+                e2e_t.append(t1 - t0)
+        e2e_s = _max_over_ranks(statistics.median(e2e_t), ws, dev)
+        h2d = (4 if DLP else 2) * hre.nbytes + hd.nbytes
+        e2e_line = {"value": g.n * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(ho.nbytes)}
+    return dict(g=g, dens_np=dens_np, idx=idx, out_mixed=None, mixed=mixed, fp64=fp64, e2e=e2e_line)
+
+
+def summarize(W, r, ws):
+    """The per-workload part of a bench line."""
+    mixed, fp64 = r["mixed"], r["fp64"]
+    n = r["g"].n
+    kt = mixed["kt"]
+    info = mixed["info"]
+    out = {
+        "value": n * ws / (mixed["ms"] / 1e3),
+        "ms_per_step": mixed["ms"],
+        "config": {"workload": W["WORKLOAD"], "n": n, "kappa": W["KAPPA"], "eps": W["EPS"],
+                   "leaf_size": W["LEAF"], "leaf_size_fp64": W["LEAF_FP64"], "sep": W["SEP"],
+                   "layers": "SLP+DLP" if W["DLP"] else "SLP",
+                   "precision": "MIXED (near field and L2P complex64, translations FP64)",
+                   "tree": {k: info[k] for k in ("nlevels", "nboxes", "nleaves", "l0", "p2p_pairs", "m2l_pairs")}},
+        "apply_only": {"value": n / (mixed["apply_ms"] / 1e3), "unit": "points/s", "ms": mixed["apply_ms"]},
+        "accuracy": {"rel_l2_vs_fp64_direct_sampled": mixed["acc"], "targets": int(len(r["idx"])),
+                     "eps": W["EPS"]},
+        "fp64": {"value": n / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
+                 "apply_only": n / (fp64["apply_ms"] / 1e3), "apply_ms": fp64["apply_ms"],
+                 "accuracy": fp64["acc"],
+                 "step_breakdown_ms_serialised": {STEP_NAMES[i]: float(fp64["kt"][i]) for i in range(9)}},
+        "step_breakdown_ms_serialised": {STEP_NAMES[i]: float(kt[i]) for i in range(9)},
+        "plan_ms": float(mixed["ms"] - mixed["apply_ms"]),
+        "work": mixed["work"],
+    }
+    return out
+
+
+def rooflines(W, r):
+    """Rooflines of the M2L (FP64 translations, exact algorithmic flop count)
+    and of the near field (flops per pair from an instruction-count capture
+    under profiles/, used only while it matches the current sources), from the
+    serialised per-step kernel times of the MIXED apply. The dominant one
+    (longer time) comes first."""
+    mixed = r["mixed"]
+    kt, work = mixed["kt"], mixed["work"]
+    out = []
+    m2l = {"kernel": "M2L" + (" (k_tr3h, modes M2L)" if W["DIM"] == 3 and W["KERNEL"] else ""),
+           "bound": "alu", "unit": "GFLOP/s", "ms": float(kt[3]), "peak": FP64_PEAK_GFLOPS,
+           "peak_source": "FP64 FMA units x max SM clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz); "
+                          "MEASURED_PEAKS.json has no FP64 figure",
+           "flops_per_apply": work["m2l_flops"], "traffic": None}
+    m2l["achieved"] = work["m2l_flops"] / (kt[3] / 1e3) / 1e9 if kt[3] > 0 else None
+    m2l["frac"] = m2l["achieved"] / FP64_PEAK_GFLOPS if m2l["achieved"] else None
+    if W["DIM"] == 3 and W["KERNEL"]:
+        prof = profile_figures("ncu_tr3h_helm3d_k10_n1e6.txt", TR3H_SOURCES)
+        if prof and "dram_bytes_per_apply" in prof:
+            m2l["traffic"] = int(float(prof["dram_bytes_per_apply"]))
+            m2l["traffic_source"] = prof["_path"]
+    out.append(m2l)
+    name = "p2p_flops_%s.txt" % ("helm3d_k10_mixed" if W["DIM"] == 3 and W["KERNEL"] else
+                                 "lap3d_mixed" if W["DIM"] == 3 else "helm2d_k20_mixed")
+    prof = profile_figures(name, P2P_SOURCES)
+    p2p = {"kernel": "P2P (k_p2p32, List 1)", "bound": "alu", "unit": "GFLOP/s", "ms": float(kt[6]),
+           "pairs_per_apply": work["p2p_pairs"], "traffic": None}
+    if prof:
+        f32 = float(prof["fp32_flops_per_pair"])
+        f64 = float(prof.get("fp64_flops_per_pair", 0.0))
+        p2p.update({"flops_per_pair_fp32": f32, "flops_per_pair_fp64": f64, "counts_source": prof["_path"],
+                    "peak": FP32_PEAK_GFLOPS,
+                    "peak_source": "FP32 FMA units x max SM clock (152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz)"})
+        ach = work["p2p_pairs"] * f32 / (kt[6] / 1e3) / 1e9 if kt[6] > 0 else None
+        p2p["achieved"] = ach
+        p2p["frac"] = ach / FP32_PEAK_GFLOPS if ach else None
+        p2p["fp64_frac"] = (work["p2p_pairs"] * f64 / (kt[6] / 1e3) / 1e9 / FP64_PEAK_GFLOPS
+                            if kt[6] > 0 and f64 else None)
+        if "dram_bytes_per_launch" in prof:
+            p2p["traffic"] = int(float(prof["dram_bytes_per_launch"]))
+    else:
+        p2p.update({"achieved": None, "frac": None, "peak": FP32_PEAK_GFLOPS,
+                    "note": "no instruction-count summary matching the current near-field sources"})
+    out.append(p2p)
+    out.sort(key=lambda x: -x["ms"])
+    return out
+
+
+def run_gpu(args):
+    import torch
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -166,170 +430,55 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    g = curve2d_long(N_POINTS, seed=0) if DIM == 2 else plane3d(N_POINTS, seed=0)
-    dens_np = densities(g.n, seed=1, nrhs=1, ncomp=2 if DLP else 1)
-    re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
-    nre = torch.from_numpy(g.nrm_re).to(dev) if DLP else None
-    nim = torch.from_numpy(g.nrm_im).to(dev) if DLP else None
-    dens = torch.from_numpy(dens_np).to(dev)
-    out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
-    kernel = (cf.HELMHOLTZ if KERNEL else cf.LAPLACE) | cf.SLP | (cf.DLP if DLP else 0)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    # work model of the workload (host bookkeeping, outside the timed regions)
-    wp = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=LEAF, sep=SEP, stream=stream)
-    work = work_model(wp)
-    wp.destroy()
-
-    def measure(precision, check):
-        leaf = LEAF if precision == cf.MIXED else LEAF_FP64
-
-        def step(timing=False):
-            p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=leaf, sep=SEP, stream=stream,
-                        precision=precision)
-            if timing:
-                p.set_timing(True)
-            p.apply(dens, out=out)
-            t = p.timings() if timing else None
-            info = p.info()
-            p.destroy()
-            return t, info
-
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        acc = None
-        if check:
-            from oracle.direct import direct
-            idx = np.random.default_rng(1).choice(g.n, 100, replace=False)
-            pts = g.re + 1j * g.im
-            u0 = direct(DIM, KERNEL, KAPPA, pts, pts[idx], sigma=dens_np[0, 0],
-                        tau=dens_np[0, 1] if DLP else None, nrm=(g.nrm_re + 1j * g.nrm_im) if DLP else None)
-            u = out.cpu().numpy()[0, idx]
-            acc = float(np.linalg.norm(u - u0) / np.linalg.norm(u0))
-        clocks = ClockSampler(local)
-        n0 = cf.launch_count()
-        step_ms, kern = [], []
-        _barrier(ws)
-        torch.cuda.synchronize()
-        clocks.start()
-        wall0 = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0.record(stream)
-            t, info = step(timing=True)
-            ev1.record(stream)
-            ev1.synchronize()
-            step_ms.append(ev0.elapsed_time(ev1))
-            kern.append(t)
-        torch.cuda.synchronize()
-        _barrier(ws)
-        wall = time.perf_counter() - wall0
-        clk = clocks.stop()
-        launches = cf.launch_count() - n0
-        ms = _max_over_ranks(statistics.mean(step_ms), ws, dev)
-        # apply alone on a resident plan (the GMRES matvec)
-        p = cf.plan(DIM, kernel, KAPPA, EPS, re, im, nre, nim, leaf_size=leaf, sep=SEP, stream=stream,
-                    precision=precision)
-        for _ in range(3):
-            p.apply(dens, out=out)
-        torch.cuda.synchronize()
-        ap = []
-        for _ in range(max(5, args.steps)):
-            flush.zero_()
-            ev0.record(stream)
-            p.apply(dens, out=out)
-            ev1.record(stream)
-            ev1.synchronize()
-            ap.append(ev0.elapsed_time(ev1))
-        p.destroy()
-        kt = np.mean(np.array(kern), axis=0)
-        return dict(ms=ms, apply_ms=statistics.median(ap), kt=kt, acc=acc, clk=clk, wall=wall,
-                    launches=launches // max(1, args.steps), info=info)
-
-    if args.precision == "fp64":
-        mixed = fp64 = measure(cf.FP64, rank == 0 and not args.skip_check)
-    elif args.precision == "mixed":
-        mixed = fp64 = measure(cf.MIXED, rank == 0 and not args.skip_check)
-    else:
-        mixed = measure(cf.MIXED, rank == 0 and not args.skip_check)
-        fp64 = measure(cf.FP64, rank == 0 and not args.skip_check)
-
-    # end to end through the C ABI with host buffers (copies inside the timed region), MIXED
-    hre, him = g.re, g.im
-    hnre, hnim = (g.nrm_re, g.nrm_im) if DLP else (None, None)
-    hd = np.ascontiguousarray(dens_np)
-    ho = np.empty((1, g.n), dtype=np.complex128)
-    e2e = []
-    for i in range(max(3, args.steps) + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ph = cf.plan(DIM, kernel, KAPPA, EPS, hre, him, hnre, hnim, leaf_size=LEAF, sep=SEP, precision=cf.MIXED)
-        ph.apply(hd, out=ho)
-        ph.destroy()
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e.append(t1 - t0)
-    e2e_s = statistics.median(e2e)
-    h2d = (4 if DLP else 2) * hre.nbytes + hd.nbytes
-    d2h = ho.nbytes
-
+    W = WORKLOADS[args.workload]
+    r = measure_workload(args, W, dev, ws, rank, local, args.steps, args.warmup)
+    extras = {}
+    if args.workload == "helm3d" and not args.no_extras and args.n == 0:
+        for name in ("lap3d", "helm2d"):
+            rx = measure_workload(args, WORKLOADS[name], dev, ws, rank, local, min(args.steps, 5),
+                                  max(3, min(args.warmup, 3)), check_targets=200, e2e=False)
+            sx = summarize(WORKLOADS[name], rx, ws)
+            sx["roofline"] = rooflines(WORKLOADS[name], rx)
+            extras[name] = sx
     if rank != 0:
         return
-    kt = mixed["kt"]
-    # roofline of the M2L (the dominant FP64 translation step, with an exact
-    # algorithmic count); the near field runs beside the far field on its own
-    # stream, so step times overlap and the longest one is reported beside it
-    dom = int(np.argmax(kt))
-    fp64_peak = 1250.0   # GFLOP/s: nominal dense FP64 of GB300 (no measured FP64 peak is provided)
-    roof = dominant_roofline("M2L", kt[3], work, fp64_peak)
-    roof["longest_step"] = {"step": STEP_NAMES[dom], "ms": float(kt[dom])}
-    if M2L_TRAFFIC_BYTES is not None and DIM == 2 and N_POINTS == 100_000 and LEAF == 64:
-        roof["traffic"] = M2L_TRAFFIC_BYTES
-        roof["traffic_source"] = "profiles/ncu_m2l_helm2d_k20_n1e5.txt (k_m2l_chunk, one apply, DRAM read+write)"
-    info = mixed["info"]
+    s = summarize(W, r, ws)
+    roofs = rooflines(W, r)
+    mixed = r["mixed"]
     line = {
-        "metric": METRIC,
-        "value": g.n * ws / (mixed["ms"] / 1e3),
+        "metric": W["METRIC"],
+        "value": s["value"],
         "unit": "points/s",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": mixed["ms"],
+        "ms_per_step": s["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
-                   "leaf_size_fp64": LEAF_FP64, "sep": SEP,
-                   "layers": "SLP+DLP" if DLP else "SLP",
-                   "precision": "MIXED (near field complex64, translations FP64)",
-                   "parallelism": f"replicas{ws}",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "tree": {k: info[k] for k in ("nlevels", "nboxes", "nleaves", "l0", "p2p_pairs", "m2l_pairs")}},
-        "apply_only": {"value": g.n / (mixed["apply_ms"] / 1e3), "unit": "points/s", "ms": mixed["apply_ms"]},
-        "accuracy": {"rel_l2_vs_direct_100_targets": mixed["acc"], "eps": EPS},
-        "fp64": {"value": g.n / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"],
-                 "apply_only": g.n / (fp64["apply_ms"] / 1e3), "apply_ms": fp64["apply_ms"],
-                 "accuracy": fp64["acc"],
-                 "step_breakdown_ms": {STEP_NAMES[i]: float(fp64["kt"][i]) for i in range(9)}},
-        "step_breakdown_ms": {STEP_NAMES[i]: float(kt[i]) for i in range(9)},
-        # the near field (slot 6) runs on its own stream beside the far field
-        "plan_ms": float(mixed["ms"] - (float(np.sum(kt)) - float(kt[6]))),
-        "work": work,
-        "roofline": roof,
-        "e2e": {"value": g.n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "config": dict(s["config"], parallelism=f"replicas{ws}",
+                       l2="flushed (256 MB write) before every timed step"),
+        "apply_only": s["apply_only"],
+        "accuracy": s["accuracy"],
+        "fp64": s["fp64"],
+        "step_breakdown_ms_serialised": s["step_breakdown_ms_serialised"],
+        "plan_ms": s["plan_ms"],
+        "work": s["work"],
+        "roofline": roofs[0],
+        "roofline_kernels": roofs,
+        "e2e": r["e2e"],
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clk"],
-        "clocks_fp64": fp64["clk"],
+        "clocks_fp64": r["fp64"]["clk"],
         "wall_s": mixed["wall"],
     }
+    if extras:
+        line["extras"] = extras
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        cb = cpu_baseline(args, W, r)
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
 
@@ -399,17 +548,17 @@ def run_batch(args):
         plans, outs, leaves, streams, b = build(precision)
         acc = None
         if check:
-            from oracle.direct import direct
+            # against the library's FP64 direct sum at sampled targets
             errs = []
             rng = np.random.default_rng(1)
             for i, g in enumerate(geoms):
-                nt = 60 if i == 0 else 20
-                idx = rng.choice(g.n, nt, replace=False)
-                pts = g.re + 1j * g.im
+                nt = 200 if i == 0 else 100
+                idx = torch.from_numpy(np.sort(rng.choice(g.n, nt, replace=False))).to(dev)
+                ref = cf.direct(3, kernel, KAPPA, pts_re[i], pts_im[i], pts_re[i][idx].contiguous(),
+                                pts_im[i][idx].contiguous(), dens[i], precision=cf.FP64).cpu().numpy()
                 for r in ((0, nrhs[i] - 1) if nrhs[i] > 1 else (0,)):
-                    u0 = direct(3, 1, KAPPA, pts, pts[idx], sigma=dens_np[i][r, 0])
-                    u = outs[i][r].cpu().numpy()[idx]
-                    errs.append(float(np.linalg.norm(u - u0) / np.linalg.norm(u0)))
+                    u = outs[i][r][idx].cpu().numpy()
+                    errs.append(float(np.linalg.norm(u - ref[r]) / np.linalg.norm(ref[r])))
             acc = {"max_rel_l2": max(errs), "median_rel_l2": float(np.median(errs)),
                    "per_geometry_rhs0": [errs[0]] + errs[2:]}
         clocks = ClockSampler(local)
@@ -431,11 +580,11 @@ def run_batch(args):
                 main.wait_stream(streams[i])
         ems = timed(eager, 0, 1)   # one pass: a step of this workload takes seconds
         # per-step breakdown of the 64-RHS geometry (dominant kernel)
-        plans[0].set_timing(True)
+        plans[0].set_timing(2)
         plans[0].apply(dens[0], out=outs[0])
         kt = np.array(plans[0].timings())
         plans[0].set_timing(False)
-        work = work_model(plans[0])
+        work = work_model(plans[0], WORKLOADS["batch3d"])
         # end to end: pinned host densities in, results out, around one replay
         hd = [torch.from_numpy(d).pin_memory() for d in dens_np]
         ho = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
@@ -471,7 +620,7 @@ def run_batch(args):
     work = dict(mixed["work"])
     work["m2l_flops"] *= nrhs[0]
     work["p2p_pairs"] *= nrhs[0]
-    roof = dominant_roofline("M2L", kt[3], work, 1250.0)
+    roof = dominant_roofline("M2L", kt[3], work, FP64_PEAK_GFLOPS)
     roof["longest_step"] = {"step": STEP_NAMES[dom], "ms": float(kt[dom])}
     roof["scope"] = "the 64-RHS geometry's apply, timed alone with per-step events"
     line = {
@@ -507,7 +656,7 @@ def run_batch(args):
         line["fp64"] = {"value": evals / (fp64["ms"] / 1e3), "ms_per_step": fp64["ms"], "accuracy": fp64["acc"],
                         "leaf_sizes": fp64["leaves"], "clocks": fp64["clk"]}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_baseline"] = cpu_baseline(args, WORKLOADS["batch3d"])
     print(json.dumps(line), flush=True)
 
 
@@ -586,10 +735,12 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def work_model(p):
-    """Algorithmic work of one apply: List-2 pairs and M2L flops (8 flops per
-    complex multiply-add, (2P+1)^2 per pair at the pair's level), List-1 pairs."""
+def work_model(p, W=None):
+    """Algorithmic work of one apply: List-2 pairs and M2L flops at each pair's
+    level (2D: 8 flops per complex multiply-add, (2P+1)^2 per pair; 3D: the
+    point-and-shoot counts below), List-1 pairs."""
     import numpy as np
+    W = W or WORKLOADS["helm3d"]
     inf = p.info()
     t = p.export_tree()
     P = p.orders()
@@ -601,13 +752,14 @@ def work_model(p):
         npairs = int(cnt[t["level"] == l].sum())
         if npairs:
             pairs_per_level[int(l)] = npairs
-            if DIM == 2:
+            if W["DIM"] == 2:
                 m2l_flops += npairs * 8 * (2 * int(P[l]) + 1) ** 2
             else:
-                m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if KERNEL else m2l_flops_pair_lap3d(int(P[l])))
+                m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if W["KERNEL"]
+                                       else m2l_flops_pair_lap3d(int(P[l])))
     return {"p2p_pairs": int(inf["p2p_pairs"]), "m2l_pairs": int(inf["m2l_pairs"]),
             "m2l_pairs_per_level": pairs_per_level, "orders": [int(x) for x in P],
-            "m2l_flops": int(m2l_flops), "p2p_flops_per_pair": P2P_FLOPS_PER_PAIR}
+            "m2l_flops": int(m2l_flops)}
 
 
 def m2l_flops_pair_3d(P):
@@ -632,67 +784,78 @@ def m2l_flops_pair_lap3d(P):
 
 
 def dominant_roofline(name, ms, work, fp64_peak_gflops):
-    """Roofline of the dominant kernel of the apply, FP64-ALU bound:
-    M2L: work["m2l_flops"]; P2P: List-1 pairs x FP64 flops per pair."""
-    flops = None
-    if name == "M2L":
-        flops = work["m2l_flops"]
-    elif name == "P2P" and P2P_FLOPS_PER_PAIR:
-        flops = work["p2p_pairs"] * P2P_FLOPS_PER_PAIR
+    """Roofline of the M2L of an apply, FP64-ALU bound (work["m2l_flops"])."""
     base = {"bound": "alu", "peak": fp64_peak_gflops, "unit": "GFLOP/s", "traffic": None, "kernel": name,
             "ms": float(ms),
-            "peak_source": "nominal GB300 dense FP64, 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 figure)"}
-    if not flops:
+            "peak_source": "FP64 FMA units x max SM clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)"}
+    flops = work["m2l_flops"]
+    if not flops or ms <= 0:
         return dict(base, achieved=None, frac=None)
     ach = flops / (ms / 1e3) / 1e9
     return dict(base, achieved=ach, frac=ach / fp64_peak_gflops)
 
 
-# FP64 operations of one near-field pair (2D Helmholtz SLP+DLP); 0 = not yet counted
-P2P_FLOPS_PER_PAIR = 0
-# DRAM bytes of the 2D Helmholtz M2L launches of one apply on the headline workload,
-# from one ncu capture (profiles/ncu_m2l_helm2d_k20_n1e5.txt); None once the kernel changes
-M2L_TRAFFIC_BYTES = 27_990_784
+# ---- the CPU baseline: the oracle, as it stands, on the host cores ----------
+
+def _oracle_direct_chunk(job):
+    """One worker's share of the oracle's direct sum (runs in a spawned process)."""
+    sys.path.insert(0, ROOT)
+    from oracle.direct import direct
+    dim, ker, kap, pts, trg, sigma, tau, nrm = job
+    t = time.perf_counter()
+    u = direct(dim, ker, kap, pts, trg, sigma=sigma, tau=tau, nrm=nrm)
+    return u, time.perf_counter() - t
 
 
-def cpu_baseline(args):
-    """The oracle, as it stands, on a bounded sample of the workload, one core:
-    2D, its FMM on 20,000 points of the same curve family (same k, eps, leaf
-    size); 3D, its direct sum for 200 targets against all N sources (the oracle
-    FMM's top level alone takes minutes there)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    if DIM == 3:
-        code = ("import sys,time,json; sys.path.insert(0, %r)\n"
-                "import numpy as np\n"
-                "from cfmm_inputs import plane3d, densities\n"
-                "from oracle.direct import direct\n"
-                "g = plane3d(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=1)\n"
-                "pts = g.re + 1j * g.im; idx = np.arange(200)\n"
-                "t=time.perf_counter(); direct(3, %d, %r, pts, pts[idx], sigma=d[0,0]); t=time.perf_counter()-t\n"
-                "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, N_POINTS, KERNEL, KAPPA)
-        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-        if r.returncode != 0:
-            return {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
-                    "sample": "failed: " + r.stderr.strip()[-200:]}
-        o = json.loads(r.stdout.strip().splitlines()[-1])
-        return {"value": 200 / o["s"], "unit": "points/s", "cores": 1, "kind": "oracle",
-                "sample": f"oracle direct sum (numpy), 200 targets against all {o['n']} sources: {o['s']:.1f} s; "
-                          "points/s = targets evaluated per second"}
-    code = ("import sys,time,json; sys.path.insert(0, %r)\n"
-            "from cfmm_inputs import curve2d_long, densities\n"
-            "from oracle import fmm2d\n"
-            "g = curve2d_long(%d, seed=0); d = densities(g.n, seed=1, nrhs=1, ncomp=2)\n"
-            "t=time.perf_counter(); fmm2d.apply(g.re, g.im, 1, %r, %r, %d, sigma=d[0,0], tau=d[0,1], "
-            "nrm_re=g.nrm_re, nrm_im=g.nrm_im); t=time.perf_counter()-t\n"
-            "print(json.dumps({'n': g.n, 's': t}))\n") % (ROOT, args.cpu_n, KAPPA, EPS, LEAF)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr.strip()[-200:]}
-    o = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": o["n"] / o["s"], "unit": "points/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle FMM (numpy/scipy) on {o['n']} points of the same curve family, "
-                      f"same k/eps/leaf, SLP+DLP, one pass: {o['s']:.1f} s"}
+def oracle_direct_sample(W, g, dens_np, idx, workers):
+    """The oracle's direct sum at targets idx against all points, split over
+    `workers` spawned processes (each single-threaded). Returns (u, wall s)."""
+    import concurrent.futures as fut
+    import multiprocessing as mp
+    import numpy as np
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    pts = g.re + 1j * g.im
+    nrm = (g.nrm_re + 1j * g.nrm_im) if W["DLP"] else None
+    sigma = dens_np[0, 0]
+    tau = dens_np[0, 1] if W["DLP"] else None
+    parts = [p for p in np.array_split(idx, workers) if len(p)]
+    jobs = [(W["DIM"], W["KERNEL"], W["KAPPA"], pts, pts[p], sigma, tau, nrm) for p in parts]
+    t0 = time.perf_counter()
+    with fut.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_direct_chunk, jobs))
+    wall = time.perf_counter() - t0
+    return np.concatenate([u for u, _ in res]), wall
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(args, W, r=None):
+    """The oracle's direct sum (numpy/scipy, as it stands) on a bounded sample
+    of the workload: `--cpu-targets` seeded targets against all N sources,
+    split over every host core; points/s = targets evaluated per second. When
+    the GPU result r is given, its error on the same targets is reported."""
+    import numpy as np
+    from cfmm_inputs import densities
+    g = r["g"] if r else _geometry(W)
+    dens_np = r["dens_np"] if r else densities(g.n, seed=1, nrhs=1, ncomp=2 if W["DLP"] else 1)
+    nt = min(args.cpu_targets, g.n)
+    idx = np.sort(np.random.default_rng(7).choice(g.n, nt, replace=False))
+    cores = cpu_cores()
+    u0, wall = oracle_direct_sample(W, g, dens_np, idx, cores)
+    out = {"value": nt / wall, "unit": "points/s", "cores": cores, "kind": "oracle",
+           "sample": f"oracle direct sum (numpy/scipy, FP64), {nt} seeded targets against all {g.n} sources, "
+                     f"split over {cores} processes: {wall:.1f} s wall; points/s = targets evaluated per second"}
+    if r:
+        # the GPU passes' error against the oracle on the same targets
+        err = lambda u: float(np.linalg.norm(u[idx] - u0) / np.linalg.norm(u0))
+        out["gpu_rel_l2_vs_oracle_on_sample"] = {"mixed": err(r["mixed"]["u"]), "fp64": err(r["fp64"]["u"])}
+    return out
 
 
 def run_reference(args):
@@ -700,21 +863,22 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    times = []
+    W = WORKLOADS[args.workload if args.workload in ("helm3d", "lap3d", "helm2d") else "helm3d"]
+    vals = []
     res = None
     for i in range(args.warmup + args.steps):
-        res = cpu_baseline(args)
-        if i >= args.warmup and res["value"]:
-            times.append(res["value"])
-    val = statistics.mean(times) if times else None
-    line = {"metric": METRIC, "value": val, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+        res = cpu_baseline(args, W)
+        if i >= args.warmup:
+            vals.append(res["value"])
+    val = statistics.mean(vals) if vals else None
+    line = {"metric": W["METRIC"], "value": val, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": N_POINTS, "kappa": KAPPA, "eps": EPS, "leaf_size": LEAF,
-                       "sep": SEP, "layers": "SLP+DLP" if DLP else "SLP", "precision": "FP64",
-                       "parallelism": "cpu"},
-            "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
-                             "sample": res["sample"] if res else None},
+            "config": {"workload": W["WORKLOAD"], "n": W["N_POINTS"], "kappa": W["KAPPA"], "eps": W["EPS"],
+                       "leaf_size": W["LEAF"], "sep": W["SEP"], "layers": "SLP+DLP" if W["DLP"] else "SLP",
+                       "precision": "FP64", "parallelism": "cpu"},
+            "cpu_baseline": {"value": val, "unit": "points/s", "cores": res["cores"] if res else None,
+                             "kind": "oracle", "sample": res["sample"] if res else None},
             "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -725,16 +889,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-n", type=int, default=20000)
+    ap.add_argument("--cpu-targets", type=int, default=1000,
+                    help="targets of the CPU baseline's sample (against all sources)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 3D Laplace and 2D lines of the default run")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
-    ap.add_argument("--workload", default="helm2d", choices=["helm2d", "helm3d", "lap3d", "batch3d", "serve"],
-                    help="helm2d: the 2D Helmholtz headline; helm3d / lap3d: the 3D Helmholtz / Laplace "
-                         "surface lines; batch3d: the batched 3D Helmholtz line; serve: the serving loop")
-    ap.add_argument("--requests", type=int, default=60, help="serve: requests per stream")
-    ap.add_argument("--rate", type=float, default=1.0, help="serve: Poisson arrival rate (Hz)")
+    ap.add_argument("--workload", default="helm3d", choices=["helm3d", "lap3d", "helm2d", "batch3d", "serve"],
+                    help="helm3d: the 3D Helmholtz surface headline (with the 3D Laplace and 2D lines); lap3d / "
+                         "helm2d: those alone; batch3d: the batched 3D Helmholtz line; serve: the serving loop")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests per stream")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (Hz); 0 = calibrated")
     ap.add_argument("--nmax", type=int, default=1_000_000, help="serve: largest request size")
     ap.add_argument("--slots", type=int, default=4, help="serve: requests in flight")
     ap.add_argument("--n", type=int, default=0,
@@ -742,18 +907,15 @@ def main():
     ap.add_argument("--sep", type=int, default=0, help="override the separation k (parameter sweeps)")
     ap.add_argument("--leaf", type=int, default=0, help="override the leaf size of both passes (parameter sweeps)")
     args = ap.parse_args()
-    if args.workload == "helm3d":
-        globals().update(W3D)
-    elif args.workload == "lap3d":
-        globals().update(WL3D)
-    elif args.workload == "batch3d":
-        globals().update(W4)
-    if args.n > 0:
-        globals()["N_POINTS"] = args.n
-    if args.sep > 0:
-        globals()["SEP"] = args.sep
-    if args.leaf > 0:
-        globals()["LEAF"] = globals()["LEAF_FP64"] = args.leaf
+    if args.workload in WORKLOADS:
+        W = WORKLOADS[args.workload]
+        if args.n > 0:
+            W["N_POINTS"] = args.n
+        if args.sep > 0:
+            W["SEP"] = args.sep
+        if args.leaf > 0:
+            W["LEAF"] = W["LEAF_FP64"] = args.leaf
+        globals().update(W)
     if args.impl == "reference":
         args.warmup = max(0, min(args.warmup, 1))
         args.steps = max(1, min(args.steps, 2))

@@ -249,7 +249,11 @@ int cfmm_plan_export_list(cfmm_plan_t plan, int which, int64_t* offsets, int32_t
  * 5 L2L, 6 P2P, 7 M2P+L2P, 8 unpermute); returns the number of steps. */
 int cfmm_plan_timings(cfmm_plan_t plan, double* t, int nsteps);
 
-/* cfmm_plan_set_timing: 1 = record per-step CUDA events during apply. */
+/* cfmm_plan_set_timing: 0 = off; 1 = record per-step CUDA events during apply
+ * (the near field runs beside the far field on the plan's second stream, so
+ * concurrent steps share the SMs); 2 = serialised: the near field runs in line
+ * on the plan's stream and every step's time is its kernels' alone (slower
+ * apply, same result bit for bit). Returns CFMM_EINVAL for other values. */
 int cfmm_plan_set_timing(cfmm_plan_t plan, int on);
 
 /* cfmm_launch_count: number of kernels this library launched so far in the

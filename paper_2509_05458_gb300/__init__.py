@@ -258,7 +258,10 @@ class Plan:
         return off, ent[: inf["list_len"][which - 1]]
 
     def set_timing(self, on=True):
-        _check(lib().cfmm_plan_set_timing(self._h, 1 if on else 0))
+        """0/False: off; 1/True: per-step events (the near field beside the far
+        field); 2: serialised (the near field in line, so no step absorbs the
+        other stream's kernels)."""
+        _check(lib().cfmm_plan_set_timing(self._h, int(on)))
 
     def timings(self):
         t = np.zeros(9)

@@ -323,6 +323,11 @@ static void record(cfmm_plan_s* P, int i) {
 }
 
 cudaStream_t near_fork(cfmm_plan_s* P) {
+    if (P->timing && P->serial) {
+        CFMM_CUDA(cudaEventRecord(P->ev_p2p[0], P->stream));
+        P->p2p_serial = true;
+        return P->stream;
+    }
     CFMM_CUDA(cudaEventRecord(P->ev_fork, P->stream));
     CFMM_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
     if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev_p2p[0], P->side));
@@ -330,7 +335,12 @@ cudaStream_t near_fork(cfmm_plan_s* P) {
     return P->side;
 }
 
+void near_launched(cfmm_plan_s* P) {
+    if (P->p2p_serial) CFMM_CUDA(cudaEventRecord(P->ev_p2p[1], P->stream));
+}
+
 void near_join(cfmm_plan_s* P) {
+    if (P->p2p_serial) return;
     if (P->timing) CFMM_CUDA(cudaEventRecord(P->ev_p2p[1], P->side));
     CFMM_CUDA(cudaEventRecord(P->ev_join, P->side));
     CFMM_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
@@ -349,6 +359,7 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     cd* sg = P->slp ? P->dens_s.get() : nullptr;
     cd* ta = P->dlp ? P->dens_s.get() + (P->slp ? (int64_t)n * nrhs : 0) : nullptr;
     P->p2p_side = false;
+    P->p2p_serial = false;
     record(P, 0);
     dim3 g((unsigned)((n + 255) / 256), nrhs);
     int comp = 0;
@@ -376,11 +387,13 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
             CFMM_CUDA(cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]));
             P->step_ms[i] = ms;
         }
-        if (P->p2p_side) {
-            // the near field ran beside the far field: its own duration
+        if (P->p2p_side || P->p2p_serial) {
+            // the near field's own duration (beside the far field, or in line)
             float ms = 0.f;
             CFMM_CUDA(cudaEventElapsedTime(&ms, P->ev_p2p[0], P->ev_p2p[1]));
             P->step_ms[6] = ms;
+            // in line it is launched inside the P2M bracket
+            if (P->p2p_serial) P->step_ms[1] -= ms;
         }
     }
 }
@@ -820,7 +833,9 @@ int cfmm_plan_export_list(cfmm_plan_t P, int which, int64_t* offsets, int32_t* e
 int cfmm_plan_set_timing(cfmm_plan_t P, int on) {
     return guarded([&] {
         CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        CFMM_REQUIRE(on >= 0 && on <= 2, CFMM_EINVAL, "timing mode must be 0, 1 or 2");
         P->timing = on != 0;
+        P->serial = on == 2;
     });
 }
 

@@ -276,6 +276,7 @@ struct cfmm_plan_s {
     // diagnostics
     int64_t p2p_pairs = 0, m2l_pairs = 0;
     bool timing = false;
+    bool serial = false;             // timing mode 2: the near field on the plan's stream
     double step_ms[9] = {0};
     cudaEvent_t ev[10] = {};
     // near field (List 1) on a second stream, concurrent with the far field:
@@ -284,6 +285,7 @@ struct cfmm_plan_s {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p2p[2] = {};
     bool p2p_side = false;           // the last apply ran the near field on `side`
+    bool p2p_serial = false;         // the last apply ran it in line (timing mode 2)
     // captured apply
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

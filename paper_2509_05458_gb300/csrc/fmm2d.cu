@@ -1130,6 +1130,7 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     // (3) P2P over List 1 (writes u) on the side stream, beside the far field
     launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
                T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), P->precision == CFMM_MIXED);
+    near_launched(P);
     // (1) P2M (shared memory sized by the leaves' orders)
     {
         int PL = S->maxP_leaf;

@@ -418,6 +418,7 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     // (3) P2P (writes u) on the side stream, beside the far field
     launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
                T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
+    near_launched(P);
     // (1) P2M (single layer: one lane per harmonic column)
     if (!(P->slp && !P->dlp &&
           lap3_p2m_slp(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),

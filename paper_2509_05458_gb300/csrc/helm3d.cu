@@ -1463,6 +1463,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     // (3) P2P (writes u) on the side stream, beside the far field
     launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
                T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
+    near_launched(P);
     auto p2x_smem = [&](int PL, int& chunk) {
         size_t nc = (size_t)(PL + 1) * (PL + 1);
         size_t per = nc + (PL + 2) + 6;

@@ -25,8 +25,12 @@ struct KParams {
 
 // near field of an apply on the plan's side stream: near_fork() makes the
 // side stream wait for what the plan's stream has queued and returns it;
-// near_join() makes the plan's stream wait for the side stream
+// near_join() makes the plan's stream wait for the side stream. In the
+// serialised timing mode near_fork() returns the plan's stream itself and
+// near_launched(), called right after the near-field launch, closes its
+// timing bracket.
 cudaStream_t near_fork(cfmm_plan_s* P);
+void near_launched(cfmm_plan_s* P);
 void near_join(cfmm_plan_s* P);
 void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
                 const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
