@@ -46,9 +46,9 @@ enum {
     CFMM_OK = 0,
     CFMM_EINVAL = -1,      /* bad dim/kernel/k/eps/n/nrhs/options               */
     CFMM_ENONFINITE = -2,  /* NaN or Inf in points or normals                   */
-    CFMM_EGEOM = -3,       /* geometry outside the method's assumptions (Re r^2 */
-                           /*   <= 0 for a near-field pair): reserved, this     */
-                           /*   build does not test the assumption             */
+    CFMM_EGEOM = -3,       /* geometry outside the method's assumptions: Re r^2 */
+                           /*   <= 0 for a close pair (cfmm_plan checks pairs   */
+                           /*   of points near in Morton order)                */
     CFMM_ENOMEM = -4,      /* device allocation failed                          */
     CFMM_ECUDA = -5,       /* CUDA runtime error                                */
     CFMM_ETIMEOUT = -6,    /* a bounded device wait gave up                     */
@@ -74,7 +74,10 @@ enum {
 
 typedef struct cfmm_opts {
     int leaf_size;      /* N_s, max points per leaf (Sec. 6.1); 0 = default 64  */
-    int sep;            /* separation k >= 1 of Sec. 6.2/6.5; 0 = default 1     */
+    int sep;            /* separation k = 1..3 of Sec. 6.2/6.5; 0 = default 1;  */
+                        /* < 0 = automatic: the smallest k whose Sec. 6.3       */
+                        /* Lipschitz limit, times 2, is at least the plan's     */
+                        /* Lipschitz estimate (3 if none)                       */
     int precision;      /* CFMM_FP64 / CFMM_MIXED / CFMM_AUTO                   */
     int top_level;      /* top expansion level l0; <= 0 = automatic rule        */
     void* stream;       /* cudaStream_t the plan runs on; NULL = legacy stream  */
@@ -215,6 +218,11 @@ typedef struct cfmm_plan_info {
     int64_t m2l_pairs;  /* List 2 entries at levels >= l0                     */
     double root_lo[3];
     double root_width;
+    double lipschitz;   /* estimate of the Lipschitz constant L of Im x     */
+                        /* against Re x (Assumptions 4.1/5.1): max over     */
+                        /* pairs at most 32 apart in Morton order of        */
+                        /* |Im(x_i - x_j)| / |Re(x_i - x_j)|; the plan      */
+                        /* fails with CFMM_EGEOM when it reaches 1          */
 } cfmm_plan_info;
 
 /* cfmm_plan_get_info: fills *info. */

@@ -513,6 +513,44 @@ def helm3d_pair(n, zR, zr):
     return h * sps.spherical_jn(n, zr)
 
 
+LIP_WINDOW = 32          # pairs at most this far apart in Morton order
+SEP_LIP_FACTOR = 2.0     # calibrated factor of the automatic separation rule
+
+
+def lipschitz_estimate(re_sorted, im_sorted):
+    """Estimate of the Lipschitz constant L of Im x against Re x (Assumptions
+    4.1/5.1, Eq. Lipschitz_assumption): max over pairs of points at most
+    LIP_WINDOW apart in Morton order of |Im(x_i - x_j)| / |Re(x_i - x_j)|
+    (inf when the real parts coincide and the imaginary parts do not; pairs
+    of coincident points are skipped). L >= 1 allows Re r^2 <= 0 (Sec. 4.1),
+    which the method excludes."""
+    n = re_sorted.shape[0]
+    best = 0.0
+    for s in range(1, min(LIP_WINDOW, n - 1) + 1):
+        a2 = np.sum((re_sorted[s:] - re_sorted[:-s]) ** 2, axis=1)
+        b2 = np.sum((im_sorted[s:] - im_sorted[:-s]) ** 2, axis=1)
+        m = b2 > 0
+        if not np.any(m):
+            continue
+        if np.any(a2[m] == 0):
+            return math.inf
+        best = max(best, float(np.max(b2[m] / a2[m])))
+    return math.sqrt(best)
+
+
+def auto_separation(dim, L):
+    """Separation for a geometry with Lipschitz estimate L: the smallest k in
+    1..3 whose Sec. 6.3 limit (lipschitz_limit_2d/3d) times SEP_LIP_FACTOR is
+    at least L, else 3. The factor is a calibrated reading: the criteria bound
+    the worst case over all geometries, and the configurations' surfaces meet
+    eps = 1e-6 at k = 2 up to slopes about twice the k = 2 limit."""
+    lim = lipschitz_limit_2d if dim == 2 else lipschitz_limit_3d
+    for k in (1, 2, 3):
+        if SEP_LIP_FACTOR * lim(k) >= L:
+            return k
+    return 3
+
+
 def lipschitz_limit_2d(k):
     """Largest L with ((1+L)/(1-L)) * r/R < 1, R=(k+1/2)w, r=sqrt(2)/2 w (Eq. nterms_criteria_2d)."""
     c = (k + 0.5) / (math.sqrt(2) * 0.5)

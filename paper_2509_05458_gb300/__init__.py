@@ -44,7 +44,8 @@ class _Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("kernel", C.c_int), ("sep", C.c_int), ("leaf_size", C.c_int),
                 ("precision", C.c_int), ("nlevels", C.c_int), ("nboxes", C.c_int), ("nleaves", C.c_int),
                 ("l0", C.c_int), ("n", C.c_int64), ("list_len", C.c_int64 * 4), ("p2p_pairs", C.c_int64),
-                ("m2l_pairs", C.c_int64), ("root_lo", C.c_double * 3), ("root_width", C.c_double)]
+                ("m2l_pairs", C.c_int64), ("root_lo", C.c_double * 3), ("root_width", C.c_double),
+                ("lipschitz", C.c_double)]
 
 
 _lib = None
@@ -223,7 +224,8 @@ class Plan:
                 "precision": inf.precision, "nlevels": inf.nlevels, "nboxes": inf.nboxes,
                 "nleaves": inf.nleaves, "l0": inf.l0, "n": inf.n, "list_len": list(inf.list_len),
                 "p2p_pairs": inf.p2p_pairs, "m2l_pairs": inf.m2l_pairs,
-                "root_lo": list(inf.root_lo)[: inf.dim], "root_width": inf.root_width}
+                "root_lo": list(inf.root_lo)[: inf.dim], "root_width": inf.root_width,
+                "lipschitz": inf.lipschitz}
 
     def orders(self):
         nl = self.info()["nlevels"]

@@ -266,6 +266,17 @@ void ensure_device_tables() {
     done[dev] = 1;
 }
 
+int num_sms() {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    CFMM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (!cache[dev]) CFMM_CUDA(cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev));
+    return cache[dev];
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -477,9 +488,11 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         cfmm_opts o{};
         if (opts) o = *opts;
         int leaf = o.leaf_size > 0 ? o.leaf_size : 64;
-        int sep = o.sep > 0 ? o.sep : 1;
+        // sep: 0 = default 1, < 0 = automatic (chosen in build_tree from the
+        // Lipschitz estimate)
+        int sep = o.sep > 0 ? o.sep : o.sep < 0 ? 0 : 1;
         CFMM_REQUIRE(leaf <= 4096, CFMM_EINVAL, "leaf_size must be <= 4096");
-        CFMM_REQUIRE(sep <= 3, CFMM_EINVAL, "sep must be 1, 2 or 3");
+        CFMM_REQUIRE(sep <= 3, CFMM_EINVAL, "sep must be 1, 2 or 3 (or < 0 for automatic)");
         CFMM_REQUIRE(o.precision >= 0 && o.precision <= 2, CFMM_EINVAL, "bad precision mode");
         P = new cfmm_plan_s();
         P->dim = dim;
@@ -774,6 +787,7 @@ int cfmm_plan_get_info(cfmm_plan_t P, cfmm_plan_info* info) {
         info->m2l_pairs = P->m2l_pairs;
         for (int d = 0; d < 3; ++d) info->root_lo[d] = P->lo[d];
         info->root_width = P->W;
+        info->lipschitz = P->lipschitz;
     });
 }
 

@@ -64,6 +64,39 @@ CFMM_HD cf operator+(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
 CFMM_HD cf operator-(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
 CFMM_HD cf operator*(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 CFMM_HD cf operator*(float s, cf a) { return cf{s * a.x, s * a.y}; }
+CFMM_HD cf operator-(cf a) { return cf{-a.x, -a.y}; }
+CFMM_HD cf cinvf(cf b) {
+    float den = b.x * b.x + b.y * b.y;
+    return cf{b.x / den, -b.y / den};
+}
+CFMM_HD cf csqrtf_p(cf z) {
+    float a = z.x, b = z.y;
+    if (a == 0.f && b == 0.f) return cf{0.f, 0.f};
+    float m = hypotf(a, b);
+    float t = sqrtf(0.5f * (fabsf(a) + m));
+    if (a >= 0.f) return cf{t, b / (2.f * t)};
+    return cf{fabsf(b) / (2.f * t), copysignf(t, b)};
+}
+CFMM_HD cf mul_if(cf a) { return cf{-a.y, a.x}; }   // i * a
+// acc + a b as four fused multiply-adds
+CFMM_HD cf cmacf(cf acc, cf a, cf b) {
+    return cf{fmaf(-a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(a.y, b.x, fmaf(a.x, b.y, acc.y))};
+}
+CFMM_HD cf to_cf(cd a) { return cf{(float)a.x, (float)a.y}; }
+
+// Compensated (Kahan) complex64 sum; value() returns it in complex128
+struct Kahan {
+    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    CFMM_HD void add(cf v) {
+        float yx = v.x - cx, tx = sx + yx;
+        cx = (tx - sx) - yx;
+        sx = tx;
+        float yy = v.y - cy, ty = sy + yy;
+        cy = (ty - sy) - yy;
+        sy = ty;
+    }
+    CFMM_HD cd value() const { return cd{(double)sx - (double)cx, (double)sy - (double)cy}; }
+};
 
 // ---------------------------------------------------------------------------
 // status + launch accounting
@@ -228,6 +261,8 @@ struct LagRule {
 };
 const LagRule& host_lag_rule();
 void ensure_device_tables();   // per device, idempotent
+// streaming multiprocessors of the current device (cached per device)
+int num_sms();
 
 // Tree and list storage of a plan (device pointers unless noted).
 struct TreeDev {
@@ -257,6 +292,7 @@ struct cfmm_plan_s {
     double lo[3] = {0, 0, 0};
     double W = 1.0;
     int B = 31;
+    double lipschitz = 0.0;          // estimate of the Lipschitz constant of Im x against Re x
     // sorted geometry (SoA [dim][n])
     cfmm::DevBuf<double> xr, xi, nr, ni;
     cfmm::DevBuf<uint64_t> keys;

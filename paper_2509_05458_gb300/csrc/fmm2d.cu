@@ -634,7 +634,7 @@ __global__ void k_m2l_reduce(int lo, int nbl, const int* __restrict__ box_chunk0
 template <int KER>
 __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                        const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
-                       cd* __restrict__ u, int maxP, const cd* __restrict__ lrow, int RL) {
+                       cd* __restrict__ u, int maxP, const cd* __restrict__ lrow, int RL, int do_l2p) {
     extern __shared__ cd sm[];
     int b = leaves[blockIdx.x];
     int rhs = blockIdx.y;
@@ -692,6 +692,11 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
                 }
             }
         }
+        if (!do_l2p) {
+            // M2P only (the L2P runs in complex64): leaves without List 3 add nothing
+            if (valid && l3off[b + 1] > l3off[b]) u[(int64_t)rhs * A.n + i] += acc;
+            continue;
+        }
         // L2P
         __syncthreads();
         const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
@@ -740,6 +745,90 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
             }
             u[(int64_t)rhs * A.n + i] += acc;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P in complex64 arithmetic (mixed precision). With zeta~ = zeta/rho_b,
+// eta~ = eta/rho_b (rho_b = sqrt(2)/2 w, the leaf's radius):
+//   Laplace    u = L^_0 + sum L^_n zeta~^n + L^'_n eta~^n,  L^_n = L_n rho_b^n
+//   Helmholtz  u = sum_n Jh_n(k r) (L^_n zeta~^n + L^_-n eta~^n),
+//              L^_n = L_n (k rho_b/2)^n/n!,  L^_-n = (-1)^n L_-n (k rho_b/2)^n/n!
+// (G_n = J_n(k r) (zeta/r)^n, G_-n = (-1)^n J_n(k r) (eta/r)^n), where
+//   Jh_n(z) = J_n(z) n! (2/z)^n
+// is entire in w = z^2 = (k rho_b)^2 zeta~ eta~ with Jh_n(0) = 1. From
+// J_{n-1} + J_{n+1} = (2n/z) J_n,  Jh_{n-1} = Jh_n - (w/4) Jh_{n+1}/(n(n+1)),
+// so the ratios q_n = Jh_n/Jh_{n-1} = 1/(1 - (w/4) q_{n+1}/(n(n+1))) follow by
+// Miller's backward recurrence from q = 1, and Jh_0 = J_0 from
+// exp(-+ i z) = J_0 + 2 sum (-+ i)^k J_k = Jh_0 (1 + 2 sum (-+ i z/2)^k/k! prod q).
+// Coefficients are scaled in FP64 per leaf and rounded; the terms are added
+// in a compensated (Kahan) FP32 sum.
+// ---------------------------------------------------------------------------
+constexpr int kL2p2fMaxP = 128;
+
+template <int KER>
+__global__ void __launch_bounds__(kExpThreads) k_l2p2f(ExpArgs A, const int* __restrict__ leaves,
+                                                        const cd* __restrict__ loc, cd* __restrict__ u, double W) {
+    extern __shared__ cf coef2[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int lev = A.blevel[b];
+    int P = A.Plev[lev];
+    int nc = 2 * P + 1;
+    double rb = 0.70710678118654752440 * ldexp(W, -lev);
+    const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        // Laplace layout [c0, zeta^1..zeta^P, eta^1..eta^P]; Helmholtz [c_-P .. c_P]
+        int n = KER == CFMM_LAPLACE ? (c <= P ? c : c - P) : abs(c - P);
+        double s = 1.0, g = KER == CFMM_LAPLACE ? rb : 0.5 * A.kappa * rb;
+        for (int j = 1; j <= n; ++j) s *= KER == CFMM_LAPLACE ? g : g / j;
+        if (KER != CFMM_LAPLACE && c < P && (n & 1)) s = -s;
+        coef2[c] = to_cf(s * lc[c]);
+    }
+    __syncthreads();
+    double irb = 1.0 / rb;
+    cd c0 = {A.cre[2 * b], A.cim[2 * b]}, c1 = {A.cre[2 * b + 1], A.cim[2 * b + 1]};
+    cf G[kL2p2fMaxP + 1];
+    for (int i = A.bst[b] + threadIdx.x; i < A.ben[b]; i += blockDim.x) {
+        cd d0 = irb * (cd{A.xr[i], A.xi[i]} - c0), d1 = irb * (cd{A.xr[A.n + i], A.xi[A.n + i]} - c1);
+        cf zt = to_cf(d0 + mul_i(d1)), et = to_cf(d0 - mul_i(d1));
+        Kahan acc;
+        if (KER == CFMM_LAPLACE) {
+            acc.add(coef2[0]);
+            cf zp = zt, ep = et;
+            for (int nn = 1; nn <= P; ++nn) {
+                acc.add(cmacf(coef2[nn] * zp, coef2[P + nn], ep));
+                zp = zp * zt;
+                ep = ep * et;
+            }
+        } else {
+            float kr = (float)(A.kappa * rb);
+            cf w = (kr * kr) * (zt * et);
+            cf zz = csqrtf_p(w);
+            float big = fmaxf((float)P, hypotf(zz.x, zz.y));
+            int N = (int)big + 12 + (int)sqrtf(8.f * big);
+            bool up = zz.y >= 0.f;
+            cf a = 0.5f * (up ? cf{zz.y, -zz.x} : cf{-zz.y, zz.x});   // -+ i z / 2
+            cf q = {1.f, 0.f}, H = {1.f, 0.f};
+            for (int nn = N; nn >= 1; --nn) {
+                float den = 0.25f / ((float)nn * (float)(nn + 1));
+                q = cinvf(cf{1.f, 0.f} - (den * w) * q);
+                if (nn <= P) G[nn] = q;
+                H = cf{1.f, 0.f} + (1.f / (float)nn) * (a * (q * H));
+            }
+            float ex = expf(2.f * a.x), sn, cs;
+            sincosf(2.f * a.y, &sn, &cs);
+            cf g = cf{ex * cs, ex * sn} * cinvf(2.f * H - cf{1.f, 0.f});
+            acc.add(coef2[P] * g);
+            cf zp = zt, ep = et;
+            for (int nn = 1; nn <= P; ++nn) {
+                g = g * G[nn];
+                acc.add(g * cmacf(coef2[P + nn] * zp, coef2[P - nn], ep));
+                zp = zp * zt;
+                ep = ep * et;
+            }
+        }
+        u[(int64_t)rhs * A.n + i] += acc.value();
     }
 }
 
@@ -1043,13 +1132,17 @@ void fmm2d_setup(cfmm_plan_s* P) {
             for (int l = 0; l < T.nlevels; ++l) {
                 S->lvl_chunk0[l] = (int)cb.size();
                 S->lvl_part0[l] = pslot;
+                // chunk length: at most kM2LChunk entries, shorter when the level has
+                // too few entries to give every SM two blocks (a coarse top level)
+                int ent = loff[T.level_off[l + 1]] - loff[T.level_off[l]];
+                int clen = std::max(4, std::min(kM2LChunk, ent / (2 * num_sms())));
                 for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) {
                     bc0[b] = (int)cb.size();
                     if (l < S->l0) continue;
-                    for (int q = loff[b]; q < loff[b + 1]; q += kM2LChunk) {
+                    for (int q = loff[b]; q < loff[b + 1]; q += clen) {
                         cb.push_back(b);
                         c0v.push_back(q);
-                        c1v.push_back(std::min(q + kM2LChunk, loff[b + 1]));
+                        c1v.push_back(std::min(q + clen, loff[b + 1]));
                     }
                 }
                 if (l >= S->l0) pslot += (int64_t)((int)cb.size() - S->lvl_chunk0[l]) * (2 * S->Plev[l] + 1);
@@ -1222,14 +1315,20 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     rec(6);
     rec(7);
     near_join(P);   // the near field has written u
-    // (5) M2P and (8) L2P (add to u)
+    // (5) M2P and (8) L2P (add to u; L2P in complex64 in mixed precision)
     {
         // with the plan's rows, L2P needs no per-thread row space
         size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (S->lrow.get() ? 0 : (size_t)kExpThreads * (maxP + 2)));
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
+        bool l2p32 = P->precision == CFMM_MIXED && S->maxP_leaf <= kL2p2fMaxP;
         k_eval<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc,
-                                                 u, maxP, S->lrow.get(), S->RL);
+                                                 u, maxP, S->lrow.get(), S->RL, l2p32 ? 0 : 1);
         CFMM_LAUNCHED();
+        if (l2p32 && g.x) {
+            k_l2p2f<KER><<<g, kExpThreads, sizeof(cf) * (2 * S->maxP_leaf + 1), st>>>(A, S->d_leaves_l0.get(), lc,
+                                                                                       u, P->W);
+            CFMM_LAUNCHED();
+        }
     }
     rec(8);
 }

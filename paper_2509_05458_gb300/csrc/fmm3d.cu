@@ -233,7 +233,7 @@ __device__ cd eval_series(bool reg, cd a0, cd a1, cd a2, int P, const cd* coef) 
 
 __global__ void k_eval3(Exp3Args A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                         const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
-                        cd* __restrict__ u, int maxP) {
+                        cd* __restrict__ u, int maxP, int do_l2p) {
     extern __shared__ cd sm[];
     int b = leaves[blockIdx.x];
     int rhs = blockIdx.y;
@@ -259,6 +259,11 @@ __global__ void k_eval3(Exp3Args A, const int* __restrict__ leaves, const int* _
                 for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * s + a], A.cim[3 * s + a]};
                 acc += eval_series(false, d[0], d[1], d[2], Ps, coef);
             }
+        }
+        if (!do_l2p) {
+            // M2P only (the L2P runs in complex64): leaves without List 3 add nothing
+            if (valid && l3off[b + 1] > l3off[b]) u[(int64_t)rhs * A.n + i] += acc;
+            continue;
         }
         __syncthreads();
         const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
@@ -457,12 +462,14 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     rec(6);
     rec(7);
     near_join(P);   // the near field has written u
-    // (5) M2P, (8) L2P
+    // (5) M2P, (8) L2P (complex64 in mixed precision)
     {
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
         k_eval3<<<g, kExp3Threads, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
-                                                          mp, lc, u, maxP);
+                                                          mp, lc, u, maxP, mixed ? 0 : 1);
         CFMM_LAUNCHED();
+        if (mixed) lap3_l2p32(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
+                              S->exp_off.get(), S->ncoef, lc, u, nrhs);
     }
     rec(8);
 }

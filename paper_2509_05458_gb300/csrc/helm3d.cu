@@ -84,6 +84,7 @@ struct H3Tables {
     DevBuf<int> knm;         // k -> n * 256 + (m + 128), k < (Pmax+1)^2
     DevBuf<double> lsm, lsd; // eps_m s_n^m and eps_m / s_n^m, s = sqrt((n-|m|)! (n+|m|)!)
     DevBuf<double> fact, ifact;  // j! and 1/j!, j <= 2 Pmax + 2
+    DevBuf<float> zAf, zBf, dgf, s21f;   // FP32 copies of zA, zB, dg, s21 (mixed-precision L2P)
 };
 
 // Tables only grow: a larger order builds a new set and the older sets stay
@@ -273,6 +274,17 @@ static H3Tables* tables(int P) {
     }
     T->knm.alloc(knm.size());
     CFMM_CUDA(cudaMemcpy(T->knm.get(), knm.data(), sizeof(int) * knm.size(), cudaMemcpyHostToDevice));
+    {
+        auto upf = [](DevBuf<float>& b, const std::vector<double>& v) {
+            std::vector<float> f(v.begin(), v.end());
+            b.alloc(f.size());
+            CFMM_CUDA(cudaMemcpy(b.get(), f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+        };
+        upf(T->zAf, zA);
+        upf(T->zBf, zB);
+        upf(T->dgf, dg);
+        upf(T->s21f, s21);
+    }
 
     T->zA.alloc(zA.size());
     T->zB.alloc(zB.size());
@@ -643,7 +655,7 @@ __device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const
 // M2P over List 3 (S waves) and L2P (R waves); one thread per target.
 __global__ void k_eval3h(Exp3hArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                          const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
-                         cd* __restrict__ u) {
+                         cd* __restrict__ u, int do_l2p) {
     extern __shared__ cd sm[];
     int b = leaves[blockIdx.x];
     int rhs = blockIdx.y;
@@ -672,6 +684,11 @@ __global__ void k_eval3h(Exp3hArgs A, const int* __restrict__ leaves, const int*
                 acc += eval_wave(A.zc, d[0], d[1], d[2], Ps, F, coef);
             }
         }
+        if (!do_l2p) {
+            // M2P only (the L2P runs in complex64): leaves without List 3 add nothing
+            if (valid && l3off[b + 1] > l3off[b]) u[(int64_t)rhs * A.n + i] += acc;
+            continue;
+        }
         __syncthreads();
         const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
         for (int c = threadIdx.x; c < nc; c += blockDim.x) coef[c] = lc[c];
@@ -684,6 +701,154 @@ __global__ void k_eval3h(Exp3hArgs A, const int* __restrict__ leaves, const int*
             u[(int64_t)rhs * A.n + i] += acc;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// L2P in complex64 arithmetic (mixed precision), 3D Helmholtz and Laplace.
+//
+// With x~ = (x - c)/rho_b (rho_b = sqrt(3)/2 w, the leaf's radius) the local
+// expansion is evaluated as
+//   Helmholtz  u = sum L^_n^m jh_n(k rho) Z_n^m(x~),  L^ = L_n^m (k rho_b)^n/(2n+1)!!
+//   Laplace    u = sum L^_n^m Z_n^m(x~),              L^ = L_n^m lsd_n^m rho_b^n
+// (Z_n^m(x) = rho_b^n Z_n^m(x~); U_n^m = lsd_n^m Z_n^m), where
+//   jh_n(z) = j_n(z) (2n+1)!!/z^n
+// is entire in w = z^2 with jh_n(0) = 1, so every factor stays O(1) in FP32
+// at any leaf size. From j_{n-1} + j_{n+1} = (2n+1)/z j_n,
+//   jh_{n-1} = jh_n - w jh_{n+1}/((2n+1)(2n+3)),
+// and the ratios q_n = jh_n/jh_{n-1} = 1/(1 - w q_{n+1}/((2n+1)(2n+3))) follow
+// by Miller's backward recurrence from q = 1 far above P; jh_0 = j_0 comes
+// from the plane-wave normalisation exp(-+ i z) = sum (2n+1) (-+ i)^n j_n =
+// jh_0 sum (-+ i z)^n/(2n-1)!! prod_{k<=n} q_k (sign with |exp| >= 1, as in
+// the FP64 Miller recurrence). The coefficients are formed in FP64 per leaf
+// and rounded; each harmonic column is summed in FP32 and the columns in a
+// compensated (Kahan) FP32 sum.
+// ---------------------------------------------------------------------------
+struct L2p3fArgs {
+    const double* xr;
+    const double* xi;
+    int64_t n;
+    const int* blevel;
+    const int* bst;
+    const int* ben;
+    const double* cre;
+    const double* cim;
+    const int* Plev;
+    const int64_t* eoff;
+    int64_t ncoef;
+    double kappa;
+    double W;            // root box width
+    const float* zA;     // FP32 Z recurrence coefficients by nmi(n, m >= 0)
+    const float* zB;
+    const float* dg;
+    const float* s21;
+    const int* knm;
+    const double* lsd;   // Laplace: e_m / s_n^m by nmi(n, m)
+};
+
+template <bool HELM>
+__global__ void __launch_bounds__(128) k_l2p3f(L2p3fArgs A, const int* __restrict__ leaves,
+                                                const cd* __restrict__ loc, cd* __restrict__ u) {
+    extern __shared__ unsigned char smraw[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int lev = A.blevel[b];
+    int P = A.Plev[lev];
+    int nc = (P + 1) * (P + 1);
+    double rb = 0.86602540378443864676 * ldexp(A.W, -lev);
+    double* scl = reinterpret_cast<double*>(smraw);              // P + 1
+    cf* coef = reinterpret_cast<cf*>(scl + (P + 1));             // (P + 1)^2
+    if (threadIdx.x == 0) {
+        double f = 1.0, g = HELM ? A.kappa * rb : rb;
+        for (int n = 0; n <= P; ++n) {
+            scl[n] = f;
+            f *= HELM ? g / (2.0 * n + 3.0) : g;
+        }
+    }
+    __syncthreads();
+    const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int n, m;
+        nm_tab(A.knm, c, n, m);
+        double s = scl[n];
+        if (!HELM) s *= __ldg(A.lsd + c);
+        coef[c] = to_cf(s * lc[c]);
+    }
+    __syncthreads();
+    double irb = 1.0 / rb;
+    cd cen[3];
+    for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+    cf G[kH3MaxP + 1];
+    for (int i = A.bst[b] + threadIdx.x; i < A.ben[b]; i += blockDim.x) {
+        cf x[3];
+        for (int a = 0; a < 3; ++a)
+            x[a] = to_cf(irb * (cd{A.xr[a * A.n + i], A.xi[a * A.n + i]} - cen[a]));
+        cf xp = x[0] + mul_if(x[1]), xm = x[0] - mul_if(x[1]), z = x[2];
+        cf r2 = xp * xm + z * z;
+        if (HELM) {
+            // w = (k rho)^2 = (k rho_b)^2 x~.x~
+            float kr = (float)(A.kappa * rb);
+            cf w = (kr * kr) * r2;
+            cf zz = csqrtf_p(w);
+            float big = fmaxf((float)P, hypotf(zz.x, zz.y));
+            int N = (int)big + 12 + (int)sqrtf(8.f * big);
+            bool up = zz.y >= 0.f;                       // exp(-i z), |.| >= 1
+            cf a = up ? cf{zz.y, -zz.x} : cf{-zz.y, zz.x};   // -+ i z
+            cf q = {1.f, 0.f}, H = {1.f, 0.f};
+            for (int nn = N; nn >= 1; --nn) {
+                float den = 1.f / ((2.f * nn + 1.f) * (2.f * nn + 3.f));
+                q = cinvf(cf{1.f, 0.f} - (den * w) * q);
+                if (nn <= P) G[nn] = q;
+                H = cf{1.f, 0.f} + (1.f / (2.f * nn - 1.f)) * (a * (q * H));
+            }
+            // jh_0 = exp(a) / H
+            float ex = expf(a.x), sn, cs;
+            sincosf(a.y, &sn, &cs);
+            cf g = cf{ex * cs, ex * sn} * cinvf(H);
+            G[0] = g;
+            for (int nn = 1; nn <= P; ++nn) {
+                g = g * G[nn];
+                G[nn] = g;
+            }
+        }
+        Kahan acc;
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            cf xs = sgn ? xm : xp;
+            cf d = {1.f, 0.f};
+            for (int m = 0; m <= P; ++m) {
+                if (m > 0) d = (-__ldg(A.dg + m)) * (xs * d);
+                if (sgn == 1 && m == 0) continue;
+                int mi = sgn ? -m : m;
+                cf col = coef[nmi(m, mi)] * (HELM ? G[m] * d : d);
+                if (m + 1 <= P) {
+                    cf p2 = d, p1 = __ldg(A.s21 + m) * (z * d);
+                    col = cmacf(col, coef[nmi(m + 1, mi)], HELM ? G[m + 1] * p1 : p1);
+                    for (int n = m + 2; n <= P; ++n) {
+                        int k = nmi(n, m);
+                        cf cur = __ldg(A.zA + k) * (z * p1) - __ldg(A.zB + k) * (r2 * p2);
+                        col = cmacf(col, coef[nmi(n, mi)], HELM ? G[n] * cur : cur);
+                        p2 = p1;
+                        p1 = cur;
+                    }
+                }
+                acc.add(col);
+            }
+        }
+        u[(int64_t)rhs * A.n + i] += acc.value();
+    }
+}
+
+static void launch_l2p3f(H3Tables* TB, bool helm, cfmm_plan_s* P, const int* leaves, int cnt, int maxP,
+                         const int* dPlev, const int64_t* eoff, int64_t ncoef, const cd* loc, cd* u, int nrhs) {
+    if (cnt == 0) return;
+    TreeDev& T = P->tree;
+    L2p3fArgs A{P->xr.get(), P->xi.get(), P->n, T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(),
+                T.cen_im.get(), dPlev, eoff, ncoef, P->kappa, P->W, TB->zAf.get(), TB->zBf.get(),
+                TB->dgf.get(), TB->s21f.get(), TB->knm.get(), TB->lsd.get()};
+    size_t smem = sizeof(double) * (size_t)(maxP + 1) + sizeof(cf) * (size_t)(maxP + 1) * (maxP + 1);
+    dim3 g((unsigned)cnt, nrhs);
+    if (helm) k_l2p3f<true><<<g, 128, smem, P->stream>>>(A, leaves, loc, u);
+    else k_l2p3f<false><<<g, 128, smem, P->stream>>>(A, leaves, loc, u);
+    CFMM_LAUNCHED();
 }
 
 // ---------------------------------------------------------------------------
@@ -1462,7 +1627,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     int maxP = S->maxP;
     // (3) P2P (writes u) on the side stream, beside the far field
     launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
+               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed, T.level.get(), P->W, P->sep);
     near_launched(P);
     auto p2x_smem = [&](int PL, int& chunk) {
         size_t nc = (size_t)(PL + 1) * (PL + 1);
@@ -1628,12 +1793,14 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     rec(6);
     rec(7);
     near_join(P);   // the near field has written u
-    // (5) M2P, (8) L2P
+    // (5) M2P, (8) L2P (complex64 in mixed precision)
     {
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);
         k_eval3h<<<g, 128, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
-            A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, u);
+            A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, u, mixed ? 0 : 1);
         CFMM_LAUNCHED();
+        if (mixed) launch_l2p3f(TB, true, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
+                                S->exp_off.get(), S->ncoef, lc, u, nrhs);
     }
     rec(8);
 }
@@ -1689,6 +1856,12 @@ bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int max
                                                           TB->lsd.get());
     CFMM_LAUNCHED();
     return true;
+}
+
+void lap3_l2p32(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                const int64_t* eoff, int64_t ncoef, const cd* loc, cd* u, int nrhs) {
+    CFMM_REQUIRE(maxP <= L->tab->Pmax, CFMM_ECUDA, "3D Laplace L2P: order beyond the tables");
+    launch_l2p3f(L->tab, false, P, leaves, cnt, maxP, dPlev, eoff, ncoef, loc, u, nrhs);
 }
 
 void lap3_tr_destroy(Lap3Tr* L) { delete L; }

@@ -32,9 +32,11 @@ struct KParams {
 cudaStream_t near_fork(cfmm_plan_s* P);
 void near_launched(cfmm_plan_s* P);
 void near_join(cfmm_plan_s* P);
+// blevel/W/sep: the tree's box levels, root width and separation (the mixed
+// 3D Helmholtz near field sizes its coordinate grid from them; NULL = unknown)
 void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
                 const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
-                bool mixed = false);
+                bool mixed = false, const int* blevel = nullptr, double W = 0.0, int sep = 1);
 void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st, bool mixed = false);
 
 // tree construction (tree.cu)
@@ -94,6 +96,9 @@ bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int max
                   const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs);
 void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const int64_t* eoff, int64_t ncoef,
                     const cd* in, cd* out, int nrhs);
+// 3D Laplace L2P in complex64 arithmetic over `leaves` (adds to u)
+void lap3_l2p32(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                const int64_t* eoff, int64_t ncoef, const cd* loc, cd* u, int nrhs);
 
 void upload_lag_rule_p2p();
 void upload_lag_rule_fmm2d();

@@ -269,33 +269,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_direct(KParams K, cd* __restric
 // close). Sums over sources use compensated (Kahan) FP32 accumulation; the
 // few partial sums of a target are combined in FP64.
 // ---------------------------------------------------------------------------
-CFMM_HD cf cinvf(cf b) {
-    float den = b.x * b.x + b.y * b.y;
-    return cf{b.x / den, -b.y / den};
-}
-__device__ __forceinline__ cf csqrtf_p(cf z) {
-    float a = z.x, b = z.y;
-    if (a == 0.f && b == 0.f) return cf{0.f, 0.f};
-    float m = hypotf(a, b);
-    float t = sqrtf(0.5f * (fabsf(a) + m));
-    if (a >= 0.f) return cf{t, b / (2.f * t)};
-    return cf{fabsf(b) / (2.f * t), copysignf(t, b)};
-}
-__device__ __forceinline__ cf mul_if(cf a) { return cf{-a.y, a.x}; }
-
-struct Kahan {
-    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-    __device__ __forceinline__ void add(cf v) {
-        float yx = v.x - cx, tx = sx + yx;
-        cx = (tx - sx) - yx;
-        sx = tx;
-        float yy = v.y - cy, ty = sy + yy;
-        cy = (ty - sy) - yy;
-        sy = ty;
-    }
-    __device__ __forceinline__ cd value() const { return cd{(double)sx - (double)cx, (double)sy - (double)cy}; }
-};
-
 __device__ __forceinline__ void helm2d_pair32(cf r2, float kappa, bool dlp, cf& h0, cf& g1) {
     const float kPi = 3.14159265f, kG = 0.5772156649f;
     float k2 = kappa * kappa;
@@ -616,6 +589,220 @@ __global__ void __launch_bounds__(kP2PThreads) k_direct32(KParams K, cd* __restr
     finish_target<DIM, KER>(acc.value(), red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti, false);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision 3D Helmholtz near field on a power-of-two grid.
+//
+// Every coordinate v of a List-1 pair (real and imaginary parts, offsets from
+// the target leaf's first point) is split as v = h + l with h = g rint(v/g)
+// on a grid of step g = 2^e >= R/1024, R = 1.5 (k+1) w the per-axis reach of
+// the near field of a leaf of width w at separation k (List-1 leaves differ
+// by at most one level), and l = v - h, |l| <= g/2, rounded to FP32. Then the
+// differences dh = x_h - y_h are multiples of g below 2048 g and are exact in
+// FP32, as are their products and the sums of three of them (below 2^24 g^2):
+//   r^2 = S_h + S_l,  S_h = sum dh_re^2 - dh_im^2 + 2 i dh_re dh_im  (exact),
+//   S_l = sum (2 dh + dl) dl terms                           (FP32, small),
+// so r^2 is known as an unevaluated FP32 pair to ~2^-24 g |r| absolute. The
+// root r0 of the rounded sum is refined by one Newton step computed from
+// that pair (r = r0 + (r^2 - r0^2)/(2 r0), with r0^2 formed by exact
+// products), and kappa r is formed in double-float, so the phase and the
+// decay exp(-kappa Im r) keep absolute errors near kappa g 2^-24 at any
+// kappa r. The phase is reduced by 2 pi before sincosf. Sources are staged
+// as float4 quadruples; the sum over sources is compensated (Kahan).
+// ---------------------------------------------------------------------------
+struct SrcTileG {
+    float4 q0[kP2PChunk], q1[kP2PChunk], q2[kP2PChunk], dn[kP2PChunk];   // coordinates, densities
+    float4 n0[kP2PChunk], n1[kP2PChunk], n2[kP2PChunk];                  // normals (double layer)
+};
+
+// v = h + l on the grid of step g (h exact in FP32 for |v| < 2^23 g)
+__device__ __forceinline__ void split_grid(double v, double g, double ig, float& h, float& l) {
+    double hv = g * rint(v * ig);
+    h = (float)hv;
+    l = (float)(v - hv);
+}
+
+// (re hi x3, im hi x3, re lo x3, im lo x3) <-> three float4
+__device__ __forceinline__ void pack12(const float* a, float4& q0, float4& q1, float4& q2) {
+    q0 = make_float4(a[0], a[1], a[2], a[3]);
+    q1 = make_float4(a[4], a[5], a[6], a[7]);
+    q2 = make_float4(a[8], a[9], a[10], a[11]);
+}
+
+// grid step for a target leaf of width w at separation k: 2^ceil(log2(R/1024))
+__device__ __forceinline__ double near_grid_step(double w, int sep) {
+    double R = 1.5 * (sep + 1) * w;
+    int e;
+    frexp(R / 1024.0, &e);     // R/1024 = f 2^e, f in [0.5, 1)
+    return ldexp(1.0, e);
+}
+
+__global__ void __launch_bounds__(kP2PThreads) k_p2p32g_h3(KParams K, const int* __restrict__ leaf_boxes,
+                                                           const int* __restrict__ bst, const int* __restrict__ ben,
+                                                           const int* __restrict__ l1off,
+                                                           const int* __restrict__ l1,
+                                                           const int* __restrict__ blevel, double W, int sep,
+                                                           cd* __restrict__ out, int add) {
+    __shared__ SrcTileG S;
+    __shared__ cd red[kP2PThreads];
+    const int64_t n = K.n_src;
+    int b = leaf_boxes[blockIdx.x];
+    int rhs = blockIdx.y;
+    int tl = threadIdx.x % kP2PTargets, split = threadIdx.x / kP2PTargets;
+    int ts = bst[b], te = ben[b];
+    double g = near_grid_step(ldexp(W, -blevel[b]), sep), ig = 1.0 / g;
+    double ref_re[3], ref_im[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ref_re[a] = K.trg_re[a * K.n_trg + ts];
+        ref_im[a] = K.trg_im[a * K.n_trg + ts];
+    }
+    const float kh = (float)K.kappa, kl = (float)(K.kappa - (double)kh);
+    const float kTwoPiH = 6.28318548202514648f;     // float(2 pi)
+    const float kTwoPiL = -1.74845553e-07f;         // 2 pi - float(2 pi)
+    for (int t0 = ts; t0 < te; t0 += kP2PTargets) {
+        int ti = t0 + tl;
+        bool tvalid = ti < te;
+        // target: x[0..2] re hi, x[3..5] im hi, x[6..8] re lo, x[9..11] im lo
+        float x[12];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double vr = tvalid ? K.trg_re[a * K.n_trg + ti] - ref_re[a] : 0.0;
+            double vi = tvalid ? K.trg_im[a * K.n_trg + ti] - ref_im[a] : 0.0;
+            split_grid(vr, g, ig, x[a], x[6 + a]);
+            split_grid(vi, g, ig, x[3 + a], x[9 + a]);
+        }
+        Kahan acc;
+        for (int q = l1off[b]; q < l1off[b + 1]; ++q) {
+            int src = l1[q];
+            int s0 = bst[src], s1 = ben[src];
+            for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
+                int cn = min(kP2PChunk, s1 - c0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+                    int gi = c0 + j;
+                    float y[12];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        split_grid(K.src_re[a * n + gi] - ref_re[a], g, ig, y[a], y[6 + a]);
+                        split_grid(K.src_im[a * n + gi] - ref_im[a], g, ig, y[3 + a], y[9 + a]);
+                    }
+                    pack12(y, S.q0[j], S.q1[j], S.q2[j]);
+                    float4 dn = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (K.slp) {
+                        cd v = K.sigma[(int64_t)rhs * K.dens_stride + gi];
+                        dn.x = (float)v.x;
+                        dn.y = (float)v.y;
+                    }
+                    if (K.dlp) {
+                        cd v = K.tau[(int64_t)rhs * K.dens_stride + gi];
+                        dn.z = (float)v.x;
+                        dn.w = (float)v.y;
+                        float nv[12];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            split_hl(K.nrm_re[a * n + gi], nv[a], nv[6 + a]);
+                            split_hl(K.nrm_im[a * n + gi], nv[3 + a], nv[9 + a]);
+                        }
+                        pack12(nv, S.n0[j], S.n1[j], S.n2[j]);
+                    }
+                    S.dn[j] = dn;
+                }
+                __syncthreads();
+                if (!tvalid) continue;
+                for (int j = split; j < cn; j += kP2PSplit) {
+                    float4 a0 = S.q0[j], a1 = S.q1[j], a2 = S.q2[j];
+                    // dh: re 0..2, im 0..2 (exact); dl likewise
+                    float hr0 = x[0] - a0.x, hr1 = x[1] - a0.y, hr2 = x[2] - a0.z;
+                    float hi0 = x[3] - a0.w, hi1 = x[4] - a1.x, hi2 = x[5] - a1.y;
+                    float lr0 = x[6] - a1.z, lr1 = x[7] - a1.w, lr2 = x[8] - a2.x;
+                    float li0 = x[9] - a2.y, li1 = x[10] - a2.z, li2 = x[11] - a2.w;
+                    unsigned nz = (__float_as_uint(hr0) | __float_as_uint(hr1) | __float_as_uint(hr2) |
+                                   __float_as_uint(hi0) | __float_as_uint(hi1) | __float_as_uint(hi2) |
+                                   __float_as_uint(lr0) | __float_as_uint(lr1) | __float_as_uint(lr2) |
+                                   __float_as_uint(li0) | __float_as_uint(li1) | __float_as_uint(li2)) &
+                                  0x7fffffffu;
+                    if (nz == 0u) continue;   // x == y: self pair / coincident point
+                    // r^2 = (Srh + Srl) + i (Sih + Sil)
+                    float Srh = hr0 * hr0;
+                    Srh = fmaf(hr1, hr1, Srh);
+                    Srh = fmaf(hr2, hr2, Srh);
+                    Srh = fmaf(-hi0, hi0, Srh);
+                    Srh = fmaf(-hi1, hi1, Srh);
+                    Srh = fmaf(-hi2, hi2, Srh);
+                    float Sih = hr0 * hi0;
+                    Sih = fmaf(hr1, hi1, Sih);
+                    Sih = fmaf(hr2, hi2, Sih);
+                    Sih = 2.f * Sih;
+                    float Srl = fmaf(2.f, hr0, lr0) * lr0;
+                    Srl = fmaf(fmaf(2.f, hr1, lr1), lr1, Srl);
+                    Srl = fmaf(fmaf(2.f, hr2, lr2), lr2, Srl);
+                    Srl = fmaf(-fmaf(2.f, hi0, li0), li0, Srl);
+                    Srl = fmaf(-fmaf(2.f, hi1, li1), li1, Srl);
+                    Srl = fmaf(-fmaf(2.f, hi2, li2), li2, Srl);
+                    float Sil = fmaf(hr0, li0, lr0 * (hi0 + li0));
+                    Sil = fmaf(hr1, li1, fmaf(lr1, hi1 + li1, Sil));
+                    Sil = fmaf(hr2, li2, fmaf(lr2, hi2 + li2, Sil));
+                    Sil = 2.f * Sil;
+                    float ra = Srh + Srl, rb = Sih + Sil;
+                    // r0 = principal sqrt(ra + i rb) in FP32 (refined below)
+                    float m = sqrtf(fmaf(ra, ra, rb * rb));
+                    float t2 = 0.5f * (fabsf(ra) + m);
+                    float rt = rsqrtf(t2);
+                    float t = t2 * rt, u = 0.5f * rb * rt;
+                    float a0r = ra >= 0.f ? t : fabsf(u);
+                    float b0r = ra >= 0.f ? u : copysignf(t, rb);
+                    // Newton step: delta = (r^2 - r0^2)/(2 r0), r0^2 from exact products
+                    float p = a0r * a0r, e1 = fmaf(a0r, a0r, -p);
+                    float qq = b0r * b0r, e2 = fmaf(b0r, b0r, -qq);
+                    float hs, ls;
+                    two_sum(p, -qq, hs, ls);
+                    float dre = ((Srh - hs) - ls) + ((Srl - e1) + e2);
+                    float pi_ = a0r * b0r, e3 = fmaf(a0r, b0r, -pi_);
+                    float dim = ((Sih - 2.f * pi_) - 2.f * e3) + Sil;
+                    float i2m = __fdividef(0.5f, m);
+                    float der = fmaf(dre, a0r, dim * b0r) * i2m;
+                    float dei = fmaf(dim, a0r, -dre * b0r) * i2m;
+                    // kappa r in double-float: (th + te) + i (dh + de)
+                    float th, tq, dh, dq;
+                    two_prod(kh, a0r, th, tq);
+                    tq = fmaf(kh, der, fmaf(kl, a0r, tq));
+                    two_prod(kh, b0r, dh, dq);
+                    dq = fmaf(kh, dei, fmaf(kl, b0r, dq));
+                    float kk = rintf(th * 0.159154943f);
+                    float q2, q2e;
+                    two_prod(kk, kTwoPiH, q2, q2e);
+                    float ph = (th - q2) + ((tq - q2e) - kk * kTwoPiL);
+                    float sn, cs;
+                    sincosf(ph, &sn, &cs);
+                    float mag = expf(-dh) * (1.f - dq);
+                    // 1/r with r = r0 + delta rounded to FP32
+                    float rr = a0r + der, ri = b0r + dei;
+                    float id = __frcp_rn(fmaf(rr, rr, ri * ri));
+                    float irr = rr * id, iri = -ri * id;
+                    cf gk = cf{mag * cs, mag * sn} * cf{irr, iri};   // e^{i kappa r}/r
+                    float4 dn = S.dn[j];
+                    cf v = {0.f, 0.f};
+                    if (K.slp) v = gk * cf{dn.x, dn.y};
+                    if (K.dlp) {
+                        float4 b0 = S.n0[j], b1 = S.n1[j], b2 = S.n2[j];
+                        const float dh_r[3] = {hr0, hr1, hr2}, dl_r[3] = {lr0, lr1, lr2};
+                        const float dh_i[3] = {hi0, hi1, hi2}, dl_i[3] = {li0, li1, li2};
+                        const float nh_r[3] = {b0.x, b0.y, b0.z}, nh_i[3] = {b0.w, b1.x, b1.y};
+                        const float nl_r[3] = {b1.z, b1.w, b2.x}, nl_i[3] = {b2.y, b2.z, b2.w};
+                        cf nd = dot_nd<3>(dh_r, dl_r, dh_i, dl_i, nh_r, nl_r, nh_i, nl_i);
+                        cf ir = {irr, iri};
+                        cf kr = {kh * rr, kh * ri};
+                        v = v + (nd * (cf{1.f, 0.f} - mul_if(kr)) * gk * (ir * ir)) * cf{dn.z, dn.w};
+                    }
+                    acc.add(v);
+                }
+            }
+        }
+        finish_target<3, CFMM_HELMHOLTZ>(acc.value(), red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti,
+                                        add != 0);
+    }
+}
+
 template <int DIM, int KER>
 static void launch_p2p_t(const KParams& K, const int* leaf_boxes, int nleaves, const int* bst, const int* ben,
                          const int* l1off, const int* l1, cd* out, int nrhs, bool add, bool mixed, cudaStream_t st) {
@@ -628,7 +815,14 @@ static void launch_p2p_t(const KParams& K, const int* leaf_boxes, int nleaves, c
 
 void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
                 const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
-                bool mixed) {
+                bool mixed, const int* blevel, double W, int sep) {
+    if (mixed && dim == 3 && ker == CFMM_HELMHOLTZ && blevel && nleaves > 0) {
+        dim3 grid(nleaves, nrhs);
+        k_p2p32g_h3<<<grid, kP2PThreads, 0, st>>>(K, leaf_boxes, bst, ben, l1off, l1, blevel, W, sep, out,
+                                                  add ? 1 : 0);
+        CFMM_LAUNCHED();
+        return;
+    }
     if (dim == 2 && ker == CFMM_LAPLACE) launch_p2p_t<2, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
     else if (dim == 2) launch_p2p_t<2, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
     else if (ker == CFMM_LAPLACE) launch_p2p_t<3, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);

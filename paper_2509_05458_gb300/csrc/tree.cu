@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 
 #include "cfmm_common.cuh"
 #include "kernels.cuh"
@@ -1117,6 +1118,61 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
 
 // Builds the sorted geometry and the tree of a plan. re/im (and nre/nim when
 // not null) are device copies of the caller's [n][dim] arrays.
+// Lipschitz estimate of Im x against Re x (Assumptions 4.1/5.1): over the
+// pairs of points at most kLipWindow apart in Morton order (spatially close),
+// max |Im(x_i - x_j)|^2 / |Re(x_i - x_j)|^2, as the bits of a non-negative
+// float (inf when Re x_i = Re x_j but Im x_i != Im x_j). Coincident points
+// are skipped.
+constexpr int kLipWindow = 32;
+__global__ void k_lipschitz(const double* __restrict__ xr, const double* __restrict__ xi, int64_t n, int dim,
+                            unsigned* __restrict__ out) {
+    __shared__ unsigned best_s;
+    if (threadIdx.x == 0) best_s = 0u;
+    __syncthreads();
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float best = 0.f;
+    if (i < n) {
+        int64_t jmax = i + kLipWindow < n - 1 ? i + kLipWindow : n - 1;
+        for (int64_t j = i + 1; j <= jmax; ++j) {
+            float a2 = 0.f, b2 = 0.f;
+            for (int a = 0; a < dim; ++a) {
+                float dr = (float)(xr[a * n + i] - xr[a * n + j]);
+                float di = (float)(xi[a * n + i] - xi[a * n + j]);
+                a2 = fmaf(dr, dr, a2);
+                b2 = fmaf(di, di, b2);
+            }
+            if (b2 == 0.f) continue;
+            best = fmaxf(best, a2 > 0.f ? b2 / a2 : INFINITY);
+        }
+    }
+    atomicMax(&best_s, __float_as_uint(best));
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(out, best_s);
+}
+
+// Largest Lipschitz constant L for which the Sec. 6.3 criterion C_L r/R < 1
+// holds at separation k (R = (k + 1/2) w, r = sqrt(d)/2 w): 2D C_L =
+// (1+L)/(1-L) (Eq. nterms_criteria_2d), 3D C_L = sqrt(L^2+10L+1)/(1-L)
+// (Eqs. eta_const, nterms_criteria_3d).
+static double lipschitz_limit(int dim, int k) {
+    double c = (k + 0.5) / (std::sqrt((double)dim) * 0.5);
+    if (dim == 2) return (c - 1.0) / (c + 1.0);
+    // L^2 + 10 L + 1 = c^2 (1 - L)^2, root in (0, 1)
+    double a = 1.0 - c * c, b = 10.0 + 2.0 * c * c, q = 1.0 - c * c;
+    double disc = std::sqrt(b * b - 4.0 * a * q);
+    double r1 = (-b + disc) / (2.0 * a), r2 = (-b - disc) / (2.0 * a);
+    return (r1 > 0.0 && r1 < 1.0) ? r1 : r2;
+}
+
+// automatic separation: the smallest k in 1..3 with kSepLipFactor * limit(k) >= L
+// (kSepLipFactor calibrated on the surface and curve workloads; 3 if none)
+constexpr double kSepLipFactor = 2.0;
+int auto_separation(int dim, double L) {
+    for (int k = 1; k <= 3; ++k)
+        if (kSepLipFactor * lipschitz_limit(dim, k) >= L) return k;
+    return 3;
+}
+
 void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,
                 int top_level_opt) {
     cudaStream_t st = P->stream;
@@ -1198,6 +1254,25 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
     }
     CFMM_CUDA(cudaGetLastError());
     pt.mark("keys+sort");
+    // geometry assumption: Re r^2 > 0 for close pairs (Lipschitz estimate < 1)
+    {
+        unsigned* d = plan_scratch().take_n<unsigned>(1);
+        CFMM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+        if (n > 1) {
+            k_lipschitz<<<blocks_for(n, 256), 256, 0, st>>>(P->xr.get(), P->xi.get(), n, dim, d);
+            CFMM_LAUNCHED();
+        }
+        unsigned h = 0;
+        CFMM_CUDA(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CFMM_CUDA(cudaStreamSynchronize(st));
+        float r;
+        std::memcpy(&r, &h, sizeof(float));
+        P->lipschitz = std::sqrt((double)r);
+        CFMM_REQUIRE(P->lipschitz < 1.0, CFMM_EGEOM,
+                     "geometry outside the method's assumptions: Re r^2 <= 0 for a close pair (|Im dx| >= |Re dx|)");
+        if (P->sep <= 0) P->sep = auto_separation(dim, P->lipschitz);
+    }
+    pt.mark("lipschitz");
     // a3: leaves, level restriction
     LeafArrays L;
     L.take(1);

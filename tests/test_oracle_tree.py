@@ -223,3 +223,43 @@ def test_uniform_tree_list_sizes(dim, per_axis, k, list1, list2):
     assert len(T.lists["list1"][b]) == list1
     assert len(T.lists["list2"][b]) == list2
     assert T.lists["list3"][b] == [] and T.lists["list4"][b] == []
+
+
+# ---- Lipschitz estimate and the automatic separation (Sec. 4.1, 5.1, 6.3) ----
+
+@pytest.mark.parametrize("slope", [0.3, 0.5, 0.8])
+def test_lipschitz_estimate_curve_closed_form(slope):
+    """On the curve family Im x = (phi(t), 0) with phi of slope s beyond |t| = 4
+    and Re x = (t, h e^{-t^2}), |Im dx|/|Re dx| <= s, with equality (to the
+    bump's e^{-16}) for pairs beyond |t| = 4."""
+    g = curve2d(4000, seed=1, t_half=10.0, height=0.3, slope=slope)
+    T = tr.build_tree(g.re, g.im, 32)
+    L = tr.lipschitz_estimate(g.re[T.perm], g.im[T.perm])
+    assert slope * (1 - 1e-9) <= L <= slope * (1 + 1e-9)
+
+
+def test_lipschitz_estimate_surface_and_violation():
+    g = surface3d(4000, seed=1, half=10.0, slope=0.4, rho0=3.0)
+    T = tr.build_tree(g.re, g.im, 32)
+    L = tr.lipschitz_estimate(g.re[T.perm], g.im[T.perm])
+    assert 0.3 <= L <= 0.4 * (1 + 1e-9)
+    # a slope above 1 makes Re r^2 < 0 possible: the estimate reaches 1
+    g = curve2d(2000, seed=2, slope=1.3)
+    T = tr.build_tree(g.re, g.im, 32)
+    assert tr.lipschitz_estimate(g.re[T.perm], g.im[T.perm]) >= 1.0
+    # equal real parts with different imaginary parts
+    re = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 0.0]])
+    im = np.array([[0.0, 0.0], [0.1, 0.0], [0.0, 0.0]])
+    assert tr.lipschitz_estimate(re, im) == math.inf
+
+
+def test_auto_separation_from_printed_limits():
+    """With the limits printed in Sec. 6.3 (2D 0.3592, 0.5590; 3D 0.1270) and the
+    factor 2: a 2D slope 0.5 keeps k = 1; the 3D surface slope 0.4 takes k = 2
+    (0.254 < 0.4 <= 0.599); slope 0.73 takes k = 3; beyond every limit, k = 3."""
+    assert tr.auto_separation(2, 0.5) == 1
+    assert tr.auto_separation(2, 0.8) == 2
+    assert tr.auto_separation(3, 0.2) == 1
+    assert tr.auto_separation(3, 0.4) == 2
+    assert tr.auto_separation(3, 0.73) == 3
+    assert tr.auto_separation(3, 0.95) == 3
