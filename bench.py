@@ -23,7 +23,8 @@ Beside the headline, the same line carries the 3D Laplace pass on the same
 surface and the 2D Helmholtz curve configuration (k = 20, N = 1e5, SLP+DLP,
 eps = 1e-6, leaf 64), each MIXED and FP64 (--no-extras skips them).
 
-Other lines (--workload): lap3d / helm2d alone; batch3d, one 3D Helmholtz
+Other lines (--workload): lap3d / helm2d alone; wobble, the paper's own wobbly curve and surface (Sec. 7.1)
+at eps 1e-6 and 1e-12; batch3d, one 3D Helmholtz
 surface (k=15, N=2e5) with 64 right-hand sides plus 32 uneven surfaces,
 replayed as one CUDA graph; serve, the serving loop on a Poisson stream of 2D
 and 3D requests (points/s with p50/p99 latency). --n, --sep and --leaf
@@ -668,13 +669,17 @@ def run_batch(args):
 
 def run_serve(args):
     """--workload serve: the serving loop on a Poisson stream of apply requests
-    (dims 2 and 3, Laplace or Helmholtz, N log-uniform in [1e3, nmax], eps in
-    {1e-3, 1e-6, 1e-9}, 1-20 matvecs each). One step = one whole stream; value
-    = point evaluations completed per second of wall time; p50/p99 request
-    latency (arrival to last result on the host) beside it. A short stream of
-    small requests runs first, untimed."""
+    (dims 2 and 3, Laplace or Helmholtz with k ~ U[1, 50], N log-uniform in
+    [1e3, nmax], eps in {1e-3, 1e-6, 1e-9}, 1-20 matvecs each on a resident
+    plan, admission by free HBM). The arrival rate loads the GPU to about 80%:
+    0.8 over the mean service time of a calibration sample of the same
+    distribution served one at a time (unless --rate is given). The stream is
+    served with precision AUTO (mixed where eps >= 1e-5) and, for comparison,
+    the same stream in plain FP64. value = point evaluations per second of wall
+    time (AUTO pass); p50/p99 latency = arrival to last result on the host."""
     import torch
 
+    from paper_2509_05458_gb300 import AUTO, FP64
     from paper_2509_05458_gb300.serving import Server, make_stream, summarize
 
     ws, rank, local = _dist()
@@ -683,30 +688,49 @@ def run_serve(args):
         dist.init_process_group("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
+    dims = (2, 3)
     srv = Server(slots=args.slots, device=local)
-    warm = make_stream(max(4, args.warmup), seed=99 + rank, rate_hz=100.0, nmin=1000, nmax=20000, dims=(2, 3))
+    warm = make_stream(max(4, args.warmup), seed=99 + rank, rate_hz=100.0, nmin=1000, nmax=20000, dims=dims)
     srv.run(warm, realtime=False)
-    runs = []
+    rate = args.rate
+    calib = None
+    if rate <= 0:
+        sample = make_stream(24, seed=1234 + rank, rate_hz=1.0, nmin=1000, nmax=args.nmax, dims=dims, lazy=True)
+        one = Server(slots=1, device=local)
+        t0 = time.perf_counter()
+        one.run(sample, realtime=False, keep_outputs=False)
+        torch.cuda.synchronize()
+        svc = (time.perf_counter() - t0) / len(sample)
+        rate = 0.8 / svc
+        calib = {"sample_requests": len(sample), "mean_service_s": svc, "rate_hz": rate}
+    passes = {}
     clocks = ClockSampler(local)
     _barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    for k in range(args.steps):
-        reqs = make_stream(args.requests, seed=7 + 1000 * k + rank, rate_hz=args.rate, nmin=1000,
-                           nmax=args.nmax, dims=(2, 3))
-        t0 = time.perf_counter()
-        res = srv.run(reqs)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        st = summarize(res, wall)
-        st["evaluations"] = sum(len(r.rhs) * r.n for r in reqs)
-        runs.append(st)
+    for name, prec in (("auto", AUTO), ("fp64", FP64)):
+        if name == "fp64" and args.precision == "mixed":
+            continue
+        runs = []
+        for k in range(args.steps):
+            reqs = make_stream(args.requests, seed=7 + 1000 * k + rank, rate_hz=rate, nmin=1000, nmax=args.nmax,
+                               dims=dims, lazy=True, precision=prec)
+            t0 = time.perf_counter()
+            res = srv.run(reqs, keep_outputs=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            st = summarize(res, wall)
+            st["evaluations"] = sum(r.points for r in res if r.error is None)
+            st["evaluations_requested"] = sum(r.n * r.nrhs for r in reqs)
+            runs.append(st)
+        passes[name] = runs
     _barrier(ws)
     clk = clocks.stop()
-    wall = _max_over_ranks(sum(r["wall_s"] for r in runs), ws, dev)
+    main = passes["auto"]
+    wall = _max_over_ranks(sum(r["wall_s"] for r in main), ws, dev)
     if rank != 0:
         return
-    evals = sum(r["evaluations"] for r in runs)
+    evals = sum(r["evaluations"] for r in main)
     line = {
         "metric": "complex-FMM serving: points/s and p50/p99 solve latency (Poisson stream, dims 2+3)",
         "value": evals * ws / wall,
@@ -721,16 +745,22 @@ def run_serve(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": f"serving loop: Poisson stream of {args.requests} apply requests at "
-                               f"{args.rate} Hz, dim in {{2,3}}, Laplace or Helmholtz (k in [1,50], 3D mapped "
-                               f"to [1,10]), N log-uniform in [1e3, {args.nmax:.0e}], eps in {{1e-3,1e-6,1e-9}}, "
-                               "1-20 matvecs per request on a resident plan, admission by free HBM",
-                   "slots": args.slots, "requests_per_step": args.requests, "rate_hz": args.rate,
-                   "nmax": args.nmax, "parallelism": f"replicas{ws}",
+                               f"{rate:.3g} Hz, dim in {{2,3}}, Laplace or Helmholtz (k ~ U[1,50] in both "
+                               f"dimensions), N log-uniform in [1e3, {args.nmax:.0e}], eps in {{1e-3,1e-6,1e-9}}, "
+                               "1-20 matvecs per request on a resident plan, admission by free HBM, precision "
+                               "AUTO (mixed where eps >= 1e-5)",
+                   "slots": args.slots, "requests_per_step": args.requests, "rate_hz": rate,
+                   "rate_calibration": calib, "nmax": args.nmax, "parallelism": f"replicas{ws}",
                    "timing": "host wall clock per stream (latency is arrival to result on the host)"},
-        "p50_s": runs[-1]["p50_s"], "p99_s": runs[-1]["p99_s"], "mean_s": runs[-1]["mean_s"],
-        "errors": sum(r["errors"] for r in runs),
-        "error_kinds": runs[-1]["error_kinds"],
-        "streams": runs,
+        "p50_s": main[-1]["p50_s"], "p99_s": main[-1]["p99_s"], "mean_s": main[-1]["mean_s"],
+        "errors": sum(r["errors"] for r in main),
+        "error_kinds": main[-1]["error_kinds"],
+        "streams": main,
+        "fp64_same_stream": ({"value": sum(r["evaluations"] for r in passes["fp64"]) /
+                              sum(r["wall_s"] for r in passes["fp64"]),
+                              "p50_s": passes["fp64"][-1]["p50_s"], "p99_s": passes["fp64"][-1]["p99_s"],
+                              "errors": sum(r["errors"] for r in passes["fp64"]), "streams": passes["fp64"]}
+                             if "fp64" in passes else None),
         "e2e": {"value": evals * ws / wall, "unit": "points/s",
                 "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "the stream itself is end to end: host points and densities in, host results out"},
@@ -738,6 +768,90 @@ def run_serve(args):
         "gpu_launches": None,
         "clocks": clk,
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_wobble(args):
+    """--workload wobble: the paper's own test interfaces (Sec. 7.1, Eqs.
+    wobble_2D_cplx and complex_wobble), single layer, N = 1e6 each: 2D and 3D
+    Laplace and Helmholtz (kappa = 2 pi), FP64 at eps = 1e-6 and 1e-12 (the
+    paper's two accuracies) and MIXED at 1e-6; one plan+apply pass per step,
+    accuracy against the library's FP64 direct sum on 200 sampled targets.
+    value = all cases' points over their summed plan+apply times."""
+    import numpy as np
+    import torch
+
+    import paper_2509_05458_gb300 as cf
+    from cfmm_inputs import wobble2d, wobble3d, densities
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    n = args.n or 1_000_000
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cases = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    tot_pts, tot_ms = 0, 0.0
+    for dim in (2, 3):
+        g = wobble2d(n, seed=0) if dim == 2 else wobble3d(n)
+        re, im = torch.from_numpy(g.re).to(dev), torch.from_numpy(g.im).to(dev)
+        dens = torch.from_numpy(densities(g.n, seed=1)).to(dev)
+        out = torch.empty((1, g.n), dtype=torch.complex128, device=dev)
+        idx = torch.from_numpy(np.sort(np.random.default_rng(1).choice(g.n, 200, replace=False))).to(dev)
+        for ker in (cf.LAPLACE, cf.HELMHOLTZ):
+            kap = 2 * np.pi if ker == cf.HELMHOLTZ else 0.0
+            ref = cf.direct(dim, ker | cf.SLP, kap, re, im, re[idx].contiguous(), im[idx].contiguous(), dens,
+                            stream=stream).cpu().numpy()[0]
+            for eps, prec in ((1e-6, cf.FP64), (1e-6, cf.MIXED), (1e-12, cf.FP64)):
+                sep = 2 if dim == 3 else 1
+                case = {"dim": dim, "kernel": "helmholtz" if ker else "laplace", "kappa": kap, "eps": eps,
+                        "precision": "MIXED" if prec == cf.MIXED else "FP64", "sep": sep, "n": g.n}
+
+                def step():
+                    p = cf.plan(dim, ker | cf.SLP, kap, eps, re, im, leaf_size=64, sep=sep, stream=stream,
+                                precision=prec)
+                    p.apply(dens, out=out)
+                    p.destroy()
+                try:
+                    for _ in range(max(1, args.warmup)):
+                        step()
+                    ms = []
+                    for _ in range(max(1, min(args.steps, 5))):
+                        flush.zero_()
+                        ev0.record(stream)
+                        step()
+                        ev1.record(stream)
+                        ev1.synchronize()
+                        ms.append(ev0.elapsed_time(ev1))
+                except cf.CfmmError as e:
+                    case["unsupported"] = str(e)
+                    cases.append(case)
+                    continue
+                m = statistics.median(ms)
+                u = out[0][idx].cpu().numpy()
+                case.update({"ms": m, "points_per_s": g.n / (m / 1e3),
+                             "rel_l2_vs_fp64_direct_200_targets": float(np.linalg.norm(u - ref) / np.linalg.norm(ref))})
+                tot_pts += g.n
+                tot_ms += m
+                cases.append(case)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    line = {"metric": "complex-FMM pts/s on the paper's wobbly interfaces (Sec. 7.1), single layer",
+            "value": tot_pts * ws / (tot_ms / 1e3), "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 / f32+f64", "data": "synthetic",
+            "config": {"workload": "wobble_2D_cplx (t uniform in [-20,20]) and complex_wobble ((t1,t2) Halton in "
+                                   "[-25,25]^2), N = %d each, SLP, leaf 64, sep 1 (2D) / 2 (3D)" % n,
+                       "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) before every timed step"},
+            "cases": cases, "clocks": clk, "roofline": None, "gpu_launches": None,
+            "e2e": None}
     print(json.dumps(line), flush=True)
 
 
@@ -901,7 +1015,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the 3D Laplace and 2D lines of the default run")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which passes to run (the headline needs both)")
-    ap.add_argument("--workload", default="helm3d", choices=["helm3d", "lap3d", "helm2d", "batch3d", "serve"],
+    ap.add_argument("--workload", default="helm3d",
+                    choices=["helm3d", "lap3d", "helm2d", "batch3d", "serve", "wobble"],
                     help="helm3d: the 3D Helmholtz surface headline (with the 3D Laplace and 2D lines); lap3d / "
                          "helm2d: those alone; batch3d: the batched 3D Helmholtz line; serve: the serving loop")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests per stream")
@@ -930,6 +1045,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "wobble":
+        run_wobble(args)
     else:
         run_gpu(args)
 

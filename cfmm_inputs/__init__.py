@@ -18,13 +18,22 @@ external packages):
   square, z = a*exp(-(x^2+y^2)/w^2), imaginary part
   s*max(rho-rho0, 0)*(x, y)/rho in (x1, x2) and 0 in x3.
 * ``densities``: i.i.d. complex Gaussians (real and imaginary N(0,1)).
+* ``wobble2d`` / ``wobble3d``: the paper's own test interfaces of Sec. 7.1
+  (Eqs. wobble_2D_cplx and complex_wobble) with the deformation psi_{a,b,t0}
+  built from xi (readings: xi(s) = (s erfc(s) - e^{-s^2}/sqrt(pi))/2, so that
+  xi' = erfc/2; psi(t) = a (xi(b (t + t0)) - xi(b (t0 - t))), odd, flat on
+  |t| < t0 and of slope a b beyond; the 2D bump's window is
+  (erfc(2 (t - 6)) - erfc(2 (t + 6)))/2, one on [-6, 6] and zero outside).
+  The paper discretises them with ChunkIE panels / a corrected trapezoidal
+  rule and samples points; here t is uniform on [-20, 20] (2D, the range is
+  not stated) and (t1, t2) are Halton points of [-25, 25]^2 (3D).
 """
 from __future__ import annotations
 
 import numpy as np
 
 __all__ = ["curve2d", "surface3d", "densities", "halton", "Geometry",
-           "curve2d_short", "curve2d_long", "plane3d", "plane3d_uneven"]
+           "curve2d_short", "curve2d_long", "plane3d", "plane3d_uneven", "wobble2d", "wobble3d", "psi_abt"]
 
 
 class Geometry:
@@ -154,3 +163,45 @@ def plane3d_uneven(count=32, seed0=100, nmin=10_000, nmax=200_000):
     ns = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=count))
     return [surface3d(int(round(n)), seed=seed0 + 1 + i, half=20.0, amp=0.5, rho0=6.0, random_shape=True)
             for i, n in enumerate(ns)]
+
+
+# ---- the paper's test interfaces (Sec. 7.1) ---------------------------------
+
+def _xi(s):
+    from scipy.special import erfc
+    return 0.5 * (s * erfc(s) - np.exp(-s * s) / np.sqrt(np.pi))
+
+
+def psi_abt(t, a, b, t0):
+    """psi_{a,b,t0}(t) = a (xi(b (t + t0)) - xi(b (t0 - t))) (see the module
+    docstring for the reading of the printed formula)."""
+    t = np.asarray(t, dtype=np.float64)
+    return a * (_xi(b * (t + t0)) - _xi(b * (t0 - t)))
+
+
+def wobble2d(n, seed=0, t_half=20.0, a=1.0 / 20.0, b=3.0, t0=13.0):
+    """Eq. wobble_2D_cplx: (t + i psi(t), 2 e^{-t^2/16} cos(8t) w(t)), t uniform
+    on [-t_half, t_half], w the window of the module docstring. No normals (the
+    paper's timings are single-layer)."""
+    from scipy.special import erfc
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = rng.uniform(-t_half, t_half, size=n)
+    w = 0.5 * (erfc(2.0 * (t - 6.0)) - erfc(2.0 * (t + 6.0)))
+    re = np.stack([t, 2.0 * np.exp(-t * t / 16.0) * np.cos(8.0 * t) * w], axis=1)
+    im = np.stack([psi_abt(t, a, b, t0), np.zeros_like(t)], axis=1)
+    return Geometry(re, im, meta=dict(family="wobble2d", n=n, seed=seed, a=a, b=b, t0=t0))
+
+
+def wobble3d(n, half=25.0, a=0.2, b=0.75, t0=12.0):
+    """Eq. complex_wobble: (u + i psi(u), v + i psi(v), e^{-(u^2+v^2)/8}
+    (cos(1.9u + 0.95v) + sin(u + 1.55v))) with u = t1 (1 - e^{-(t1^2+t2^2)/300}/2),
+    v likewise, (t1, t2) the Halton points (bases 2, 3) of [-half, half]^2."""
+    t1 = (2.0 * halton(n, 2) - 1.0) * half
+    t2 = (2.0 * halton(n, 3) - 1.0) * half
+    e = np.exp(-(t1 * t1 + t2 * t2) / 300.0)
+    u = t1 - 0.5 * t1 * e
+    v = t2 - 0.5 * t2 * e
+    z = np.exp(-(u * u + v * v) / 8.0) * (np.cos(1.9 * u + 0.95 * v) + np.sin(u + 1.55 * v))
+    re = np.stack([u, v, z], axis=1)
+    im = np.stack([psi_abt(u, a, b, t0), psi_abt(v, a, b, t0), np.zeros_like(u)], axis=1)
+    return Geometry(re, im, meta=dict(family="wobble3d", n=n, a=a, b=b, t0=t0))

@@ -113,6 +113,26 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps,
                          int64_t n, const cfmm_opts* opts);
 
 /*
+ * cfmm_plan_targets: a plan that evaluates the potential of m sources at n
+ * separate targets (Sec. 2.3 Eq. evaluation_problem with distinct x_i and
+ * y_j; the targets may carry their own imaginary parts, the "two different
+ * functions psi" of the remark after Lemma 4.1.1, and the Lipschitz condition
+ * then holds for both). The tree, centres, lists and orders are built on the
+ * m + n points together (sources first); the targets enter the expansions
+ * with zero density, and a source that coincides with a target is skipped
+ * for it, as in the direct sum.
+ *   src_re/src_im [m][dim], nrm_re/nrm_im [m][dim] (source normals; NULL
+ *   without CFMM_DLP), trg_re/trg_im [n][dim], float64, host or device.
+ * cfmm_apply on such a plan takes densities [nrhs][ncomp][m] and writes out
+ * [nrhs][n] (the targets, in the caller's order). Returns NULL on failure.
+ */
+cfmm_plan_t cfmm_plan_targets(int dim, int kernel, double k, double eps,
+                              const double* src_re, const double* src_im,
+                              const double* nrm_re, const double* nrm_im, int64_t m,
+                              const double* trg_re, const double* trg_im, int64_t n,
+                              const cfmm_opts* opts);
+
+/*
  * cfmm_apply: one FMM pass (the eight steps of Sec. 6.4) for nrhs
  * right-hand sides. densities: [nrhs][ncomp][n] complex128; out: [nrhs][n]
  * complex128 (overwritten). Host or device pointers. Asynchronous on the
@@ -212,7 +232,7 @@ typedef struct cfmm_plan_info {
     int nboxes;
     int nleaves;
     int l0;             /* top expansion level                               */
-    int64_t n;
+    int64_t n;          /* points of the tree (sources + separate targets)   */
     int64_t list_len[4];/* total entries of Lists 1..4                        */
     int64_t p2p_pairs;  /* sum over leaves of n_target * n_source over List 1 */
     int64_t m2l_pairs;  /* List 2 entries at levels >= l0                     */
@@ -223,6 +243,8 @@ typedef struct cfmm_plan_info {
                         /* pairs at most 32 apart in Morton order of        */
                         /* |Im(x_i - x_j)| / |Re(x_i - x_j)|; the plan      */
                         /* fails with CFMM_EGEOM when it reaches 1          */
+    int64_t n_src;      /* sources (n_src = n without separate targets)      */
+    int64_t n_trg;      /* separate targets (0: the targets are the sources) */
 } cfmm_plan_info;
 
 /* cfmm_plan_get_info: fills *info. */

@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = ["LAPLACE", "HELMHOLTZ", "SLP", "DLP", "GREEN_SCALE", "FP64", "MIXED", "AUTO",
-           "Plan", "plan", "Batch", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
+           "Plan", "plan", "plan_targets", "Batch", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
 
 LAPLACE, HELMHOLTZ = 0, 1
 SLP, DLP, GREEN_SCALE = 1 << 4, 1 << 5, 1 << 6
@@ -45,7 +45,7 @@ class _Info(C.Structure):
                 ("precision", C.c_int), ("nlevels", C.c_int), ("nboxes", C.c_int), ("nleaves", C.c_int),
                 ("l0", C.c_int), ("n", C.c_int64), ("list_len", C.c_int64 * 4), ("p2p_pairs", C.c_int64),
                 ("m2l_pairs", C.c_int64), ("root_lo", C.c_double * 3), ("root_width", C.c_double),
-                ("lipschitz", C.c_double)]
+                ("lipschitz", C.c_double), ("n_src", C.c_int64), ("n_trg", C.c_int64)]
 
 
 _lib = None
@@ -65,6 +65,8 @@ def lib():
     L.cfmm_plan.argtypes = [ci, ci, dbl, dbl, vp, vp, i64]
     L.cfmm_plan_ex.restype = vp
     L.cfmm_plan_ex.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, C.POINTER(_Opts)]
+    L.cfmm_plan_targets.restype = vp
+    L.cfmm_plan_targets.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, vp, vp, i64, C.POINTER(_Opts)]
     L.cfmm_apply.restype = ci
     L.cfmm_apply.argtypes = [vp, vp, ci, vp]
     L.cfmm_apply_capture.restype = ci
@@ -153,11 +155,13 @@ def _stream_ptr(stream):
 class Plan:
     """A resident plan: sorted points, tree, lists and translation tables on the GPU."""
 
-    def __init__(self, handle, dim, ncomp, n, keep):
+    def __init__(self, handle, dim, ncomp, n, keep, nsrc=None, nout=None):
         self._h = handle
         self.dim = dim
         self.ncomp = ncomp
-        self.n = n
+        self.n = n                                 # points of the tree
+        self.nsrc = n if nsrc is None else nsrc    # densities per component
+        self.nout = n if nout is None else nout    # outputs (the separate targets, if any)
         self._keep = keep
 
     def __del__(self):
@@ -176,8 +180,9 @@ class Plan:
         return self._h
 
     def apply(self, densities, out=None):
-        """densities: complex128 [nrhs, ncomp, n] (or [n] / [nrhs, n] when ncomp == 1),
-        torch (CUDA or CPU) or numpy. Returns complex128 [nrhs, n] of the same kind."""
+        """densities: complex128 [nrhs, ncomp, nsrc] (or [nsrc] / [nrhs, nsrc] when
+        ncomp == 1), torch (CUDA or CPU) or numpy. Returns complex128 [nrhs, nout]
+        of the same kind (nsrc = nout = n without separate targets)."""
         d = densities
         is_torch = hasattr(d, "data_ptr")
         if is_torch:
@@ -189,7 +194,7 @@ class Plan:
             d = d.to(torch.complex128).contiguous()
             nrhs = d.shape[0]
             if out is None:
-                out = torch.empty((nrhs, self.n), dtype=torch.complex128, device=d.device)
+                out = torch.empty((nrhs, self.nout), dtype=torch.complex128, device=d.device)
         else:
             d = np.asarray(d, dtype=np.complex128)
             if d.ndim == 1:
@@ -199,9 +204,9 @@ class Plan:
             d = np.ascontiguousarray(d)
             nrhs = d.shape[0]
             if out is None:
-                out = np.empty((nrhs, self.n), dtype=np.complex128)
-        if d.shape[1] != self.ncomp or d.shape[2] != self.n:
-            raise ValueError(f"densities must be [nrhs, {self.ncomp}, {self.n}]")
+                out = np.empty((nrhs, self.nout), dtype=np.complex128)
+        if d.shape[1] != self.ncomp or d.shape[2] != self.nsrc:
+            raise ValueError(f"densities must be [nrhs, {self.ncomp}, {self.nsrc}]")
         _check(lib().cfmm_apply(self._h, _ptr(d), nrhs, _ptr(out)))
         return out
 
@@ -225,7 +230,7 @@ class Plan:
                 "nleaves": inf.nleaves, "l0": inf.l0, "n": inf.n, "list_len": list(inf.list_len),
                 "p2p_pairs": inf.p2p_pairs, "m2l_pairs": inf.m2l_pairs,
                 "root_lo": list(inf.root_lo)[: inf.dim], "root_width": inf.root_width,
-                "lipschitz": inf.lipschitz}
+                "lipschitz": inf.lipschitz, "n_src": inf.n_src, "n_trg": inf.n_trg}
 
     def orders(self):
         nl = self.info()["nlevels"]
@@ -327,6 +332,25 @@ def plan(dim, kernel, k, eps, pts_re, pts_im, nrm_re=None, nrm_im=None, leaf_siz
     dlp = bool(kernel & DLP)
     slp = bool(kernel & SLP) or not dlp
     return Plan(h, dim, int(slp) + int(dlp), n, (re, im, nre, nim))
+
+
+def plan_targets(dim, kernel, k, eps, src_re, src_im, trg_re, trg_im, nrm_re=None, nrm_im=None, leaf_size=64,
+                 sep=1, precision=FP64, top_level=0, stream=None):
+    """cfmm_plan_targets: the potential of the sources at separate targets (their
+    own imaginary parts allowed). apply() takes densities [nrhs, ncomp, m] and
+    returns [nrhs, n_targets]."""
+    re, im = _as_f64(src_re), _as_f64(src_im)
+    tre, tim = _as_f64(trg_re), _as_f64(trg_im)
+    nre, nim = _as_f64(nrm_re), _as_f64(nrm_im)
+    m, n = int(re.shape[0]), int(tre.shape[0])
+    opts = _Opts(int(leaf_size), int(sep), int(precision), int(top_level), _stream_ptr(stream))
+    h = lib().cfmm_plan_targets(int(dim), int(kernel), float(k), float(eps), _ptr(re), _ptr(im), _ptr(nre),
+                                _ptr(nim), m, _ptr(tre), _ptr(tim), n, C.byref(opts))
+    if not h:
+        _check(lib().cfmm_last_status() or -5)
+    dlp = bool(kernel & DLP)
+    slp = bool(kernel & SLP) or not dlp
+    return Plan(h, dim, int(slp) + int(dlp), m + n, (re, im, tre, tim, nre, nim), nsrc=m, nout=n)
 
 
 def direct(dim, kernel, k, src_re, src_im, trg_re, trg_im, densities, nrm_re=None, nrm_im=None,

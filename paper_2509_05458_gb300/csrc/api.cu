@@ -312,21 +312,27 @@ static int guarded(F f) {
 }
 
 // ---- apply-path helpers (permutation of densities and results) -----------
-__global__ void k_permute_dens(const cd* __restrict__ dens, const int* __restrict__ perm, int64_t n, int nrhs,
-                               int ncomp, int comp, cd* __restrict__ out) {
+// densities [nrhs][ncomp][nsrc] in the caller's order -> sorted [nrhs][n];
+// union points beyond the sources (separate targets) carry zero density
+__global__ void k_permute_dens(const cd* __restrict__ dens, const int* __restrict__ perm, int64_t n, int64_t nsrc,
+                               int nrhs, int ncomp, int comp, cd* __restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (i >= n) return;
-    out[(int64_t)r * n + i] = dens[((int64_t)r * ncomp + comp) * n + perm[i]];
+    int64_t j = perm[i];
+    out[(int64_t)r * n + i] = j < nsrc ? dens[((int64_t)r * ncomp + comp) * nsrc + j] : cd{0.0, 0.0};
 }
 
-__global__ void k_unpermute(const cd* __restrict__ us, const int* __restrict__ perm, int64_t n, cd scale,
-                            cd* __restrict__ out) {
+// sorted [nrhs][n] -> the caller's [nrhs][nout] at union indices [first, first + nout)
+__global__ void k_unpermute(const cd* __restrict__ us, const int* __restrict__ perm, int64_t n, int64_t first,
+                            int64_t nout, cd scale, cd* __restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (i >= n) return;
+    int64_t j = (int64_t)perm[i] - first;
+    if (j < 0 || j >= nout) return;
     cd v = us[(int64_t)r * n + i];
-    out[(int64_t)r * n + perm[i]] = v * scale;
+    out[(int64_t)r * nout + j] = v * scale;
 }
 
 static void record(cfmm_plan_s* P, int i) {
@@ -375,11 +381,11 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     dim3 g((unsigned)((n + 255) / 256), nrhs);
     int comp = 0;
     if (P->slp) {
-        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, nrhs, ncomp, comp++, sg);
+        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, P->n_src, nrhs, ncomp, comp++, sg);
         CFMM_LAUNCHED();
     }
     if (P->dlp) {
-        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, nrhs, ncomp, comp++, ta);
+        k_permute_dens<<<g, 256, 0, st>>>(dens, P->perm.get(), n, P->n_src, nrhs, ncomp, comp++, ta);
         CFMM_LAUNCHED();
     }
     record(P, 1);
@@ -388,7 +394,8 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
     else fmm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
     record(P, 8);
     cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
-    k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, scale, out);
+    int64_t first = P->n_trg > 0 ? P->n_src : 0, nout = P->n_trg > 0 ? P->n_trg : n;
+    k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, first, nout, scale, out);
     CFMM_LAUNCHED();
     record(P, 9);
     if (P->timing) {
@@ -470,8 +477,11 @@ int cfmm_debug_fail_allocs(int count) {
     });
 }
 
-cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
-                         const double* nrm_re, const double* nrm_im, int64_t n, const cfmm_opts* opts) {
+// cfmm_plan_ex and cfmm_plan_targets: sources [0, m) and (when n > 0) separate
+// targets [m, m + n) of the tree's points
+static cfmm_plan_t plan_common(int dim, int kernel, double k, double eps, const double* src_re,
+                               const double* src_im, const double* nrm_re, const double* nrm_im, int64_t m,
+                               const double* trg_re, const double* trg_im, int64_t ntrg, const cfmm_opts* opts) {
     cfmm_plan_s* P = nullptr;
     int rc = guarded([&] {
         CFMM_REQUIRE(dim == 2 || dim == 3, CFMM_EINVAL, "dim must be 2 or 3");
@@ -480,8 +490,10 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         CFMM_REQUIRE((kernel & ~(0xF | CFMM_SLP | CFMM_DLP | CFMM_GREEN_SCALE)) == 0, CFMM_EINVAL, "unknown kernel flags");
         CFMM_REQUIRE(ker == CFMM_LAPLACE || (std::isfinite(k) && k > 0.0), CFMM_EINVAL, "Helmholtz needs k > 0");
         CFMM_REQUIRE(std::isfinite(eps) && eps >= 1e-15 && eps <= 0.1, CFMM_EINVAL, "eps must be in [1e-15, 0.1]");
-        CFMM_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), CFMM_EINVAL, "n must be in [1, 2^31)");
-        CFMM_REQUIRE(pts_re && pts_im, CFMM_EINVAL, "points are required");
+        CFMM_REQUIRE(m >= 1 && ntrg >= 0 && m + ntrg < ((int64_t)1 << 31), CFMM_EINVAL,
+                     "point counts must be >= 1 (sources), >= 0 (targets), below 2^31 in total");
+        CFMM_REQUIRE(src_re && src_im, CFMM_EINVAL, "points are required");
+        CFMM_REQUIRE(ntrg == 0 || (trg_re && trg_im), CFMM_EINVAL, "target points are required");
         bool dlp = (kernel & CFMM_DLP) != 0;
         bool slp = (kernel & CFMM_SLP) != 0 || !dlp;
         CFMM_REQUIRE(!dlp || (nrm_re && nrm_im), CFMM_EINVAL, "double layer needs normals");
@@ -494,6 +506,7 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         CFMM_REQUIRE(leaf <= 4096, CFMM_EINVAL, "leaf_size must be <= 4096");
         CFMM_REQUIRE(sep <= 3, CFMM_EINVAL, "sep must be 1, 2 or 3 (or < 0 for automatic)");
         CFMM_REQUIRE(o.precision >= 0 && o.precision <= 2, CFMM_EINVAL, "bad precision mode");
+        int64_t n = m + ntrg;
         P = new cfmm_plan_s();
         P->dim = dim;
         P->kernel = ker;
@@ -504,6 +517,8 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         P->kappa = ker == CFMM_HELMHOLTZ ? k : 0.0;
         P->eps = eps;
         P->n = n;
+        P->n_src = m;
+        P->n_trg = ntrg;
         P->leaf_size = leaf;
         P->sep = sep;
         P->precision = o.precision == CFMM_AUTO ? (eps >= 1e-5 ? CFMM_MIXED : CFMM_FP64) : o.precision;
@@ -518,11 +533,29 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
         Scratch& scr = plan_scratch();
         scr.rewind();
         plan_host_stage().rewind();
-        size_t cnt = (size_t)n * dim;
-        const double* re = stage_in(pts_re, cnt, P->stream);
-        const double* im = stage_in(pts_im, cnt, P->stream);
-        const double* nre = dlp ? stage_in(nrm_re, cnt, P->stream) : nullptr;
-        const double* nim = dlp ? stage_in(nrm_im, cnt, P->stream) : nullptr;
+        size_t cs = (size_t)m * dim, ct = (size_t)ntrg * dim;
+        const double *re, *im, *nre = nullptr, *nim = nullptr;
+        if (ntrg == 0) {
+            re = stage_in(src_re, cs, P->stream);
+            im = stage_in(src_im, cs, P->stream);
+            nre = dlp ? stage_in(nrm_re, cs, P->stream) : nullptr;
+            nim = dlp ? stage_in(nrm_im, cs, P->stream) : nullptr;
+        } else {
+            // the tree's points: sources then targets (targets get zero normals)
+            auto cat = [&](const double* a, const double* b) {
+                double* d = scr.take_n<double>(cs + ct);
+                CFMM_CUDA(cudaMemcpyAsync(d, a, cs * sizeof(double), cudaMemcpyDefault, P->stream));
+                if (b) CFMM_CUDA(cudaMemcpyAsync(d + cs, b, ct * sizeof(double), cudaMemcpyDefault, P->stream));
+                else CFMM_CUDA(cudaMemsetAsync(d + cs, 0, ct * sizeof(double), P->stream));
+                return (const double*)d;
+            };
+            re = cat(src_re, trg_re);
+            im = cat(src_im, trg_im);
+            if (dlp) {
+                nre = cat(nrm_re, nullptr);
+                nim = cat(nrm_im, nullptr);
+            }
+        }
         build_tree(P, re, im, nre, nim, o.top_level);
         if (dim == 2) fmm2d_presetup(P);   // its row table overlaps the lists
         build_plan_lists(P);
@@ -540,6 +573,25 @@ cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double
     return P;
 }
 
+cfmm_plan_t cfmm_plan_ex(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
+                         const double* nrm_re, const double* nrm_im, int64_t n, const cfmm_opts* opts) {
+    if (n < 1) {
+        guarded([&] { CFMM_REQUIRE(false, CFMM_EINVAL, "n must be in [1, 2^31)"); });
+        return nullptr;
+    }
+    return plan_common(dim, kernel, k, eps, pts_re, pts_im, nrm_re, nrm_im, n, nullptr, nullptr, 0, opts);
+}
+
+cfmm_plan_t cfmm_plan_targets(int dim, int kernel, double k, double eps, const double* src_re, const double* src_im,
+                              const double* nrm_re, const double* nrm_im, int64_t m, const double* trg_re,
+                              const double* trg_im, int64_t n, const cfmm_opts* opts) {
+    if (n < 1) {
+        guarded([&] { CFMM_REQUIRE(false, CFMM_EINVAL, "the target count must be >= 1"); });
+        return nullptr;
+    }
+    return plan_common(dim, kernel, k, eps, src_re, src_im, nrm_re, nrm_im, m, trg_re, trg_im, n, opts);
+}
+
 cfmm_plan_t cfmm_plan(int dim, int kernel, double k, double eps, const double* pts_re, const double* pts_im,
                       int64_t n) {
     return cfmm_plan_ex(dim, kernel, k, eps, pts_re, pts_im, nullptr, nullptr, n, nullptr);
@@ -551,7 +603,8 @@ int cfmm_apply(cfmm_plan_t P, const double* densities, int nrhs, double* out) {
         CFMM_REQUIRE(nrhs >= 1, CFMM_EINVAL, "nrhs must be >= 1");
         CFMM_REQUIRE(densities && out, CFMM_EINVAL, "densities and out are required");
         int ncomp = (P->slp ? 1 : 0) + (P->dlp ? 1 : 0);
-        size_t din = (size_t)nrhs * ncomp * P->n * 2, dout = (size_t)nrhs * P->n * 2;
+        int64_t nout = P->n_trg > 0 ? P->n_trg : P->n;
+        size_t din = (size_t)nrhs * ncomp * P->n_src * 2, dout = (size_t)nrhs * nout * 2;
         bool dev_in = is_device_ptr(densities), dev_out = is_device_ptr(out);
         const cd* d_in = reinterpret_cast<const cd*>(densities);
         cd* d_out = reinterpret_cast<cd*>(out);
@@ -782,6 +835,8 @@ int cfmm_plan_get_info(cfmm_plan_t P, cfmm_plan_info* info) {
         info->nleaves = P->tree.nleaves;
         info->l0 = P->tree.l0;
         info->n = P->n;
+        info->n_src = P->n_src;
+        info->n_trg = P->n_trg;
         for (int w = 0; w < 4; ++w) info->list_len[w] = P->tree.llen[w];
         info->p2p_pairs = P->p2p_pairs;
         info->m2l_pairs = P->m2l_pairs;

@@ -286,7 +286,9 @@ struct cfmm_plan_s {
     int dim = 2, kernel = 0, flags = 0, sep = 1, leaf_size = 64, precision = 0;
     bool slp = true, dlp = false, green = false;
     double kappa = 0.0, eps = 1e-6;
-    int64_t n = 0;
+    int64_t n = 0;                   // points of the tree (sources + separate targets)
+    int64_t n_src = 0;               // caller's sources: union indices [0, n_src)
+    int64_t n_trg = 0;               // separate targets: union indices [n_src, n); 0 = targets are the sources
     cudaStream_t stream = nullptr;
     int device = 0;
     double lo[3] = {0, 0, 0};

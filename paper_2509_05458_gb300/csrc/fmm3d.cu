@@ -424,10 +424,14 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
                T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
     near_launched(P);
-    // (1) P2M (single layer: one lane per harmonic column)
-    if (!(P->slp && !P->dlp &&
-          lap3_p2m_slp(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
-                       S->exp_off.get(), S->ncoef, sigma, dstride, mp, nrhs))) {
+    // (1) P2M (single layer: one lane per harmonic column; complex64 products
+    // with FP64 sums in mixed precision)
+    bool slp1 = P->slp && !P->dlp;
+    bool p2m_done = slp1 && mixed &&
+                    lap3_p2m32(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
+                               S->exp_off.get(), S->ncoef, sigma, dstride, mp, nrhs);
+    if (!p2m_done && !(slp1 && lap3_p2m_slp(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP,
+                                            S->dPlev.get(), S->exp_off.get(), S->ncoef, sigma, dstride, mp, nrhs))) {
         int chunk;
         size_t smem = p2x_smem(maxP, chunk);
         dim3 g((unsigned)S->leaves_l0.size(), nrhs);

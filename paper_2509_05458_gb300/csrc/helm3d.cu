@@ -745,6 +745,33 @@ struct L2p3fArgs {
     const double* lsd;   // Laplace: e_m / s_n^m by nmi(n, m)
 };
 
+// jh_n(z) = j_n(z) (2n+1)!!/z^n, n = 0..P, in complex64 from w = z^2 (see
+// the comment above k_l2p3f): ratios by Miller's backward recurrence from 1,
+// jh_0 from the plane-wave normalisation.
+__device__ __forceinline__ void jhat_seq(cf w, int P, cf* G) {
+    cf zz = csqrtf_p(w);
+    float big = fmaxf((float)P, hypotf(zz.x, zz.y));
+    int N = (int)big + 12 + (int)sqrtf(8.f * big);
+    bool up = zz.y >= 0.f;                           // exp(-i z), |.| >= 1
+    cf a = up ? cf{zz.y, -zz.x} : cf{-zz.y, zz.x};   // -+ i z
+    cf q = {1.f, 0.f}, H = {1.f, 0.f};
+    for (int nn = N; nn >= 1; --nn) {
+        float den = 1.f / ((2.f * nn + 1.f) * (2.f * nn + 3.f));
+        q = cinvf(cf{1.f, 0.f} - (den * w) * q);
+        if (nn <= P) G[nn] = q;
+        H = cf{1.f, 0.f} + (1.f / (2.f * nn - 1.f)) * (a * (q * H));
+    }
+    // jh_0 = exp(a) / H
+    float ex = expf(a.x), sn, cs;
+    sincosf(a.y, &sn, &cs);
+    cf g = cf{ex * cs, ex * sn} * cinvf(H);
+    G[0] = g;
+    for (int nn = 1; nn <= P; ++nn) {
+        g = g * G[nn];
+        G[nn] = g;
+    }
+}
+
 template <bool HELM>
 __global__ void __launch_bounds__(128) k_l2p3f(L2p3fArgs A, const int* __restrict__ leaves,
                                                 const cd* __restrict__ loc, cd* __restrict__ u) {
@@ -787,28 +814,7 @@ __global__ void __launch_bounds__(128) k_l2p3f(L2p3fArgs A, const int* __restric
         if (HELM) {
             // w = (k rho)^2 = (k rho_b)^2 x~.x~
             float kr = (float)(A.kappa * rb);
-            cf w = (kr * kr) * r2;
-            cf zz = csqrtf_p(w);
-            float big = fmaxf((float)P, hypotf(zz.x, zz.y));
-            int N = (int)big + 12 + (int)sqrtf(8.f * big);
-            bool up = zz.y >= 0.f;                       // exp(-i z), |.| >= 1
-            cf a = up ? cf{zz.y, -zz.x} : cf{-zz.y, zz.x};   // -+ i z
-            cf q = {1.f, 0.f}, H = {1.f, 0.f};
-            for (int nn = N; nn >= 1; --nn) {
-                float den = 1.f / ((2.f * nn + 1.f) * (2.f * nn + 3.f));
-                q = cinvf(cf{1.f, 0.f} - (den * w) * q);
-                if (nn <= P) G[nn] = q;
-                H = cf{1.f, 0.f} + (1.f / (2.f * nn - 1.f)) * (a * (q * H));
-            }
-            // jh_0 = exp(a) / H
-            float ex = expf(a.x), sn, cs;
-            sincosf(a.y, &sn, &cs);
-            cf g = cf{ex * cs, ex * sn} * cinvf(H);
-            G[0] = g;
-            for (int nn = 1; nn <= P; ++nn) {
-                g = g * G[nn];
-                G[nn] = g;
-            }
+            jhat_seq((kr * kr) * r2, P, G);
         }
         Kahan acc;
         for (int sgn = 0; sgn < 2; ++sgn) {
@@ -835,6 +841,137 @@ __global__ void __launch_bounds__(128) k_l2p3f(L2p3fArgs A, const int* __restric
         }
         u[(int64_t)rhs * A.n + i] += acc.value();
     }
+}
+
+// Single-layer P2M in complex64 products (mixed precision), 3D Helmholtz and
+// Laplace. With y~ = (y - c)/rho_b,
+//   Helmholtz  M_n^m = i k (2n+1) (k rho_b)^n/(2n+1)!! sum s jh_n(k rho) Z_n^{-m}(y~)
+//   Laplace    M_n^m = lsd_n^m rho_b^n sum s Z_n^{-m}(y~)
+// (the forms of k_p2x3h_slp rewritten as in k_l2p3f). Each warp stages 32
+// sources (their jh table, x+, x-, x3 and density) and then takes (source,
+// harmonic column) items in rounds of 32, one per lane; a column owns the
+// coefficients (n, -mu), n >= |mu|, so with 2P+1 >= 32 columns the lanes of a
+// round write disjoint coefficients (fewer columns: one source at a time, a
+// lane per column). Products are complex64 and each warp's accumulator row is
+// a compensated (Kahan) complex64 sum; the rows are summed in warp order in
+// FP64 and scaled in FP64.
+constexpr int kP2m3fWarps = 4;
+
+template <bool HELM>
+__global__ void __launch_bounds__(kP2m3fWarps * 32) k_p2m3f(L2p3fArgs A, const int* __restrict__ boxes,
+                                                             const cd* __restrict__ sigma, int64_t dstride,
+                                                             cd* __restrict__ out) {
+    extern __shared__ unsigned char smraw[];
+    int b = boxes[blockIdx.x];
+    int rhs = blockIdx.y;
+    int lev = A.blevel[b];
+    int P = A.Plev[lev];
+    int nc = (P + 1) * (P + 1), C = 2 * P + 1;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* acc = reinterpret_cast<float4*>(smraw);                         // [nwarp][nc]: sum, compensation
+    cf* Gs = reinterpret_cast<cf*>(acc + (size_t)kP2m3fWarps * nc);         // [nwarp][32][P+1]
+    cf* Ys = Gs + (size_t)kP2m3fWarps * 32 * (P + 1);                       // [nwarp][32][4]
+    float4* accw = acc + (size_t)wid * nc;
+    cf* Gw = Gs + (size_t)wid * 32 * (P + 1);
+    cf* Yw = Ys + (size_t)wid * 32 * 4;
+    for (int c = lane; c < nc; c += 32) accw[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto kadd = [&](int k, cf t) {
+        float4 a = accw[k];
+        float yx = t.x - a.z, tx = a.x + yx;
+        float yy = t.y - a.w, ty = a.y + yy;
+        accw[k] = make_float4(tx, ty, (tx - a.x) - yx, (ty - a.y) - yy);
+    };
+    double rb = 0.86602540378443864676 * ldexp(A.W, -lev), irb = 1.0 / rb;
+    cd cen[3];
+    for (int a = 0; a < 3; ++a) cen[a] = cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+    float kr = (float)(A.kappa * rb);
+    int s0 = A.bst[b], s1 = A.ben[b];
+    for (int base = s0 + wid * 32; base < s1; base += kP2m3fWarps * 32) {
+        int cnt = min(32, s1 - base);
+        __syncwarp();
+        if (lane < cnt) {
+            int j = base + lane;
+            cf y[3];
+            for (int a = 0; a < 3; ++a) y[a] = to_cf(irb * (cd{A.xr[a * A.n + j], A.xi[a * A.n + j]} - cen[a]));
+            cf xp = y[0] + mul_if(y[1]), xm = y[0] - mul_if(y[1]);
+            Yw[lane * 4 + 0] = xp;
+            Yw[lane * 4 + 1] = xm;
+            Yw[lane * 4 + 2] = y[2];
+            Yw[lane * 4 + 3] = to_cf(sigma[rhs * dstride + j]);
+            if (HELM) jhat_seq((kr * kr) * (xp * xm + y[2] * y[2]), P, Gw + lane * (P + 1));
+        }
+        __syncwarp();
+        int items = cnt * C;
+        int step = C >= 32 ? 32 : C;
+        for (int r0 = 0; r0 < items; r0 += step) {
+            int it = r0 + lane;
+            if (lane < step && it < items) {
+                int js = it / C, col = it - js * C;
+                cf xp = Yw[js * 4 + 0], xm = Yw[js * 4 + 1], z = Yw[js * 4 + 2], d = Yw[js * 4 + 3];
+                cf r2 = xp * xm + z * z;
+                const cf* G = Gw + js * (P + 1);
+                int am = col <= P ? col : col - P;
+                bool neg = col > P;
+                int m = neg ? am : -am;
+                cf xs = neg ? xm : xp;
+                for (int i = 1; i <= am; ++i) d = (-__ldg(A.dg + i)) * (xs * d);
+                kadd(nmi(am, m), HELM ? G[am] * d : d);
+                if (am + 1 <= P) {
+                    cf p2 = d, p1 = __ldg(A.s21 + am) * (z * d);
+                    kadd(nmi(am + 1, m), HELM ? G[am + 1] * p1 : p1);
+                    for (int n = am + 2; n <= P; ++n) {
+                        int kk = nmi(n, am);
+                        cf cur = __ldg(A.zA + kk) * (z * p1) - __ldg(A.zB + kk) * (r2 * p2);
+                        kadd(nmi(n, m), HELM ? G[n] * cur : cur);
+                        p2 = p1;
+                        p1 = cur;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    cd* o = out + (int64_t)rhs * A.ncoef + A.eoff[b];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        cd v = {0.0, 0.0};
+        for (int w = 0; w < kP2m3fWarps; ++w) {
+            float4 a = acc[(size_t)w * nc + c];
+            v += cd{(double)a.x - (double)a.z, (double)a.y - (double)a.w};
+        }
+        int n, m;
+        nm_tab(A.knm, c, n, m);
+        double sc = 1.0, g = HELM ? A.kappa * rb : rb;
+        for (int j = 1; j <= n; ++j) sc *= HELM ? g / (2.0 * j + 1.0) : g;
+        if (HELM) o[c] = mul_i((A.kappa * (2.0 * n + 1.0) * sc) * v);
+        else o[c] = (__ldg(A.lsd + c) * sc) * v;
+    }
+}
+
+// shared memory of k_p2m3f at order P
+static size_t p2m3f_smem(int P) {
+    size_t nc = (size_t)(P + 1) * (P + 1);
+    return sizeof(float4) * kP2m3fWarps * nc + sizeof(cf) * (size_t)kP2m3fWarps * 32 * (P + 1 + 4);
+}
+
+static void launch_p2m3f(H3Tables* TB, bool helm, cfmm_plan_s* P, const int* boxes, int cnt, int PL,
+                         const int* dPlev, const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride,
+                         cd* out, int nrhs) {
+    if (cnt <= 0) return;
+    TreeDev& T = P->tree;
+    L2p3fArgs A{P->xr.get(), P->xi.get(), P->n, T.level.get(), T.start.get(), T.end.get(), T.cen_re.get(),
+                T.cen_im.get(), dPlev, eoff, ncoef, P->kappa, P->W, TB->zAf.get(), TB->zBf.get(),
+                TB->dgf.get(), TB->s21f.get(), TB->knm.get(), TB->lsd.get()};
+    size_t smem = p2m3f_smem(PL);
+    dim3 g((unsigned)cnt, nrhs);
+    if (helm) {
+        if (smem > 48 * 1024) CFMM_CUDA(cudaFuncSetAttribute(k_p2m3f<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2m3f<true><<<g, kP2m3fWarps * 32, smem, P->stream>>>(A, boxes, sigma, dstride, out);
+    } else {
+        if (smem > 48 * 1024) CFMM_CUDA(cudaFuncSetAttribute(k_p2m3f<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2m3f<false><<<g, kP2m3fWarps * 32, smem, P->stream>>>(A, boxes, sigma, dstride, out);
+    }
+    CFMM_LAUNCHED();
 }
 
 static void launch_l2p3f(H3Tables* TB, bool helm, cfmm_plan_s* P, const int* leaves, int cnt, int maxP,
@@ -1659,6 +1796,12 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     for (int l = S->l0; l < T.nlevels; ++l) {
         int cnt = S->p2m_off[l + 1] - S->p2m_off[l];
         if (cnt <= 0) continue;
+        if (slp_only && mixed && p2m3f_smem(S->Plev[l]) <= (size_t)kH3Smem) {
+            // complex64 products, FP64 sums
+            launch_p2m3f(TB, true, P, S->d_p2m.get() + S->p2m_off[l], cnt, S->Plev[l], S->dPlev.get(),
+                         S->exp_off.get(), S->ncoef, sigma, dstride, mp, nrhs);
+            continue;
+        }
         if (slp_only && slp_fits(l)) {
             p2x_slp(l, 0, S->d_p2m.get() + S->p2m_off[l], cnt, S->d_p2m_roff.get() + S->p2m_off[l], S->p2m_rtot[l], mp);
             continue;
@@ -1855,6 +1998,13 @@ bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int max
     k_p2x3h_slp<true><<<g, kH3Threads, smem, P->stream>>>(A, leaves, nullptr, nullptr, 0, nullptr, nullptr, out,
                                                           TB->lsd.get());
     CFMM_LAUNCHED();
+    return true;
+}
+
+bool lap3_p2m32(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs) {
+    if (maxP > L->tab->Pmax || p2m3f_smem(maxP) > (size_t)kH3Smem) return false;
+    launch_p2m3f(L->tab, false, P, leaves, cnt, maxP, dPlev, eoff, ncoef, sigma, dstride, out, nrhs);
     return true;
 }
 

@@ -96,6 +96,10 @@ bool lap3_p2m_slp(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int max
                   const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs);
 void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const int64_t* eoff, int64_t ncoef,
                     const cd* in, cd* out, int nrhs);
+// single-layer 3D Laplace P2M with complex64 products and FP64 sums over
+// `leaves` (writes their multipoles); false when the order does not fit
+bool lap3_p2m32(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
+                const int64_t* eoff, int64_t ncoef, const cd* sigma, int64_t dstride, cd* out, int nrhs);
 // 3D Laplace L2P in complex64 arithmetic over `leaves` (adds to u)
 void lap3_l2p32(Lap3Tr* L, cfmm_plan_s* P, const int* leaves, int cnt, int maxP, const int* dPlev,
                 const int64_t* eoff, int64_t ncoef, const cd* loc, cd* u, int nrhs);

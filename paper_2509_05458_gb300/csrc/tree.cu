@@ -1124,20 +1124,32 @@ static void build_lists(cfmm_plan_s* P, cudaStream_t st) {
 // float (inf when Re x_i = Re x_j but Im x_i != Im x_j). Coincident points
 // are skipped.
 constexpr int kLipWindow = 32;
-__global__ void k_lipschitz(const double* __restrict__ xr, const double* __restrict__ xi, int64_t n, int dim,
-                            unsigned* __restrict__ out) {
+constexpr int kLipBlock = 256;
+__global__ void __launch_bounds__(kLipBlock) k_lipschitz(const double* __restrict__ xr, const double* __restrict__ xi,
+                                                         int64_t n, int dim, unsigned* __restrict__ out) {
+    // the block's points and the kLipWindow after them (differences in FP64,
+    // their squares in FP32: the ratio needs no more precision)
+    __shared__ double sre[3][kLipBlock + kLipWindow], sim[3][kLipBlock + kLipWindow];
     __shared__ unsigned best_s;
+    int64_t i0 = blockIdx.x * (int64_t)kLipBlock;
     if (threadIdx.x == 0) best_s = 0u;
+    for (int k = threadIdx.x; k < kLipBlock + kLipWindow; k += blockDim.x) {
+        int64_t j = i0 + k;
+        for (int a = 0; a < dim; ++a) {
+            sre[a][k] = j < n ? xr[a * n + j] : 0.0;
+            sim[a][k] = j < n ? xi[a * n + j] : 0.0;
+        }
+    }
     __syncthreads();
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int t = threadIdx.x;
+    int64_t i = i0 + t;
     float best = 0.f;
     if (i < n) {
-        int64_t jmax = i + kLipWindow < n - 1 ? i + kLipWindow : n - 1;
-        for (int64_t j = i + 1; j <= jmax; ++j) {
+        int cnt = (int)min((int64_t)kLipWindow, n - 1 - i);
+        for (int q = 1; q <= cnt; ++q) {
             float a2 = 0.f, b2 = 0.f;
             for (int a = 0; a < dim; ++a) {
-                float dr = (float)(xr[a * n + i] - xr[a * n + j]);
-                float di = (float)(xi[a * n + i] - xi[a * n + j]);
+                float dr = (float)(sre[a][t] - sre[a][t + q]), di = (float)(sim[a][t] - sim[a][t + q]);
                 a2 = fmaf(dr, dr, a2);
                 b2 = fmaf(di, di, b2);
             }
@@ -1259,7 +1271,7 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
         unsigned* d = plan_scratch().take_n<unsigned>(1);
         CFMM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
         if (n > 1) {
-            k_lipschitz<<<blocks_for(n, 256), 256, 0, st>>>(P->xr.get(), P->xi.get(), n, dim, d);
+            k_lipschitz<<<blocks_for(n, kLipBlock), kLipBlock, 0, st>>>(P->xr.get(), P->xi.get(), n, dim, d);
             CFMM_LAUNCHED();
         }
         unsigned h = 0;

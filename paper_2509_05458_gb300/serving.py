@@ -16,7 +16,15 @@ does not depend on what else is in flight: `tests/test_gpu_serving.py` checks
 that each result is bitwise the same alone and in the mix.
 
 Latency of a request = time from its arrival to its last result copied back
-to the host; the run reports p50/p99 latency and points/s.
+to the host; the run reports p50/p99 latency and points/s. Requests the
+library cannot serve (for instance a 3D Helmholtz geometry whose top-level
+expansion order exceeds the translation kernels' limit, CFMM_EUNSUPPORTED)
+fail alone and are counted by error kind.
+
+Large streams are generated lazily: a request may carry only the parameters
+of its synthetic geometry and densities, and a producer thread materialises
+the next few requests ahead of their arrival (so the host-side generation is
+not part of a request's latency unless the producer falls behind).
 """
 from __future__ import annotations
 
@@ -41,29 +49,56 @@ class Request:
     kernel: int                     # LAPLACE/HELMHOLTZ or-ed with SLP/DLP
     kappa: float
     eps: float
-    pts_re: np.ndarray              # [n, dim] float64 (host)
-    pts_im: np.ndarray
-    rhs: List[np.ndarray]           # each [ncomp, n] complex128 (host)
+    pts_re: Optional[np.ndarray]    # [n, dim] float64 (host); None until materialised
+    pts_im: Optional[np.ndarray]
+    rhs: Optional[List[np.ndarray]]  # each [ncomp, n] complex128 (host)
     nrm_re: Optional[np.ndarray] = None
     nrm_im: Optional[np.ndarray] = None
     arrival: float = 0.0            # seconds from the start of the run
     leaf_size: int = 64
     precision: int = AUTO
     sep: int = 1                    # well-separatedness k (Sec. 6.2)
+    spec: Optional[dict] = None     # parameters of a lazily generated request
 
     @property
     def n(self):
-        return self.pts_re.shape[0]
+        return self.pts_re.shape[0] if self.pts_re is not None else int(self.spec["n"])
+
+    @property
+    def nrhs(self):
+        return len(self.rhs) if self.rhs is not None else int(self.spec["nmv"])
+
+    def materialize(self):
+        """Generate the geometry and densities of a lazily specified request."""
+        if self.pts_re is not None:
+            return self
+        from cfmm_inputs import curve2d, surface3d, densities
+        sp = self.spec
+        if self.dim == 2:
+            g = curve2d(sp["n"], seed=sp["gseed"], t_half=sp["t_half"], height=sp["height"])
+        else:
+            g = surface3d(sp["n"], seed=sp["gseed"], half=20.0, random_shape=True)
+        dens = densities(sp["n"], seed=sp["gseed"] + 1, nrhs=sp["nmv"], ncomp=1)
+        self.pts_re, self.pts_im = g.re, g.im
+        self.rhs = [dens[i] for i in range(sp["nmv"])]
+        return self
+
+    def release(self):
+        """Drop the host data of a lazily specified request once it is served."""
+        if self.spec is not None:
+            self.pts_re = self.pts_im = self.rhs = None
 
 
 @dataclasses.dataclass
 class Result:
     rid: int
-    outputs: List[np.ndarray]       # each [n] complex128
+    outputs: List[np.ndarray]       # each [n] complex128 (empty when outputs are not kept)
     arrival: float
     admitted: float
     done: float
     error: Optional[str] = None
+    points: int = 0                 # point evaluations delivered (n per right-hand side)
+    checksums: Optional[List[complex]] = None   # sum of each output (when outputs are not kept)
 
     @property
     def latency(self):
@@ -95,10 +130,12 @@ class Server:
         self.cv = threading.Condition()
         self.active = 0
 
-    def _run_one(self, req: Request, stream, t0: float, admitted: float) -> Result:
+    def _run_one(self, req: Request, stream, t0: float, admitted: float, keep=True) -> Result:
         torch = self.torch
-        outs = []
+        outs, sums = [], []
+        points = 0
         try:
+            req.materialize()
             with torch.cuda.stream(stream):
                 re = torch.from_numpy(np.ascontiguousarray(req.pts_re)).to(self.dev, non_blocking=True)
                 im = torch.from_numpy(np.ascontiguousarray(req.pts_im)).to(self.dev, non_blocking=True)
@@ -112,26 +149,50 @@ class Server:
                 for r in req.rhs:
                     d = torch.from_numpy(np.ascontiguousarray(r)[None]).to(self.dev, non_blocking=True)
                     p.apply(d, out=out)
-                    outs.append(out[0].cpu().numpy())   # synchronises this stream only
+                    h = out[0].cpu().numpy()   # synchronises this stream only
+                    if keep:
+                        outs.append(h)
+                    else:
+                        sums.append(complex(h.sum()))
+                    points += req.n
                 p.destroy()
             err = None
         except Exception as e:   # reported per request; the server keeps going
             err = f"{type(e).__name__}: {e}"
-        return Result(req.rid, outs, req.arrival, admitted, time.perf_counter() - t0, err)
+        finally:
+            if not keep:
+                req.release()
+        return Result(req.rid, outs, req.arrival, admitted, time.perf_counter() - t0, err, points,
+                      None if keep else sums)
 
-    def run(self, requests: List[Request], realtime=True) -> List[Result]:
+    def run(self, requests: List[Request], realtime=True, keep_outputs=True, prefetch=8) -> List[Result]:
         """Serve `requests`. With realtime=True a request is not visible before its
-        arrival time (seconds after the call starts); admission is FIFO."""
+        arrival time (seconds after the call starts); admission is FIFO. Lazily
+        specified requests are materialised by a producer thread up to
+        `prefetch` requests ahead of admission."""
         torch = self.torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         results: List[Optional[Result]] = [None] * len(reqs)
         t0 = time.perf_counter()
         streams = [torch.cuda.Stream(device=self.dev) for _ in range(self.slots)]
         free_streams = list(range(self.slots))
+        ready = threading.Semaphore(0)
+        window = threading.Semaphore(max(1, prefetch))
+        stop = threading.Event()
+
+        def producer():
+            for r in reqs:
+                if not window.acquire(timeout=None) or stop.is_set():
+                    return
+                r.materialize()
+                ready.release()
+
+        prod = threading.Thread(target=producer, daemon=True)
+        prod.start()
 
         def worker(i, req, sidx, need, admitted):
             try:
-                results[i] = self._run_one(req, streams[sidx], t0, admitted)
+                results[i] = self._run_one(req, streams[sidx], t0, admitted, keep_outputs)
             finally:
                 with self.cv:
                     self.in_use -= need
@@ -142,38 +203,46 @@ class Server:
         futs = []
         waiting = []
         k = 0
-        # one long-lived host thread per slot (their plan-construction scratch is reused)
-        with cfut.ThreadPoolExecutor(max_workers=self.slots) as pool:
-            while k < len(reqs) or waiting:
-                now = time.perf_counter() - t0
-                while k < len(reqs) and (not realtime or reqs[k].arrival <= now):
-                    waiting.append((k, reqs[k]))
-                    k += 1
-                with self.cv:
-                    progressed = False
-                    while waiting and free_streams:
-                        i, req = waiting[0]
-                        need = min(estimate_bytes(req), self.budget)
-                        if self.in_use + need > self.budget and self.active > 0:
-                            break                   # the head of the queue waits for memory
-                        waiting.pop(0)
-                        self.in_use += need
-                        self.active += 1
-                        sidx = free_streams.pop(0)
-                        futs.append(pool.submit(worker, i, req, sidx, need, time.perf_counter() - t0))
-                        progressed = True
-                    if not progressed:
-                        nxt = reqs[k].arrival - now if (realtime and k < len(reqs)) else 0.05
-                        self.cv.wait(timeout=max(1e-4, min(0.05, nxt)))
-            for f in futs:
-                f.result()
+        try:
+            # one long-lived host thread per slot (their plan-construction scratch is reused)
+            with cfut.ThreadPoolExecutor(max_workers=self.slots) as pool:
+                while k < len(reqs) or waiting:
+                    now = time.perf_counter() - t0
+                    while k < len(reqs) and (not realtime or reqs[k].arrival <= now):
+                        if not ready.acquire(blocking=False):
+                            break                    # its data is still being generated
+                        waiting.append((k, reqs[k]))
+                        k += 1
+                    with self.cv:
+                        progressed = False
+                        while waiting and free_streams:
+                            i, req = waiting[0]
+                            need = min(estimate_bytes(req), self.budget)
+                            if self.in_use + need > self.budget and self.active > 0:
+                                break                   # the head of the queue waits for memory
+                            waiting.pop(0)
+                            window.release()
+                            self.in_use += need
+                            self.active += 1
+                            sidx = free_streams.pop(0)
+                            futs.append(pool.submit(worker, i, req, sidx, need, time.perf_counter() - t0))
+                            progressed = True
+                        if not progressed:
+                            nxt = reqs[k].arrival - now if (realtime and k < len(reqs)) else 0.005
+                            self.cv.wait(timeout=max(1e-4, min(0.005 if k < len(reqs) else 0.05, nxt)))
+                for f in futs:
+                    f.result()
+        finally:
+            stop.set()
+            window.release()
         torch.cuda.synchronize(self.dev)
         return results
 
 
 def summarize(results: List[Result], wall_s: float):
     lat = sorted(r.latency for r in results if r.error is None)
-    pts = sum(len(r.outputs) * (r.outputs[0].shape[0] if r.outputs else 0) for r in results if r.error is None)
+    pts = sum(r.points if r.points else len(r.outputs) * (r.outputs[0].shape[0] if r.outputs else 0)
+              for r in results if r.error is None)
 
     def pct(p):
         if not lat:
@@ -191,11 +260,12 @@ def summarize(results: List[Result], wall_s: float):
             "points_per_s": pts / wall_s if wall_s > 0 else None, "wall_s": wall_s}
 
 
-def make_stream(nreq, seed=7, rate_hz=20.0, nmin=1_000, nmax=200_000, dims=(2,), max_matvec=20):
+def make_stream(nreq, seed=7, rate_hz=20.0, nmin=1_000, nmax=200_000, dims=(2,), max_matvec=20, lazy=False,
+                precision=AUTO):
     """A Poisson stream of requests on the synthetic families: dim in `dims`,
-    Laplace or Helmholtz (k ~ U[1, 50]), N log-uniform in [nmin, nmax],
-    eps in {1e-3, 1e-6, 1e-9}, 1..max_matvec right-hand sides."""
-    from cfmm_inputs import curve2d, surface3d, densities
+    Laplace or Helmholtz (k ~ U[1, 50] in both dimensions), N log-uniform in
+    [nmin, nmax], eps in {1e-3, 1e-6, 1e-9}, 1..max_matvec right-hand sides.
+    lazy=True: the requests carry the parameters only (Request.materialize)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
@@ -204,22 +274,17 @@ def make_stream(nreq, seed=7, rate_hz=20.0, nmin=1_000, nmax=200_000, dims=(2,),
         dim = int(rng.choice(dims))
         helm = bool(rng.integers(0, 2))
         kappa = float(rng.uniform(1.0, 50.0)) if helm else 0.0
-        if dim == 3:
-            # 3D Helmholtz surfaces are 40 units wide: k in [1, 10] keeps them
-            # within the range where the complex-coordinate expansions stay
-            # accurate (Sec. 6.5); the draw is mapped, not redrawn
-            kappa = 1.0 + (kappa - 1.0) * 9.0 / 49.0 if helm else 0.0
         n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
         eps = float(rng.choice([1e-3, 1e-6, 1e-9]))
         nmv = int(rng.integers(1, max_matvec + 1))
         gseed = int(rng.integers(0, 2**31 - 1))
-        if dim == 2:
-            g = curve2d(n, seed=gseed, t_half=10.0 + 30.0 * rng.uniform(), height=float(rng.uniform(0.3, 1.0)))
-        else:
-            g = surface3d(n, seed=gseed, half=20.0, random_shape=True)
-        dens = densities(n, seed=gseed + 1, nrhs=nmv, ncomp=1)
-        out.append(Request(rid, dim, (1 if helm else 0) | SLP, kappa, eps, g.re, g.im,
-                           [dens[i] for i in range(nmv)], arrival=t, sep=2 if dim == 3 else 1))
+        t_half, height = 10.0 + 30.0 * rng.uniform(), float(rng.uniform(0.3, 1.0))
+        spec = dict(n=n, nmv=nmv, gseed=gseed, t_half=t_half, height=height)
+        r = Request(rid, dim, (1 if helm else 0) | SLP, kappa, eps, None, None, None, arrival=t,
+                    sep=2 if dim == 3 else 1, precision=precision, spec=spec)
+        if not lazy:
+            r.materialize()
+        out.append(r)
     return out
 
 

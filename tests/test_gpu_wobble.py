@@ -1,0 +1,53 @@
+"""The paper's own test interfaces (Sec. 7.1, Eqs. wobble_2D_cplx and
+complex_wobble) through the C ABI: single layer potentials of 2D/3D Laplace
+and Helmholtz (kappa = 2 pi, as the paper's 2D timings) against the oracle FMM
+(same tree and orders, relative l2 <= 1e-12) and within eps of the oracle's
+direct sum (Eq. relerr), at eps = 1e-6 and 1e-12 (the paper's two accuracies)."""
+import numpy as np
+import pytest
+
+from cfmm_inputs import wobble2d, wobble3d, densities
+from oracle import fmm2d, fmm3d, helm3d as H
+from oracle.direct import direct, relerr_paper, relerr_l2
+from tests.gpu_util import gpu_plan, to_dev
+
+pytestmark = pytest.mark.gpu
+KAPPA = 2 * np.pi
+
+
+@pytest.mark.parametrize("ker", [0, 1])
+@pytest.mark.parametrize("eps", [1e-6, 1e-12])
+def test_wobble2d(cuda, ker, eps):
+    import paper_2509_05458_gb300 as cf
+    g = wobble2d(3000, seed=4)
+    kap = KAPPA if ker else 0.0
+    p = gpu_plan(cf, g, ker, kap, eps, cuda, 32)
+    dens = densities(g.n, seed=5, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()[0]
+    uo, T = fmm2d.apply(g.re, g.im, ker, kap, eps, 32, sigma=dens[0, 0])
+    assert list(p.orders()) == fmm2d.expansion_orders(T, ker, kap, eps)
+    assert relerr_l2(u, uo) <= (1e-12 if eps > 1e-10 else 1e-11)
+    pts = g.re + 1j * g.im
+    u0 = direct(2, ker, kap, pts, pts, sigma=dens[0, 0])
+    assert relerr_paper(u, u0, dens[0, 0]) <= eps
+
+
+@pytest.mark.parametrize("ker,eps", [(0, 1e-6), (0, 1e-12), (1, 1e-6)])
+def test_wobble3d(cuda, ker, eps):
+    import paper_2509_05458_gb300 as cf
+    g = wobble3d(1500)
+    kap = KAPPA if ker else 0.0
+    p = gpu_plan(cf, g, ker, kap, eps, cuda, 32, sep=2)
+    dens = densities(g.n, seed=6, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()[0]
+    if ker == 0:
+        uo, T = fmm3d.apply(g.re, g.im, eps, 32, k=2, sigma=dens[0, 0])
+        assert list(p.orders()) == fmm3d.expansion_orders(T, eps)
+    else:
+        uo, T = H.apply(g.re, g.im, kap, eps, 32, k=2, sigma=dens[:, 0], coaxial="exact")
+        uo = uo[0]
+        assert list(p.orders()) == H.expansion_orders(T, kap, eps)
+    assert relerr_l2(u, uo) <= (1e-12 if eps > 1e-10 else 1e-11)
+    pts = g.re + 1j * g.im
+    u0 = direct(3, ker, kap, pts, pts, sigma=dens[0, 0])
+    assert relerr_paper(u, u0, dens[0, 0]) <= eps

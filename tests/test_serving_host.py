@@ -19,8 +19,23 @@ def test_stream_is_seeded_and_within_bounds():
         helm = (r.kernel & 0xF) == 1
         assert (r.kappa > 0) == helm
         if r.dim == 3:
-            assert r.sep == 2 and r.kappa <= 10.0
+            assert r.sep == 2 and r.kappa <= 50.0
     assert {r.dim for r in a} == {2, 3}
+    # kappa ~ U[1, 50] in both dimensions (no remapping)
+    big = make_stream(400, seed=6, rate_hz=10.0, nmin=1000, nmax=2000, dims=(2, 3), max_matvec=1, lazy=True)
+    assert max(r.kappa for r in big if r.dim == 3) > 40.0
+
+
+def test_lazy_stream_materializes_the_same_data():
+    a = make_stream(6, seed=8, nmin=1000, nmax=5000, dims=(2, 3), max_matvec=3)
+    b = make_stream(6, seed=8, nmin=1000, nmax=5000, dims=(2, 3), max_matvec=3, lazy=True)
+    for x, y in zip(a, b):
+        assert y.pts_re is None and y.n == x.n and y.nrhs == len(x.rhs)
+        y.materialize()
+        assert np.array_equal(x.pts_re, y.pts_re) and np.array_equal(x.pts_im, y.pts_im)
+        assert all(np.array_equal(p, q) for p, q in zip(x.rhs, y.rhs))
+        y.release()
+        assert y.pts_re is None
 
 
 def test_memory_estimate_grows_with_size_and_kernel():
