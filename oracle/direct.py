@@ -73,6 +73,75 @@ def kernel_pair(dim, kernel, kappa, d, nrm=None):
     return slp, dlp
 
 
+def kernel_pair_grad(dim, kernel, kappa, d, nrm=None):
+    """grad_x K(x, y) and grad_x (n . grad_y K)(x, y) for d = x - y (Sec. 2.1:
+    the target gradient of the single and double layer kernels, whose normal
+    components give S' and D').
+
+    With K = K(r), grad_x K = K'(r) d / r, and since n . grad_y K = -K'(r) (n.d)/r,
+    grad_x (n . grad_y K) = -(K'(r)/r) n - (K''(r) - K'(r)/r) (n.d) d / r^2.
+    d: complex [..., dim]; returns (gs, gd) complex [..., dim] (gd None without nrm).
+    """
+    r2 = np.sum(d * d, axis=-1)
+    r = np.sqrt(r2)
+    if dim == 2 and kernel == LAPLACE:
+        k1 = 1.0 / r                              # K = log r
+        k2 = -1.0 / r2
+    elif dim == 2 and kernel == HELMHOLTZ:
+        z = kappa * r
+        h0, h1 = sps.hankel1(0, z), sps.hankel1(1, z)
+        k1 = -kappa * h1                          # K = H0(kappa r)
+        k2 = -kappa * kappa * (h0 - h1 / z)       # d/dr (-kappa H1) = -kappa^2 H1'(z)
+    elif dim == 3 and kernel == LAPLACE:
+        k1 = -1.0 / r2                            # K = 1/r
+        k2 = 2.0 / (r2 * r)
+    elif dim == 3 and kernel == HELMHOLTZ:
+        e = np.exp(1j * kappa * r)                # K = e^{i kappa r}/r
+        k1 = e * (1j * kappa * r - 1.0) / r2
+        k2 = e * (2.0 - 2j * kappa * r - kappa * kappa * r2) / (r2 * r)
+    else:
+        raise ValueError("unsupported dim/kernel")
+    gs = (k1 / r)[..., None] * d
+    gd = None
+    if nrm is not None:
+        nd = np.sum(nrm * d, axis=-1)
+        gd = -(k1 / r)[..., None] * nrm - ((k2 - k1 / r) * nd / r2)[..., None] * d
+    return gs, gd
+
+
+def direct_grad(dim, kernel, kappa, src, trg, sigma=None, tau=None, nrm=None, chunk=None):
+    """grad_x u(x_i) for u of ``direct``: [nrhs][dim][N] (or [dim][N]); pairs
+    with x - y == 0 are skipped."""
+    src = np.asarray(src, dtype=np.complex128)
+    trg = np.asarray(trg, dtype=np.complex128)
+    single = True
+    if sigma is not None:
+        sigma = np.asarray(sigma, dtype=np.complex128)
+        single = sigma.ndim == 1
+    if tau is not None:
+        tau = np.asarray(tau, dtype=np.complex128)
+        single = tau.ndim == 1
+        nrm = np.asarray(nrm, dtype=np.complex128)
+    nrhs = (np.atleast_2d(sigma) if sigma is not None else np.atleast_2d(tau)).shape[0]
+    N, M = trg.shape[0], src.shape[0]
+    out = np.zeros((nrhs, dim, N), dtype=np.complex128)
+    if chunk is None:
+        chunk = max(1, min(N, 2_000_000 // max(M, 1)))
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        d = trg[a:b, None, :] - src[None, :, :]
+        zero = np.all(d == 0, axis=-1)
+        d = np.where(zero[..., None], 1.0, d)
+        gs, gd = kernel_pair_grad(dim, kernel, kappa, d, None if tau is None else np.broadcast_to(nrm[None], d.shape))
+        if sigma is not None:
+            gs = np.where(zero[..., None], 0.0, gs)
+            out[:, :, a:b] += np.einsum("tmk,rm->rkt", gs, np.atleast_2d(sigma))
+        if tau is not None:
+            gd = np.where(zero[..., None], 0.0, gd)
+            out[:, :, a:b] += np.einsum("tmk,rm->rkt", gd, np.atleast_2d(tau))
+    return out[0] if single else out
+
+
 def direct(dim, kernel, kappa, src, trg, sigma=None, tau=None, nrm=None,
            chunk=None, green_scale=False):
     """u(x_i) = sum_j K(x_i, y_j) sigma_j + sum_j (n_j . grad_y K)(x_i, y_j) tau_j.

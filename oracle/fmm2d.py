@@ -43,7 +43,7 @@ import numpy as np
 import scipy.special as sps
 
 from . import tree as tr
-from .direct import kernel_pair, LAPLACE, HELMHOLTZ
+from .direct import kernel_pair, kernel_pair_grad, LAPLACE, HELMHOLTZ
 
 
 def _zeta_eta(d):
@@ -224,6 +224,45 @@ class Expansions2D:
         G = cyl_seq("J", -P, P, self.kappa, x - c[None, :])
         return L @ G.T
 
+    # ---- target gradients (d/dx1 = d/dzeta + d/deta, d/dx2 = i (d/dzeta - d/deta)) ----
+
+    @staticmethod
+    def _grad(dz, de):
+        """[nrhs, ntarg] d/dzeta, d/deta -> [nrhs, 2, ntarg] gradient."""
+        return np.stack([dz + de, 1j * (dz - de)], axis=1)
+
+    def lap_m2p_grad(self, P, M, d):
+        """grad of M0 log r + sum Mp_n eta^-n + sum Mm_n zeta^-n (log r = log(zeta eta)/2)."""
+        zeta, eta = _zeta_eta(d)
+        n = np.arange(1, P + 1)
+        dz = M[:, :1] * (0.5 / zeta)[None, :] - M[:, P + 1:] @ (n[:, None] * zeta[None, :] ** (-n - 1)[:, None])
+        de = M[:, :1] * (0.5 / eta)[None, :] - M[:, 1:P + 1] @ (n[:, None] * eta[None, :] ** (-n - 1)[:, None])
+        return self._grad(dz, de)
+
+    def lap_l2p_grad(self, P, L, d):
+        """grad of L0 + sum Lp_n zeta^n + sum Lm_n eta^n."""
+        zeta, eta = _zeta_eta(d)
+        n = np.arange(1, P + 1)
+        dz = L[:, 1:P + 1] @ (n[:, None] * zeta[None, :] ** (n - 1)[:, None])
+        de = L[:, P + 1:] @ (n[:, None] * eta[None, :] ** (n - 1)[:, None])
+        return self._grad(dz, de)
+
+    def hel_m2p_grad(self, P, M, c, x):
+        """d/dzeta S_n = (kappa/2) S_{n-1}, d/deta S_n = -(kappa/2) S_{n+1}."""
+        S = cyl_seq("H", -P - 1, P + 1, self.kappa, x - c[None, :])
+        idx = np.arange(-P, P + 1) + P + 1
+        dz = (0.5 * self.kappa) * (M @ S[:, idx - 1].T)
+        de = (-0.5 * self.kappa) * (M @ S[:, idx + 1].T)
+        return self._grad(dz, de)
+
+    def hel_l2p_grad(self, P, L, c, x):
+        """d/dzeta G_n = (kappa/2) G_{n-1}, d/deta G_n = -(kappa/2) G_{n+1}."""
+        G = cyl_seq("J", -P - 1, P + 1, self.kappa, x - c[None, :])
+        idx = np.arange(-P, P + 1) + P + 1
+        dz = (0.5 * self.kappa) * (L @ G[:, idx - 1].T)
+        de = (-0.5 * self.kappa) * (L @ G[:, idx + 1].T)
+        return self._grad(dz, de)
+
     def hel_shift(self, kind, Pin, Pout, E, a):
         """E'_m = sum_n T_{n-m}(a) E_n, |m|<=Pout, |n|<=Pin; T = G or S."""
         T = cyl_seq(kind, -(Pin + Pout), Pin + Pout, self.kappa, a[None, :])[0]
@@ -243,11 +282,14 @@ def expansion_orders(T, kernel, kappa, eps):
     return [tr.nterms_helmholtz(2, T.k, e, kappa, T.width(l), tr.helm2d_pair) for l in range(nl)]
 
 
-def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None):
+def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, grad=False):
     """Apply the 2D complex-coordinate FMM on tree T.
 
     pts: complex [n, 2] in tree (sorted) order; sigma/tau: complex [nrhs, n]
-    sorted; nrm: complex [n, 2] sorted. Returns u: complex [nrhs, n] sorted.
+    sorted; nrm: complex [n, 2] sorted. Returns u: complex [nrhs, n] sorted;
+    with grad=True, (u, g) with the target gradient g [nrhs, 2, n] from the
+    differentiated evaluation steps (P2P, M2P, L2P; the expansions are the
+    same).
     """
     n = pts.shape[0]
     if P_levels is None:
@@ -255,6 +297,7 @@ def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=N
     X = Expansions2D(kernel, kappa, P_levels)
     nr = (sigma if sigma is not None else tau).shape[0]
     u = np.zeros((nr, n), complex)
+    g = np.zeros((nr, 2, n), complex) if grad else None
     nb = T.nboxes
     lv = T.box_level
     cen = T.center_re + 1j * T.center_im          # complexified centres, Eq. complexify_center_average
@@ -318,8 +361,15 @@ def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=N
                 u[:, ts:te] += sg @ np.where(zero, 0, slp).T
             if dipole:
                 u[:, ts:te] += tau[:, s:e] @ np.where(zero, 0, dlp).T
+            if grad:
+                gs, gd = kernel_pair_grad(2, kernel, kappa, dd,
+                                          None if not dipole else np.broadcast_to(nrm[None, s:e, :], dd.shape))
+                if sg is not None:
+                    g[:, :, ts:te] += np.einsum("tmk,rm->rkt", np.where(zero[..., None], 0, gs), sg)
+                if dipole:
+                    g[:, :, ts:te] += np.einsum("tmk,rm->rkt", np.where(zero[..., None], 0, gd), tau[:, s:e])
     if not expand:
-        return u
+        return (u, g) if grad else u
     # (4) M2L over List 2
     for b in range(nb):
         if lv[b] < l0:
@@ -341,8 +391,12 @@ def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=N
             Pa = P_levels[lv[a]]
             if lap:
                 u[:, ts:te] += X.lap_m2p(Pa, M[a], pts[ts:te] - cen[a][None, :])
+                if grad:
+                    g[:, :, ts:te] += X.lap_m2p_grad(Pa, M[a], pts[ts:te] - cen[a][None, :])
             else:
                 u[:, ts:te] += X.hel_m2p(Pa, M[a], cen[a], pts[ts:te])
+                if grad:
+                    g[:, :, ts:te] += X.hel_m2p_grad(Pa, M[a], cen[a], pts[ts:te])
     # (6) P2L over List 4
     for b in range(nb):
         if lv[b] < l0:
@@ -371,9 +425,13 @@ def fmm2d(T, kernel, kappa, eps, pts, sigma=None, tau=None, nrm=None, P_levels=N
         P = P_levels[lv[b]]
         if lap:
             u[:, ts:te] += X.lap_l2p(P, Lc[b], pts[ts:te] - cen[b][None, :])
+            if grad:
+                g[:, :, ts:te] += X.lap_l2p_grad(P, Lc[b], pts[ts:te] - cen[b][None, :])
         else:
             u[:, ts:te] += X.hel_l2p(P, Lc[b], cen[b], pts[ts:te])
-    return u
+            if grad:
+                g[:, :, ts:te] += X.hel_l2p_grad(P, Lc[b], cen[b], pts[ts:te])
+    return (u, g) if grad else u
 
 
 def apply(geom_re, geom_im, kernel, kappa, eps, N_s, k=1, sigma=None, tau=None,
@@ -405,3 +463,25 @@ def apply(geom_re, geom_im, kernel, kappa, eps, N_s, k=1, sigma=None, tau=None,
     u = np.empty_like(u_s)
     u[:, perm] = u_s
     return (u[0] if single else u), T
+
+
+def apply_grad(geom_re, geom_im, kernel, kappa, eps, N_s, k=1, sigma=None, tau=None,
+               nrm_re=None, nrm_im=None, P_levels=None, T=None):
+    """As ``apply``, also returning the target gradient: (u, g, T) with g
+    [nrhs, 2, n] (or [2, n]) in input order."""
+    pts = np.asarray(geom_re) + 1j * np.asarray(geom_im)
+    if T is None:
+        T = tr.build_tree(geom_re, geom_im, N_s, k=k, kappa=kappa, eps=eps,
+                          helmholtz=(kernel == HELMHOLTZ))
+    perm = T.perm
+    single = (sigma if sigma is not None else tau).ndim == 1
+    prep = lambda v: None if v is None else np.atleast_2d(np.asarray(v, complex))[:, perm]
+    nrm = None
+    if tau is not None:
+        nrm = (np.asarray(nrm_re) + 1j * np.asarray(nrm_im))[perm]
+    u_s, g_s = fmm2d(T, kernel, kappa, eps, pts[perm], prep(sigma), prep(tau), nrm, P_levels, grad=True)
+    u = np.empty_like(u_s)
+    u[:, perm] = u_s
+    g = np.empty_like(g_s)
+    g[:, :, perm] = g_s
+    return (u[0], g[0], T) if single else (u, g, T)

@@ -39,7 +39,7 @@ import functools
 import numpy as np
 
 from . import tree as tr
-from .direct import kernel_pair, LAPLACE
+from .direct import kernel_pair, kernel_pair_grad, LAPLACE
 
 
 def idx(n, m):
@@ -104,6 +104,37 @@ def _get(tab, n, m):
     return tab[idx(n, m)]
 
 
+def regular_dir(P, x, v):
+    """v . grad U_n^m(x), n <= P (d+ U_n^m = -U_{n-1}^{m-1}/2, d- U_n^m = U_{n-1}^{m+1}/2,
+    dz U_n^m = U_{n-1}^m with v . grad = v+ d+ + v- d- + v3 dz, v+- = v1 +- i v2)."""
+    U = regular(P, x)
+    v = np.asarray(v, complex)
+    vp, vm, v3 = v[..., 0] + 1j * v[..., 1], v[..., 0] - 1j * v[..., 1], v[..., 2]
+    out = np.zeros_like(U)
+    for n in range(1, P + 1):
+        for m in range(-n, n + 1):
+            out[idx(n, m)] = (vp * (-0.5) * _get(U, n - 1, m - 1) + vm * 0.5 * _get(U, n - 1, m + 1)
+                              + v3 * _get(U, n - 1, m))
+    return out
+
+
+def irregular_dir(P, x, v):
+    """v . grad T_n^m(x), n <= P (d+ T_n^m = -T_{n+1}^{m-1}/2, d- T_n^m = T_{n+1}^{m+1}/2,
+    dz T_n^m = -T_{n+1}^m)."""
+    T = irregular(P + 1, x)
+    v = np.asarray(v, complex)
+    vp, vm, v3 = v[..., 0] + 1j * v[..., 1], v[..., 0] - 1j * v[..., 1], v[..., 2]
+    out = np.zeros(((P + 1) ** 2,) + T.shape[1:], complex)
+    for n in range(P + 1):
+        for m in range(-n, n + 1):
+            out[idx(n, m)] = (vp * (-0.5) * _get(T, n + 1, m - 1) + vm * 0.5 * _get(T, n + 1, m + 1)
+                              - v3 * _get(T, n + 1, m))
+    return out
+
+
+_UNIT = np.eye(3)
+
+
 class Laplace3D:
     """Operators of the 3D Laplace expansions (coefficients stacked by idx(n, m))."""
 
@@ -154,6 +185,16 @@ class Laplace3D:
     def l2p(P, L, d):
         U = regular(P, d)
         return L @ U
+
+    @staticmethod
+    def m2p_grad(P, M, d):
+        """target gradient of M2P: [nrhs, 3, ntarg]."""
+        return np.stack([M @ irregular_dir(P, d, _UNIT[a]) for a in range(3)], axis=1)
+
+    @staticmethod
+    def l2p_grad(P, L, d):
+        """target gradient of L2P: [nrhs, 3, ntarg]."""
+        return np.stack([L @ regular_dir(P, d, _UNIT[a]) for a in range(3)], axis=1)
 
     kernel = LAPLACE
     kappa = 0.0
@@ -227,8 +268,10 @@ def expansion_orders(T, eps):
     return [tr.nterms_laplace(3, T.k, eps * tr.P_HEADROOM)] * T.nlevels
 
 
-def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
-    """3D FMM on tree T; pts/sigma/tau/nrm in tree (sorted) order.
+def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None, grad=False):
+    """3D FMM on tree T; pts/sigma/tau/nrm in tree (sorted) order. grad=True
+    returns (u, g) with the target gradient g [nrhs, 3, n] from the
+    differentiated P2P, M2P and L2P steps.
 
     ops: the expansion operators (``Laplace3D`` by default, or an instance of
     ``oracle.helm3d.Helmholtz3D``); translations receive the level of the box
@@ -240,6 +283,7 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
     X = Laplace3D if ops is None else ops
     nr = (sigma if sigma is not None else tau).shape[0]
     u = np.zeros((nr, n), complex)
+    g = np.zeros((nr, 3, n), complex) if grad else None
     nb = T.nboxes
     lv = T.box_level
     cen = T.center_re + 1j * T.center_im
@@ -293,8 +337,15 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
                 u[:, ts:te] += sg @ np.where(zero, 0, slp).T
             if dipole:
                 u[:, ts:te] += tau[:, s:e] @ np.where(zero, 0, dlp).T
+            if grad:
+                gs, gd = kernel_pair_grad(3, X.kernel, X.kappa, dd, None if not dipole else
+                                          np.broadcast_to(nrm[None, s:e, :], dd.shape))
+                if sg is not None:
+                    g[:, :, ts:te] += np.einsum("tmk,rm->rkt", np.where(zero[..., None], 0, gs), sg)
+                if dipole:
+                    g[:, :, ts:te] += np.einsum("tmk,rm->rkt", np.where(zero[..., None], 0, gd), tau[:, s:e])
     if not expand:
-        return u
+        return (u, g) if grad else u
     for b in range(nb):
         if lv[b] >= l0:
             Lc[b] = np.zeros((nr, (P_levels[lv[b]] + 1) ** 2), complex)
@@ -314,6 +365,8 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
             ts, te = st[b], en[b]
             for a in T.lists["list3"][b]:
                 u[:, ts:te] += X.m2p(P_levels[lv[a]], M[a], pts[ts:te] - cen[a][None, :])
+                if grad:
+                    g[:, :, ts:te] += X.m2p_grad(P_levels[lv[a]], M[a], pts[ts:te] - cen[a][None, :])
     for b in range(nb):
         if lv[b] < l0:
             continue
@@ -335,7 +388,9 @@ def fmm3d(T, eps, pts, sigma=None, tau=None, nrm=None, P_levels=None, ops=None):
         if T.box_leaf[b] and lv[b] >= l0:
             ts, te = st[b], en[b]
             u[:, ts:te] += X.l2p(P_levels[lv[b]], Lc[b], pts[ts:te] - cen[b][None, :])
-    return u
+            if grad:
+                g[:, :, ts:te] += X.l2p_grad(P_levels[lv[b]], Lc[b], pts[ts:te] - cen[b][None, :])
+    return (u, g) if grad else u
 
 
 def apply(geom_re, geom_im, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None, nrm_im=None,
@@ -364,3 +419,22 @@ def apply(geom_re, geom_im, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None, nr
     u = np.empty_like(u_s)
     u[:, perm] = u_s
     return (u[0] if single else u), T
+
+
+def apply_grad(geom_re, geom_im, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None, nrm_im=None,
+               P_levels=None, T=None, ops=None):
+    """As ``apply``, also returning the target gradient: (u, g, T), g [nrhs, 3, n]
+    (or [3, n]) in input order."""
+    pts = np.asarray(geom_re) + 1j * np.asarray(geom_im)
+    if T is None:
+        T = tr.build_tree(geom_re, geom_im, N_s, k=k, eps=eps, helmholtz=False)
+    perm = T.perm
+    single = (sigma if sigma is not None else tau).ndim == 1
+    prep = lambda v: None if v is None else np.atleast_2d(np.asarray(v, complex))[:, perm]
+    nrm = None if tau is None else (np.asarray(nrm_re) + 1j * np.asarray(nrm_im))[perm]
+    u_s, g_s = fmm3d(T, eps, pts[perm], prep(sigma), prep(tau), nrm, P_levels, ops, grad=True)
+    u = np.empty_like(u_s)
+    u[:, perm] = u_s
+    g = np.empty_like(g_s)
+    g[:, :, perm] = g_s
+    return (u[0], g[0], T) if single else (u, g, T)

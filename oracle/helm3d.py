@@ -412,6 +412,14 @@ class Helmholtz3D:
     def l2p(self, P, L, d):
         return L @ wave("j", P, self.kappa, d)
 
+    def m2p_grad(self, P, M, d):
+        """target gradient of M2P: [nrhs, 3, ntarg] (wave_dir along the axes)."""
+        return np.stack([M @ wave_dir("h", P, self.kappa, d, np.eye(3)[a]) for a in range(3)], axis=1)
+
+    def l2p_grad(self, P, L, d):
+        """target gradient of L2P: [nrhs, 3, ntarg]."""
+        return np.stack([L @ wave_dir("j", P, self.kappa, d, np.eye(3)[a]) for a in range(3)], axis=1)
+
     def _radius(self, level):
         return math.sqrt(3.0) * 0.5 * self.T.width(level)
 
@@ -467,3 +475,16 @@ def apply(geom_re, geom_im, kappa, eps, N_s, k=1, sigma=None, tau=None, nrm_re=N
         P_levels = expansion_orders(T, kappa, eps)
     return fmm3d.apply(geom_re, geom_im, eps, N_s, k=k, sigma=sigma, tau=tau, nrm_re=nrm_re,
                        nrm_im=nrm_im, P_levels=P_levels, T=T, ops=Helmholtz3D(kappa, T, coaxial))
+
+
+def apply_grad(geom_re, geom_im, kappa, eps, N_s, k=1, sigma=None, tau=None, nrm_re=None,
+               nrm_im=None, P_levels=None, T=None, top_level=0, coaxial="projection"):
+    """As ``apply``, also returning the target gradient: (u, g, T)."""
+    from . import fmm3d
+    if T is None:
+        T = tr.build_tree(geom_re, geom_im, N_s, k=k, kappa=kappa, eps=eps, helmholtz=True,
+                          top_level=top_level)
+    if P_levels is None:
+        P_levels = expansion_orders(T, kappa, eps)
+    return fmm3d.apply_grad(geom_re, geom_im, eps, N_s, k=k, sigma=sigma, tau=tau, nrm_re=nrm_re,
+                            nrm_im=nrm_im, P_levels=P_levels, T=T, ops=Helmholtz3D(kappa, T, coaxial))
