@@ -142,6 +142,25 @@ cfmm_plan_t cfmm_plan_targets(int dim, int kernel, double k, double eps,
 int cfmm_apply(cfmm_plan_t plan, const double* densities, int nrhs, double* out);
 
 /*
+ * cfmm_apply_grad: as cfmm_apply, and also the target gradient of the result,
+ *   grad_i = grad_x [ sum_j K(x, y_j) sigma_j + (n_j . grad_y K)(x, y_j) tau_j ] at x = x_i,
+ * whose components along a target normal give the normal derivatives S' and
+ * D' of Sec. 2.1 (off the surface; on it, the discrete sums of the same
+ * kernels). The expansions are those of cfmm_apply; the evaluation steps are
+ * differentiated: the near field pair by pair (grad_x K = (K'/r) d, grad_x
+ * (n . grad_y K) = -(K'/r) n - ((K'' - K'/r)/r^2)(n.d) d with d = x - y), M2P
+ * and L2P through the derivative relations of their expansion functions.
+ * The gradient is computed in FP64 (also on a MIXED plan, whose potential
+ * keeps its mixed-precision near field and L2P).
+ *   out  [nrhs][n_out] complex128 potential, or NULL;
+ *   grad [nrhs][dim][n_out] complex128, d/dx_1, .., d/dx_dim at the targets.
+ * n_out = n (targets are the sources) or the plan's separate target count.
+ * Host or device pointers, as cfmm_apply. Returns 0 or a negative status.
+ */
+int cfmm_apply_grad(cfmm_plan_t plan, const double* densities, int nrhs, double* out, double* grad);
+
+/*
+ * cfmm_apply_capture: records one cfmm_apply/*
  * cfmm_apply_capture: records one cfmm_apply of device buffers (densities,
  * out: device pointers, which must stay valid while the graph is used) into a
  * CUDA graph owned by the plan, replacing any earlier one. The plan must have

@@ -65,6 +65,8 @@ def lib():
     L.cfmm_plan.argtypes = [ci, ci, dbl, dbl, vp, vp, i64]
     L.cfmm_plan_ex.restype = vp
     L.cfmm_plan_ex.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, C.POINTER(_Opts)]
+    L.cfmm_apply_grad.restype = ci
+    L.cfmm_apply_grad.argtypes = [vp, vp, ci, vp, vp]
     L.cfmm_plan_targets.restype = vp
     L.cfmm_plan_targets.argtypes = [ci, ci, dbl, dbl, vp, vp, vp, vp, i64, vp, vp, i64, C.POINTER(_Opts)]
     L.cfmm_apply.restype = ci
@@ -209,6 +211,40 @@ class Plan:
             raise ValueError(f"densities must be [nrhs, {self.ncomp}, {self.nsrc}]")
         _check(lib().cfmm_apply(self._h, _ptr(d), nrhs, _ptr(out)))
         return out
+
+    def apply_grad(self, densities, out=None, grad=None, potential=True):
+        """cfmm_apply_grad: (potential [nrhs, nout] or None, gradient [nrhs, dim, nout]),
+        complex128, of the same kind (torch CUDA/CPU or numpy) as densities."""
+        d = densities
+        is_torch = hasattr(d, "data_ptr")
+        if is_torch:
+            import torch
+            if d.dim() == 1:
+                d = d.reshape(1, 1, -1)
+            elif d.dim() == 2:
+                d = d.reshape(d.shape[0], 1, -1) if self.ncomp == 1 else d.reshape(1, *d.shape)
+            d = d.to(torch.complex128).contiguous()
+            nrhs = d.shape[0]
+            if potential and out is None:
+                out = torch.empty((nrhs, self.nout), dtype=torch.complex128, device=d.device)
+            if grad is None:
+                grad = torch.empty((nrhs, self.dim, self.nout), dtype=torch.complex128, device=d.device)
+        else:
+            d = np.asarray(d, dtype=np.complex128)
+            if d.ndim == 1:
+                d = d.reshape(1, 1, -1)
+            elif d.ndim == 2:
+                d = d.reshape(d.shape[0], 1, -1) if self.ncomp == 1 else d.reshape(1, *d.shape)
+            d = np.ascontiguousarray(d)
+            nrhs = d.shape[0]
+            if potential and out is None:
+                out = np.empty((nrhs, self.nout), dtype=np.complex128)
+            if grad is None:
+                grad = np.empty((nrhs, self.dim, self.nout), dtype=np.complex128)
+        if d.shape[1] != self.ncomp or d.shape[2] != self.nsrc:
+            raise ValueError(f"densities must be [nrhs, {self.ncomp}, {self.nsrc}]")
+        _check(lib().cfmm_apply_grad(self._h, _ptr(d), nrhs, _ptr(out), _ptr(grad)))
+        return out, grad
 
     def capture(self, densities, out):
         """Record one apply of CUDA tensors (densities [nrhs, ncomp, n] complex128,

@@ -364,7 +364,7 @@ void near_join(cfmm_plan_s* P) {
 }
 
 // the full apply on device buffers (densities [nrhs][ncomp][n], out [nrhs][n])
-static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
+static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out, cd* grad = nullptr) {
     cudaStream_t st = P->stream;
     int64_t n = P->n;
     int ncomp = (P->slp ? 1 : 0) + (P->dlp ? 1 : 0);
@@ -372,6 +372,14 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
         P->dens_s.alloc((size_t)n * nrhs * ncomp);
         P->out_s.alloc((size_t)n * nrhs);
         P->ws_nrhs = nrhs;
+    }
+    cd* gs = nullptr;
+    if (grad) {
+        if (P->grad_nrhs < nrhs) {
+            P->grad_s.alloc((size_t)n * nrhs * P->dim);
+            P->grad_nrhs = nrhs;
+        }
+        gs = P->grad_s.get();
     }
     cd* sg = P->slp ? P->dens_s.get() : nullptr;
     cd* ta = P->dlp ? P->dens_s.get() + (P->slp ? (int64_t)n * nrhs : 0) : nullptr;
@@ -389,14 +397,22 @@ static void apply_device(cfmm_plan_s* P, const cd* dens, int nrhs, cd* out) {
         CFMM_LAUNCHED();
     }
     record(P, 1);
-    if (P->dim == 2) fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
-    else if (P->kernel == CFMM_HELMHOLTZ) helm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
-    else fmm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs);
+    if (P->dim == 2) fmm2d_apply(P, sg, ta, n, P->out_s.get(), nrhs, gs);
+    else if (P->kernel == CFMM_HELMHOLTZ) helm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs, gs);
+    else fmm3d_apply(P, sg, ta, n, P->out_s.get(), nrhs, gs);
     record(P, 8);
     cd scale = P->green ? green_scale(P->dim, P->kernel) : cd{1.0, 0.0};
     int64_t first = P->n_trg > 0 ? P->n_src : 0, nout = P->n_trg > 0 ? P->n_trg : n;
-    k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, first, nout, scale, out);
-    CFMM_LAUNCHED();
+    if (out) {
+        k_unpermute<<<g, 256, 0, st>>>(P->out_s.get(), P->perm.get(), n, first, nout, scale, out);
+        CFMM_LAUNCHED();
+    }
+    if (grad) {
+        // the gradient's dim components are rows of their own
+        dim3 gg((unsigned)((n + 255) / 256), nrhs * P->dim);
+        k_unpermute<<<gg, 256, 0, st>>>(gs, P->perm.get(), n, first, nout, scale, grad);
+        CFMM_LAUNCHED();
+    }
     record(P, 9);
     if (P->timing) {
         CFMM_CUDA(cudaEventSynchronize(P->ev[9]));
@@ -625,6 +641,36 @@ int cfmm_apply(cfmm_plan_t P, const double* densities, int nrhs, double* out) {
             CFMM_CUDA(cudaMemcpyAsync(out, d_out, dout * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
             CFMM_CUDA(cudaStreamSynchronize(P->stream));
         }
+    });
+}
+
+int cfmm_apply_grad(cfmm_plan_t P, const double* densities, int nrhs, double* out, double* grad) {
+    return guarded([&] {
+        CFMM_REQUIRE(P, CFMM_EINVAL, "null plan");
+        CFMM_REQUIRE(nrhs >= 1, CFMM_EINVAL, "nrhs must be >= 1");
+        CFMM_REQUIRE(densities && grad, CFMM_EINVAL, "densities and grad are required");
+        int ncomp = (P->slp ? 1 : 0) + (P->dlp ? 1 : 0);
+        int64_t nout = P->n_trg > 0 ? P->n_trg : P->n;
+        size_t din = (size_t)nrhs * ncomp * P->n_src * 2, dout = out ? (size_t)nrhs * nout * 2 : 0,
+               dgrad = (size_t)nrhs * P->dim * nout * 2;
+        bool dev_in = is_device_ptr(densities), dev_out = !out || is_device_ptr(out), dev_g = is_device_ptr(grad);
+        const cd* d_in = reinterpret_cast<const cd*>(densities);
+        cd* d_out = reinterpret_cast<cd*>(out);
+        cd* d_g = reinterpret_cast<cd*>(grad);
+        if (!dev_in || !dev_out || !dev_g) {
+            P->staging.alloc(din + dout + dgrad);
+            double* base = P->staging.get();
+            if (!dev_in) {
+                CFMM_CUDA(cudaMemcpyAsync(base, densities, din * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+                d_in = reinterpret_cast<const cd*>(base);
+            }
+            if (!dev_out) d_out = reinterpret_cast<cd*>(base + din);
+            if (!dev_g) d_g = reinterpret_cast<cd*>(base + din + dout);
+        }
+        apply_device(P, d_in, nrhs, d_out, d_g);
+        if (!dev_out) CFMM_CUDA(cudaMemcpyAsync(out, d_out, dout * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+        if (!dev_g) CFMM_CUDA(cudaMemcpyAsync(grad, d_g, dgrad * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+        if (!dev_out || !dev_g) CFMM_CUDA(cudaStreamSynchronize(P->stream));
     });
 }
 

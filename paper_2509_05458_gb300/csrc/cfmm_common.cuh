@@ -309,6 +309,8 @@ struct cfmm_plan_s {
     int maxP = 0;
     // workspaces (grown on demand)
     cfmm::DevBuf<cd> mpole, local, dens_s, out_s, m2l_part;
+    cfmm::DevBuf<cd> grad_s;         // sorted target gradient [nrhs][dim][n] (cfmm_apply_grad)
+    int grad_nrhs = 0;
     cfmm::DevBuf<double> staging;
     int ws_nrhs = 0;
     // diagnostics

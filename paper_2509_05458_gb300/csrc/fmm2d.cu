@@ -749,6 +749,104 @@ __global__ void k_eval(ExpArgs A, const int* __restrict__ leaves, const int* __r
 }
 
 // ---------------------------------------------------------------------------
+// Target gradients of M2P (List 3) and L2P (FP64), added to g [rhs][2][n]:
+// d/dx1 = d/dzeta + d/deta, d/dx2 = i (d/dzeta - d/deta), with
+//   Laplace  u = M0 log(zeta eta)/2 + sum Mp_n eta^-n + Mm_n zeta^-n:
+//            d/dzeta = M0/(2 zeta) - sum n Mm_n zeta^-n-1 (likewise eta);
+//            u = L0 + sum Lp_n zeta^n + Lm_n eta^n: d/dzeta = sum n Lp_n zeta^n-1;
+//   Helmholtz d/dzeta T_n = (kappa/2) T_{n-1}, d/deta T_n = -(kappa/2) T_{n+1}
+//            for T = S (M2P) and G (L2P).
+// ---------------------------------------------------------------------------
+template <int KER>
+__global__ void k_eval_grad(ExpArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
+                            const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
+                            cd* __restrict__ g, int maxP) {
+    extern __shared__ cd sm[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    cd* coef = sm;                                  // 2*maxP+1
+    cd* rows = sm + 2 * maxP + 1;                   // per thread: 2*maxP+3 (Helmholtz rows n = -P-1..P+1)
+    int s0 = A.bst[b], s1 = A.ben[b];
+    const double kh = 0.5 * A.kappa;
+    for (int t0 = s0; t0 < s1; t0 += blockDim.x) {
+        int i = t0 + threadIdx.x;
+        bool valid = i < s1;
+        cd x0 = {0, 0}, x1 = {0, 0};
+        if (valid) {
+            x0 = cd{A.xr[i], A.xi[i]};
+            x1 = cd{A.xr[A.n + i], A.xi[A.n + i]};
+        }
+        cd dz = {0, 0}, de = {0, 0};
+        cd* row = rows + (size_t)threadIdx.x * (2 * maxP + 3);
+        for (int q = l3off[b]; q < l3off[b + 1]; ++q) {
+            int s = l3[q];
+            int Ps = A.Plev[A.blevel[s]];
+            __syncthreads();
+            const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
+            for (int c = threadIdx.x; c < 2 * Ps + 1; c += blockDim.x) coef[c] = m[c];
+            __syncthreads();
+            if (!valid) continue;
+            cd z, e;
+            zeta_eta(x0 - cd{A.cre[2 * s], A.cim[2 * s]}, x1 - cd{A.cre[2 * s + 1], A.cim[2 * s + 1]}, z, e);
+            if (KER == CFMM_LAPLACE) {
+                cd iz = cinv(z), ie = cinv(e);
+                dz += 0.5 * (coef[0] * iz);
+                de += 0.5 * (coef[0] * ie);
+                cd zp = iz * iz, ep = ie * ie;   // zeta^-n-1
+                for (int nn = 1; nn <= Ps; ++nn) {
+                    dz -= (double)nn * (coef[Ps + nn] * zp);
+                    de -= (double)nn * (coef[nn] * ep);
+                    zp = zp * iz;
+                    ep = ep * ie;
+                }
+            } else {
+                cyl_row(1, z, e, A.kappa, Ps, row);          // S_n, n = -Ps-1..Ps+1
+                for (int nn = -Ps; nn <= Ps; ++nn) {
+                    cd c = coef[Ps + nn];
+                    dz = cmac(dz, c, row[nn + Ps + 1 - 1]);
+                    de = cmac(de, c, row[nn + Ps + 1 + 1]);
+                }
+            }
+        }
+        __syncthreads();
+        const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+        for (int c = threadIdx.x; c < 2 * P + 1; c += blockDim.x) coef[c] = lc[c];
+        __syncthreads();
+        if (!valid) continue;
+        cd z, e;
+        zeta_eta(x0 - cd{A.cre[2 * b], A.cim[2 * b]}, x1 - cd{A.cre[2 * b + 1], A.cim[2 * b + 1]}, z, e);
+        cd lz = {0, 0}, le = {0, 0};
+        if (KER == CFMM_LAPLACE) {
+            cd zp = {1, 0}, ep = {1, 0};   // zeta^n-1
+            for (int nn = 1; nn <= P; ++nn) {
+                lz += (double)nn * (coef[nn] * zp);
+                le += (double)nn * (coef[P + nn] * ep);
+                zp = zp * z;
+                ep = ep * e;
+            }
+        } else {
+            cyl_row(0, z, e, A.kappa, P, row);               // G_n, n = -P-1..P+1
+            for (int nn = -P; nn <= P; ++nn) {
+                cd c = coef[P + nn];
+                lz = cmac(lz, c, row[nn + P + 1 - 1]);
+                le = cmac(le, c, row[nn + P + 1 + 1]);
+            }
+        }
+        if (KER == CFMM_LAPLACE) {
+            dz += lz;
+            de += le;
+        } else {
+            dz = kh * (dz + lz);
+            de = (-kh) * (de + le);
+        }
+        cd* go = g + (int64_t)rhs * 2 * A.n + i;
+        go[0] += dz + de;
+        go[A.n] += mul_i(dz - de);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // L2P in complex64 arithmetic (mixed precision). With zeta~ = zeta/rho_b,
 // eta~ = eta/rho_b (rho_b = sqrt(2)/2 w, the leaf's radius):
 //   Laplace    u = L^_0 + sum L^_n zeta~^n + L^'_n eta~^n,  L^_n = L_n rho_b^n
@@ -1190,12 +1288,14 @@ void fmm2d_setup(cfmm_plan_s* P) {
                    (const void*)k_l2l<CFMM_LAPLACE>, (const void*)k_l2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l<CFMM_LAPLACE>, (const void*)k_m2l<CFMM_HELMHOLTZ>,
                    (const void*)k_m2l_chunk,
-                   (const void*)k_eval<CFMM_LAPLACE>, (const void*)k_eval<CFMM_HELMHOLTZ>})
+                   (const void*)k_eval<CFMM_LAPLACE>, (const void*)k_eval<CFMM_HELMHOLTZ>,
+                   (const void*)k_eval_grad<CFMM_LAPLACE>, (const void*)k_eval_grad<CFMM_HELMHOLTZ>})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
 }
 
 template <int KER>
-static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
+static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs,
+                    cd* g) {
     TreeDev& T = P->tree;
     cudaStream_t st = P->stream;
     auto rec = [&](int i) {
@@ -1207,6 +1307,9 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
         for (int i = 2; i <= 6; ++i) rec(i);
         launch_p2p(2, KER, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
                    T.lent[0].get(), u, nrhs, false, st, P->precision == CFMM_MIXED);
+        if (g)
+            launch_p2p_grad(2, KER, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
+                            T.lent[0].get(), g, nrhs, st);
         rec(7);
         rec(8);
         return;
@@ -1221,8 +1324,14 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
               S->dPlev.get(), S->exp_off.get(), S->ncoef};
     int maxP = S->maxP;
     // (3) P2P over List 1 (writes u) on the side stream, beside the far field
-    launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), P->precision == CFMM_MIXED);
+    {
+        cudaStream_t ns = near_fork(P);
+        launch_p2p(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+                   T.loff[0].get(), T.lent[0].get(), u, nrhs, false, ns, P->precision == CFMM_MIXED);
+        if (g)
+            launch_p2p_grad(2, KER, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+                            T.loff[0].get(), T.lent[0].get(), g, nrhs, ns);
+    }
     near_launched(P);
     // (1) P2M (shared memory sized by the leaves' orders)
     {
@@ -1319,25 +1428,31 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
     {
         // with the plan's rows, L2P needs no per-thread row space
         size_t smem = sizeof(cd) * ((size_t)(2 * maxP + 1) + (S->lrow.get() ? 0 : (size_t)kExpThreads * (maxP + 2)));
-        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
+        dim3 gr((unsigned)S->leaves_l0.size(), nrhs);
         bool l2p32 = P->precision == CFMM_MIXED && S->maxP_leaf <= kL2p2fMaxP;
-        k_eval<KER><<<g, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc,
-                                                 u, maxP, S->lrow.get(), S->RL, l2p32 ? 0 : 1);
+        k_eval<KER><<<gr, kExpThreads, smem, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc,
+                                                  u, maxP, S->lrow.get(), S->RL, l2p32 ? 0 : 1);
         CFMM_LAUNCHED();
-        if (l2p32 && g.x) {
-            k_l2p2f<KER><<<g, kExpThreads, sizeof(cf) * (2 * S->maxP_leaf + 1), st>>>(A, S->d_leaves_l0.get(), lc,
-                                                                                       u, P->W);
+        if (l2p32 && gr.x) {
+            k_l2p2f<KER><<<gr, kExpThreads, sizeof(cf) * (2 * S->maxP_leaf + 1), st>>>(A, S->d_leaves_l0.get(), lc,
+                                                                                        u, P->W);
+            CFMM_LAUNCHED();
+        }
+        if (g && gr.x) {
+            size_t gsm = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)kExpThreads * (2 * maxP + 3));
+            k_eval_grad<KER><<<gr, kExpThreads, gsm, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
+                                                            mp, lc, g, maxP);
             CFMM_LAUNCHED();
         }
     }
     rec(8);
 }
 
-void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
+void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs, cd* g) {
     Fmm2dState* S = state(P);
     CFMM_REQUIRE(S, CFMM_EINVAL, "plan has no 2D state");
-    if (P->kernel == CFMM_LAPLACE) apply_t<CFMM_LAPLACE>(P, S, sigma, tau, dstride, u, nrhs);
-    else apply_t<CFMM_HELMHOLTZ>(P, S, sigma, tau, dstride, u, nrhs);
+    if (P->kernel == CFMM_LAPLACE) apply_t<CFMM_LAPLACE>(P, S, sigma, tau, dstride, u, nrhs, g);
+    else apply_t<CFMM_HELMHOLTZ>(P, S, sigma, tau, dstride, u, nrhs, g);
 }
 
 }  // namespace cfmm

@@ -231,6 +231,112 @@ __device__ cd eval_series(bool reg, cd a0, cd a1, cd a2, int P, const cd* coef) 
     return acc;
 }
 
+// Target gradient of a solid-harmonic series: with d+ U_n^m = -U_{n-1}^{m-1}/2,
+// d- U_n^m = U_{n-1}^{m+1}/2, dz U_n^m = U_{n-1}^m (L2P, reg) and d+ T_n^m =
+// -T_{n+1}^{m-1}/2, d- T_n^m = T_{n+1}^{m+1}/2, dz T_n^m = -T_{n+1}^m (M2P),
+// the derivatives of sum c_n^m H_n^m are series in H_{n'}^{m'} with shifted
+// coefficients; one pass over H_{n'}^{m'}, n' <= Q (Q = P - 1 for L2P, P + 1
+// for M2P), accumulates (dz, d+, d-). grad = (d+ + d-, i (d+ - d-), dz).
+__device__ void eval_series_grad(bool reg, cd a0, cd a1, cd a2, int P, const cd* coef, cd& Dz, cd& Dp, cd& Dm) {
+    cd xp = a0 + mul_i(a1), xm = a0 - mul_i(a1), z = a2;
+    cd r2 = xp * xm + z * z;
+    cd ir2 = {0, 0}, irho = {0, 0};
+    if (!reg) {
+        ir2 = cinv(r2);
+        irho = cinv(csqrt_p(r2));
+    }
+    int Q = reg ? P - 1 : P + 1;
+    int sh = reg ? 1 : -1;                       // coefficient order n' + sh
+    auto c = [&](int n, int m) -> cd {
+        if (n < 0 || n > P || m > n || -m > n) return cd{0, 0};
+        return coef[nm_idx(n, m)];
+    };
+    Dz = Dp = Dm = cd{0, 0};
+    auto add = [&](int n, int mi, cd h) {
+        int k = n + sh;
+        Dz += h * (reg ? c(k, mi) : -c(k, mi));
+        Dp += h * (-0.5 * c(k, mi + 1));
+        Dm += h * (0.5 * c(k, mi - 1));
+    };
+    if (Q < 0) return;
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        cd xs = sgn ? xm : xp;
+        cd d = reg ? cd{1, 0} : irho;
+        for (int m = 0; m <= Q; ++m) {
+            if (m > 0) d = reg ? d * (-0.5 * xs) * (1.0 / m) : d * (-(2.0 * m - 1.0)) * (xs * ir2);
+            if (sgn == 1 && m == 0) continue;
+            double sg = (sgn && (m & 1)) ? -1.0 : 1.0;
+            int mi = sgn ? -m : m;
+            add(m, mi, sg * d);
+            if (m + 1 > Q) continue;
+            cd p2 = d;
+            cd p1 = reg ? z * d : (2.0 * m + 1.0) * (z * ir2) * d;
+            add(m + 1, mi, sg * p1);
+            for (int n = m + 2; n <= Q; ++n) {
+                cd cur;
+                if (reg) cur = ((2.0 * n - 1.0) * (z * p1) - r2 * p2) * (1.0 / ((n - m) * (double)(n + m)));
+                else cur = ((2.0 * n - 1.0) * (z * p1) - ((double)(n - 1) * (n - 1) - (double)m * m) * p2) * ir2;
+                add(n, mi, sg * cur);
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+}
+
+// target gradients of M2P (List 3) and L2P, FP64, added to g [rhs][3][n]
+__global__ void k_eval3_grad(Exp3Args A, const int* __restrict__ leaves, const int* __restrict__ l3off,
+                             const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
+                             cd* __restrict__ g) {
+    extern __shared__ cd sm[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    cd* coef = sm;
+    int s0 = A.bst[b], s1 = A.ben[b];
+    for (int t0 = s0; t0 < s1; t0 += blockDim.x) {
+        int i = t0 + threadIdx.x;
+        bool valid = i < s1;
+        cd x[3] = {{0, 0}, {0, 0}, {0, 0}};
+        if (valid) load3(A.xr, A.xi, A.n, i, x);
+        cd Dz = {0, 0}, Dp = {0, 0}, Dm = {0, 0};
+        for (int q = l3off[b]; q < l3off[b + 1]; ++q) {
+            int s = l3[q];
+            int Ps = A.Plev[A.blevel[s]];
+            __syncthreads();
+            const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
+            for (int c = threadIdx.x; c < (Ps + 1) * (Ps + 1); c += blockDim.x) coef[c] = m[c];
+            __syncthreads();
+            if (valid) {
+                cd d[3];
+                for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * s + a], A.cim[3 * s + a]};
+                cd z_, p_, m_;
+                eval_series_grad(false, d[0], d[1], d[2], Ps, coef, z_, p_, m_);
+                Dz += z_;
+                Dp += p_;
+                Dm += m_;
+            }
+        }
+        __syncthreads();
+        const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+        for (int c = threadIdx.x; c < (P + 1) * (P + 1); c += blockDim.x) coef[c] = lc[c];
+        __syncthreads();
+        if (valid) {
+            cd d[3];
+            for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+            cd z_, p_, m_;
+            eval_series_grad(true, d[0], d[1], d[2], P, coef, z_, p_, m_);
+            Dz += z_;
+            Dp += p_;
+            Dm += m_;
+            cd* go = g + (int64_t)rhs * 3 * A.n + i;
+            go[0] += Dp + Dm;
+            go[A.n] += mul_i(Dp - Dm);
+            go[2 * A.n] += Dz;
+        }
+    }
+}
+
 __global__ void k_eval3(Exp3Args A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                         const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
                         cd* __restrict__ u, int maxP, int do_l2p) {
@@ -380,12 +486,12 @@ void fmm3d_setup(cfmm_plan_s* P) {
         CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
-    for (auto f : {(const void*)k_point_to_exp3, (const void*)k_eval3})
+    for (auto f : {(const void*)k_point_to_exp3, (const void*)k_eval3, (const void*)k_eval3_grad})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax3Smem));
     S->tr = lap3_tr_create(P, maxP);
 }
 
-void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
+void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs, cd* g) {
     Fmm3dState* S = state3(P);
     CFMM_REQUIRE(S, CFMM_EINVAL, "plan has no 3D state");
     TreeDev& T = P->tree;
@@ -402,6 +508,9 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
         for (int i = 2; i <= 6; ++i) rec(i);
         launch_p2p(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
                    T.lent[0].get(), u, nrhs, false, st, mixed);
+        if (g)
+            launch_p2p_grad(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(),
+                            T.loff[0].get(), T.lent[0].get(), g, nrhs, st);
         rec(7);
         rec(8);
         return;
@@ -421,8 +530,14 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
         return sizeof(cd) * ((size_t)(maxP + 1) * (maxP + 1) + (size_t)chunk * nt + (size_t)chunk * 6);
     };
     // (3) P2P (writes u) on the side stream, beside the far field
-    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed);
+    {
+        cudaStream_t ns = near_fork(P);
+        launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+                   T.loff[0].get(), T.lent[0].get(), u, nrhs, false, ns, mixed);
+        if (g)
+            launch_p2p_grad(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(),
+                            T.end.get(), T.loff[0].get(), T.lent[0].get(), g, nrhs, ns);
+    }
     near_launched(P);
     // (1) P2M (single layer: one lane per harmonic column; complex64 products
     // with FP64 sums in mixed precision)
@@ -468,12 +583,17 @@ void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride
     near_join(P);   // the near field has written u
     // (5) M2P, (8) L2P (complex64 in mixed precision)
     {
-        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
-        k_eval3<<<g, kExp3Threads, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
+        dim3 gr((unsigned)S->leaves_l0.size(), nrhs);
+        k_eval3<<<gr, kExp3Threads, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
                                                           mp, lc, u, maxP, mixed ? 0 : 1);
         CFMM_LAUNCHED();
         if (mixed) lap3_l2p32(S->tr, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
                               S->exp_off.get(), S->ncoef, lc, u, nrhs);
+        if (g && gr.x) {
+            k_eval3_grad<<<gr, kExp3Threads, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
+                A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, g);
+            CFMM_LAUNCHED();
+        }
     }
     rec(8);
 }

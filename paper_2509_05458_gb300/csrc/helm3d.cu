@@ -652,6 +652,110 @@ __device__ cd eval_wave(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const
     return acc;
 }
 
+// Target gradient of sum c_n^m F_n Z_n^m (F_n = f_n(k rho)/rho^n, f = j or h):
+// grad(F_n Z) = F_n grad Z - k F_{n+1} Z x with dz Z_n^m = g3 Z_{n-1}^m,
+// d+ Z_n^m = -gp Z_{n-1}^{m-1}, d- Z_n^m = gm Z_{n-1}^{m+1} (the tables g3, gp,
+// gm of the double layer), so in one pass over Z_{n'}^{m'}, n' <= P (F given
+// for n <= P + 1):
+//   Dz = sum g3(n'+1, m') c_{n'+1}^{m'} F_{n'+1} Z,  D+ = sum -gp(n'+1, m'+1)
+//   c_{n'+1}^{m'+1} F_{n'+1} Z,  D- = sum gm(n'+1, m'-1) c_{n'+1}^{m'-1} F_{n'+1} Z,
+//   B = sum c_{n'}^{m'} F_{n'+1} Z;
+// grad = (D+ + D- - k x1 B, i (D+ - D-) - k x2 B, Dz - k x3 B).
+__device__ void eval_wave_grad(ZCoef zc, cd a0, cd a1, cd a2, int P, const cd* F, const cd* coef, cd& Dz, cd& Dp,
+                               cd& Dm, cd& B) {
+    cd xp = a0 + mul_i(a1), xm = a0 - mul_i(a1), z = a2;
+    cd r2 = xp * xm + z * z;
+    auto c = [&](int n, int m) -> cd {
+        if (n > P || m > n || -m > n) return cd{0, 0};
+        return coef[nmi(n, m)];
+    };
+    Dz = Dp = Dm = B = cd{0, 0};
+    auto add = [&](int n, int mi, cd zv) {
+        cd t = F[n + 1] * zv;
+        B = cmac(B, t, coef[nmi(n, mi)]);
+        if (n + 1 > P) return;
+        int k1 = n + 1;
+        Dz = cmac(Dz, t, __ldg(zc.g3 + nmi(k1, mi)) * c(k1, mi));
+        if (mi + 1 <= k1) Dp = cmac(Dp, t, (-__ldg(zc.gp + nmi(k1, mi + 1))) * c(k1, mi + 1));
+        if (mi - 1 >= -k1) Dm = cmac(Dm, t, __ldg(zc.gm + nmi(k1, mi - 1)) * c(k1, mi - 1));
+    };
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        cd xs = sgn ? xm : xp;
+        cd d = {1, 0};
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) d = (-__ldg(zc.dg + m)) * (xs * d);
+            if (sgn == 1 && m == 0) continue;
+            int mi = sgn ? -m : m;
+            add(m, mi, d);
+            if (m + 1 > P) continue;
+            cd p2 = d, p1 = __ldg(zc.s21 + m) * (z * d);
+            add(m + 1, mi, p1);
+            for (int n = m + 2; n <= P; ++n) {
+                int k = nmi(n, m);
+                cd cur = zc.A[k] * (z * p1) - zc.B[k] * (r2 * p2);
+                add(n, mi, cur);
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+}
+
+// target gradients of M2P (List 3, S waves) and L2P (R waves), FP64, added to
+// g [rhs][3][n]
+__global__ void k_eval3h_grad(Exp3hArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
+                              const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
+                              cd* __restrict__ g) {
+    extern __shared__ cd sm[];
+    int b = leaves[blockIdx.x];
+    int rhs = blockIdx.y;
+    int P = A.Plev[A.blevel[b]];
+    int nc = (P + 1) * (P + 1);
+    cd* coef = sm;
+    int s0 = A.bst[b], s1 = A.ben[b];
+    cd F[kH3MaxP + 3];
+    for (int t0 = s0; t0 < s1; t0 += blockDim.x) {
+        int i = t0 + threadIdx.x;
+        bool valid = i < s1;
+        cd x[3] = {{0, 0}, {0, 0}, {0, 0}};
+        if (valid) load3(A.xr, A.xi, A.n, i, x);
+        cd G[3] = {{0, 0}, {0, 0}, {0, 0}};
+        auto accum = [&](const cd* d, int Pq) {
+            cd Dz, Dp, Dm, B;
+            eval_wave_grad(A.zc, d[0], d[1], d[2], Pq, F, coef, Dz, Dp, Dm, B);
+            G[0] += Dp + Dm - A.kappa * (d[0] * B);
+            G[1] += mul_i(Dp - Dm) - A.kappa * (d[1] * B);
+            G[2] += Dz - A.kappa * (d[2] * B);
+        };
+        for (int q = l3off[b]; q < l3off[b + 1]; ++q) {
+            int s = l3[q];
+            int Ps = A.Plev[A.blevel[s]];
+            __syncthreads();
+            const cd* m = mp + (int64_t)rhs * A.ncoef + A.eoff[s];
+            for (int c = threadIdx.x; c < (Ps + 1) * (Ps + 1); c += blockDim.x) coef[c] = m[c];
+            __syncthreads();
+            if (valid) {
+                cd d[3];
+                for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * s + a], A.cim[3 * s + a]};
+                radial_seq(false, A.kappa, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], Ps + 1, F);
+                accum(d, Ps);
+            }
+        }
+        __syncthreads();
+        const cd* lc = loc + (int64_t)rhs * A.ncoef + A.eoff[b];
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) coef[c] = lc[c];
+        __syncthreads();
+        if (valid) {
+            cd d[3];
+            for (int a = 0; a < 3; ++a) d[a] = x[a] - cd{A.cre[3 * b + a], A.cim[3 * b + a]};
+            radial_seq(true, A.kappa, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], P + 1, F);
+            accum(d, P);
+            cd* go = g + (int64_t)rhs * 3 * A.n + i;
+            for (int a = 0; a < 3; ++a) go[(int64_t)a * A.n] += G[a];
+        }
+    }
+}
+
 // M2P over List 3 (S waves) and L2P (R waves); one thread per target.
 __global__ void k_eval3h(Exp3hArgs A, const int* __restrict__ leaves, const int* __restrict__ l3off,
                          const int* __restrict__ l3, const cd* __restrict__ mp, const cd* __restrict__ loc,
@@ -1727,11 +1831,12 @@ void helm3d_setup(cfmm_plan_s* P) {
         CFMM_CUDA(cudaMemcpyAsync(S->d_p2l_boxes.get(), boxes.data(), sizeof(int) * boxes.size(),
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
-    for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp<false>, (const void*)k_eval3h, (const void*)k_tr3h})
+    for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp<false>, (const void*)k_eval3h, (const void*)k_tr3h,
+                   (const void*)k_eval3h_grad})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
 }
 
-void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs) {
+void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstride, cd* u, int nrhs, cd* g) {
     Helm3dState* S = state(P);
     CFMM_REQUIRE(S, CFMM_EINVAL, "plan has no 3D Helmholtz state");
     TreeDev& T = P->tree;
@@ -1746,6 +1851,9 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         for (int i = 2; i <= 6; ++i) rec(i);
         launch_p2p(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(), T.loff[0].get(),
                    T.lent[0].get(), u, nrhs, false, st, mixed);
+        if (g)
+            launch_p2p_grad(3, P->kernel, K, T.d_leaf_boxes.get(), T.nleaves, T.start.get(), T.end.get(),
+                            T.loff[0].get(), T.lent[0].get(), g, nrhs, st);
         rec(7);
         rec(8);
         return;
@@ -1763,8 +1871,14 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                 S->exp_off.get(), S->ncoef, P->kappa, zc};
     int maxP = S->maxP;
     // (3) P2P (writes u) on the side stream, beside the far field
-    launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
-               T.loff[0].get(), T.lent[0].get(), u, nrhs, false, near_fork(P), mixed, T.level.get(), P->W, P->sep);
+    {
+        cudaStream_t ns = near_fork(P);
+        launch_p2p(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(), T.end.get(),
+                   T.loff[0].get(), T.lent[0].get(), u, nrhs, false, ns, mixed, T.level.get(), P->W, P->sep);
+        if (g)
+            launch_p2p_grad(3, P->kernel, K, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), T.start.get(),
+                            T.end.get(), T.loff[0].get(), T.lent[0].get(), g, nrhs, ns);
+    }
     near_launched(P);
     auto p2x_smem = [&](int PL, int& chunk) {
         size_t nc = (size_t)(PL + 1) * (PL + 1);
@@ -1938,12 +2052,17 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     near_join(P);   // the near field has written u
     // (5) M2P, (8) L2P (complex64 in mixed precision)
     {
-        dim3 g((unsigned)S->leaves_l0.size(), nrhs);
-        k_eval3h<<<g, 128, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
+        dim3 gr((unsigned)S->leaves_l0.size(), nrhs);
+        k_eval3h<<<gr, 128, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
             A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, u, mixed ? 0 : 1);
         CFMM_LAUNCHED();
         if (mixed) launch_l2p3f(TB, true, P, S->d_leaves_l0.get(), (int)S->leaves_l0.size(), maxP, S->dPlev.get(),
                                 S->exp_off.get(), S->ncoef, lc, u, nrhs);
+        if (g && gr.x) {
+            k_eval3h_grad<<<gr, 128, sizeof(cd) * (size_t)(maxP + 1) * (maxP + 1), st>>>(
+                A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(), mp, lc, g);
+            CFMM_LAUNCHED();
+        }
     }
     rec(8);
 }

@@ -38,6 +38,9 @@ void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int n
                 const int* ben, const int* l1off, const int* l1, cd* out, int nrhs, bool add, cudaStream_t st,
                 bool mixed = false, const int* blevel = nullptr, double W = 0.0, int sep = 1);
 void launch_direct(int dim, int ker, const KParams& K, cd* out, int nrhs, cudaStream_t st, bool mixed = false);
+// near-field target gradient over List 1 in FP64: g = sorted [nrhs][dim][n], overwritten
+void launch_p2p_grad(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
+                     const int* ben, const int* l1off, const int* l1, cd* g, int nrhs, cudaStream_t st);
 
 // tree construction (tree.cu)
 void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double* nre, const double* nim,
@@ -51,7 +54,9 @@ void build_plan_lists(cfmm_plan_s* P);
 void fmm2d_presetup(cfmm_plan_s* P);
 void fmm2d_setup(cfmm_plan_s* P);
 void fmm2d_release(cfmm_plan_s* P);
-void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+// g: sorted target gradient [nrhs][dim][n] (overwritten) or NULL
+void fmm2d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs,
+                 cd* g = nullptr);
 
 // Green's function constants of CFMM_GREEN_SCALE: -1/(2 pi) (2D Laplace),
 // i/4 (2D Helmholtz), 1/(4 pi) (3D Laplace and Helmholtz)
@@ -75,12 +80,16 @@ int direct_noalloc(int dim, int kernel, double k, const double* src_re, const do
 // 3D Laplace expansions (fmm3d.cu)
 void fmm3d_setup(cfmm_plan_s* P);
 void fmm3d_release(cfmm_plan_s* P);
-void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+// g: sorted target gradient [nrhs][dim][n] (overwritten) or NULL
+void fmm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs,
+                 cd* g = nullptr);
 
 // 3D Helmholtz expansions (helm3d.cu)
 void helm3d_setup(cfmm_plan_s* P);
 void helm3d_release(cfmm_plan_s* P);
-void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs);
+// g: sorted target gradient [nrhs][dim][n] (overwritten) or NULL
+void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dens_stride, cd* out_sorted, int nrhs,
+                 cd* g = nullptr);
 int nterms_helm3d(int k, double eps, double kappa, double w);
 // 3D Laplace point-and-shoot translations (helm3d.cu, used by fmm3d.cu)
 // largest 3D Helmholtz expansion order: the limit of the translation tables

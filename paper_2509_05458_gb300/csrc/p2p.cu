@@ -148,6 +148,64 @@ __device__ __forceinline__ void pair_kernel(const double* dr, const double* di, 
     }
 }
 
+// grad_x of K(x, y) sg + (n . grad_y K)(x, y) ta for one pair (d = x - y != 0),
+// added to g[0..DIM-1] (Sec. 2.1: S' and D' are its normal components). With
+// K = K(r): grad_x K = (K'/r) d and grad_x (n . grad_y K) = -(K'/r) n -
+// ((K'' - K'/r)/r^2) (n.d) d.
+template <int DIM, int KER>
+__device__ __forceinline__ void pair_grad(const double* dr, const double* di, const double* nr, const double* ni,
+                                          cd sg, cd ta, bool slp, bool dlp, double kappa, cd* g) {
+    cd d[DIM];
+    cd r2 = {0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        d[a] = cd{dr[a], di[a]};
+        r2 += d[a] * d[a];
+    }
+    cd a1, a2;   // K'/r and (K'' - K'/r)/r^2
+    if (DIM == 2 && KER == CFMM_LAPLACE) {
+        cd ir2 = cinv(r2);
+        a1 = ir2;
+        a2 = -2.0 * (ir2 * ir2);
+    } else if (DIM == 2) {
+        cd r = csqrt_p(r2);
+        cd h0, h1;
+        hankel01(kappa * r, &h0, &h1);
+        cd ir = cinv(r), ir2 = cinv(r2);
+        a1 = (-kappa) * (h1 * ir);
+        a2 = (-kappa * kappa * h0 + (2.0 * kappa) * (h1 * ir)) * ir2;
+    } else if (KER == CFMM_LAPLACE) {
+        cd r = csqrt_p(r2);
+        cd ir = cinv(r), ir2 = cinv(r2);
+        cd ir3 = ir * ir2;
+        a1 = -ir3;
+        a2 = 3.0 * (ir3 * ir2);
+    } else {
+        cd r = csqrt_p(r2);
+        cd ir = cinv(r), ir2 = cinv(r2);
+        cd e = cexp_i(kappa * r);
+        cd ikr = mul_i(kappa * r);
+        cd ir3 = ir * ir2;
+        a1 = (e * (ikr - cd{1.0, 0.0})) * ir3;
+        a2 = (e * (cd{3.0, 0.0} - 3.0 * ikr - (kappa * kappa) * r2)) * (ir3 * ir2);
+    }
+    cd cs = slp ? a1 * sg : cd{0, 0};
+    cd cn = {0, 0}, cdd = {0, 0};
+    if (dlp) {
+        cd nd = {0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nd += cd{nr[a], ni[a]} * d[a];
+        cn = -(a1 * ta);
+        cdd = -(a2 * (nd * ta));
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        cd v = (cs + cdd) * d[a];
+        if (dlp) v += cn * cd{nr[a], ni[a]};
+        g[a] += v;
+    }
+}
+
 struct SrcTile {
     double re[kP2PChunk][3];
     double im[kP2PChunk][3];
@@ -237,6 +295,76 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(KParams K, const int* __res
             accumulate_sources<DIM, KER>(S, K, rhs, bst[a], ben[a], ti, tvalid, xr, xim, acc, split);
         }
         finish_target<DIM, KER>(acc, red, tl, split, tvalid, out + (int64_t)rhs * K.n_trg + ti, add != 0);
+    }
+}
+
+// near-field gradient over List 1 (FP64); g = sorted gradient [rhs][DIM][n]
+// (overwritten). Same staging and fixed-order combination as k_p2p.
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_grad(KParams K, const int* __restrict__ leaf_boxes,
+                                                          const int* __restrict__ bst, const int* __restrict__ ben,
+                                                          const int* __restrict__ l1off, const int* __restrict__ l1,
+                                                          cd* __restrict__ g) {
+    __shared__ SrcTile S;
+    __shared__ cd red[kP2PThreads];
+    const int64_t n = K.n_src;
+    int b = leaf_boxes[blockIdx.x];
+    int rhs = blockIdx.y;
+    int tl = threadIdx.x % kP2PTargets, split = threadIdx.x / kP2PTargets;
+    int ts = bst[b], te = ben[b];
+    for (int t0 = ts; t0 < te; t0 += kP2PTargets) {
+        int ti = t0 + tl;
+        bool tvalid = ti < te;
+        double xr[DIM], xim[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            xr[a] = tvalid ? K.trg_re[a * K.n_trg + ti] : 0.0;
+            xim[a] = tvalid ? K.trg_im[a * K.n_trg + ti] : 0.0;
+        }
+        cd acc[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[a] = cd{0.0, 0.0};
+        for (int q = l1off[b]; q < l1off[b + 1]; ++q) {
+            int src = l1[q];
+            int s0 = bst[src], s1 = ben[src];
+            for (int c0 = s0; c0 < s1; c0 += kP2PChunk) {
+                int cn = min(kP2PChunk, s1 - c0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < cn; j += blockDim.x) {
+                    int gi = c0 + j;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        S.re[j][a] = K.src_re[a * n + gi];
+                        S.im[j][a] = K.src_im[a * n + gi];
+                        if (K.dlp) {
+                            S.nr[j][a] = K.nrm_re[a * n + gi];
+                            S.ni[j][a] = K.nrm_im[a * n + gi];
+                        }
+                    }
+                    if (K.slp) S.sg[j] = K.sigma[(int64_t)rhs * K.dens_stride + gi];
+                    if (K.dlp) S.ta[j] = K.tau[(int64_t)rhs * K.dens_stride + gi];
+                }
+                __syncthreads();
+                if (!tvalid) continue;
+                for (int j = split; j < cn; j += kP2PSplit) {
+                    double dr[DIM], di[DIM];
+                    bool zero = true;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        dr[a] = xr[a] - S.re[j][a];
+                        di[a] = xim[a] - S.im[j][a];
+                        zero = zero && dr[a] == 0.0 && di[a] == 0.0;
+                    }
+                    if (zero) continue;
+                    pair_grad<DIM, KER>(dr, di, S.nr[j], S.ni[j], K.slp ? S.sg[j] : cd{0, 0},
+                                        K.dlp ? S.ta[j] : cd{0, 0}, K.slp, K.dlp, K.kappa, acc);
+                }
+            }
+        }
+        cd* gout = g + (int64_t)rhs * DIM * K.n_trg + ti;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            finish_target<DIM, KER>(acc[a], red, tl, split, tvalid, gout + (int64_t)a * K.n_trg, false);
     }
 }
 
@@ -827,6 +955,23 @@ void launch_p2p(int dim, int ker, const KParams& K, const int* leaf_boxes, int n
     else if (dim == 2) launch_p2p_t<2, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
     else if (ker == CFMM_LAPLACE) launch_p2p_t<3, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
     else launch_p2p_t<3, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, out, nrhs, add, mixed, st);
+}
+
+template <int DIM, int KER>
+static void launch_p2p_grad_t(const KParams& K, const int* leaf_boxes, int nleaves, const int* bst, const int* ben,
+                              const int* l1off, const int* l1, cd* g, int nrhs, cudaStream_t st) {
+    if (nleaves == 0) return;
+    dim3 grid(nleaves, nrhs);
+    k_p2p_grad<DIM, KER><<<grid, kP2PThreads, 0, st>>>(K, leaf_boxes, bst, ben, l1off, l1, g);
+    CFMM_LAUNCHED();
+}
+
+void launch_p2p_grad(int dim, int ker, const KParams& K, const int* leaf_boxes, int nleaves, const int* bst,
+                     const int* ben, const int* l1off, const int* l1, cd* g, int nrhs, cudaStream_t st) {
+    if (dim == 2 && ker == CFMM_LAPLACE) launch_p2p_grad_t<2, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, g, nrhs, st);
+    else if (dim == 2) launch_p2p_grad_t<2, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, g, nrhs, st);
+    else if (ker == CFMM_LAPLACE) launch_p2p_grad_t<3, CFMM_LAPLACE>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, g, nrhs, st);
+    else launch_p2p_grad_t<3, CFMM_HELMHOLTZ>(K, leaf_boxes, nleaves, bst, ben, l1off, l1, g, nrhs, st);
 }
 
 template <int DIM, int KER>
