@@ -101,16 +101,17 @@ def gmres(matvec, b, tol=1e-10, restart=60, maxiter=2000):
             H[k + 1, k] = float(torch.linalg.vector_norm(w))
             if abs(H[k + 1, k]) > 0:
                 V.append(w / H[k + 1, k])
+            # earlier rotations G_i = [[conj c, conj s], [-s, c]] on the new column
             for i in range(k):
-                t0 = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
-                H[i + 1, k] = -np.conj(sn[i]) * H[i, k] + np.conj(cs[i]) * H[i + 1, k]
+                t0 = np.conj(cs[i]) * H[i, k] + np.conj(sn[i]) * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
                 H[i, k] = t0
             den = math.hypot(abs(H[k, k]), abs(H[k + 1, k]))
             cs[k] = H[k, k] / den
             sn[k] = H[k + 1, k] / den
             H[k, k] = den
             H[k + 1, k] = 0.0
-            g[k + 1] = -np.conj(sn[k]) * g[k]
+            g[k + 1] = -sn[k] * g[k]
             g[k] = np.conj(cs[k]) * g[k]
             it += 1
             hist.append(abs(g[k + 1]) / bn)

@@ -68,6 +68,7 @@ struct Fmm2dState {
     std::vector<int> leaves_l0;            // leaves at level >= l0
     DevBuf<int> d_leaves_l0;
     int maxP_leaf = 0;                     // largest order at a leaf level (P2M)
+    int maxP_fine = 0;                     // largest order at or below the coarsest leaf level (M2P, L2P)
     bool rows_side = false;                // the row table is being built on the side stream
     int n_p2l = 0;                         // boxes with a non-empty List 4
     DevBuf<int> d_p2l_boxes;
@@ -1129,13 +1130,19 @@ void fmm2d_presetup(cfmm_plan_s* P) {
         return (int)(std::upper_bound(T.level_off.begin(), T.level_off.end(), b) - T.level_off.begin()) - 1;
     };
     S->maxP_leaf = 0;
+    int lmin = T.nlevels;
     for (int b : T.leaf_boxes) {
         int lb = level_of(b);
         if (lb >= S->l0) {
             S->leaves_l0.push_back(b);
             S->maxP_leaf = std::max(S->maxP_leaf, S->Plev[lb]);
+            lmin = std::min(lmin, lb);
         }
     }
+    // a leaf's List 3 boxes lie below its level: their orders and the leaf's
+    // own are at most the largest order at or below the coarsest leaf level
+    S->maxP_fine = 0;
+    for (int l = lmin; l < T.nlevels; ++l) S->maxP_fine = std::max(S->maxP_fine, S->Plev[l]);
     S->d_leaves_l0.alloc(S->leaves_l0.size());
     upload(S->d_leaves_l0.get(), S->leaves_l0.data(), sizeof(int) * S->leaves_l0.size(), st);
     pt.mark("setup:leaves");
@@ -1439,9 +1446,12 @@ static void apply_t(cfmm_plan_s* P, Fmm2dState* S, const cd* sigma, const cd* ta
             CFMM_LAUNCHED();
         }
         if (g && gr.x) {
-            size_t gsm = sizeof(cd) * ((size_t)(2 * maxP + 1) + (size_t)kExpThreads * (2 * maxP + 3));
+            int Pg = S->maxP_fine;
+            size_t gsm = sizeof(cd) * ((size_t)(2 * Pg + 1) + (size_t)kExpThreads * (2 * Pg + 3));
+            CFMM_REQUIRE(gsm <= (size_t)kMaxSmem, CFMM_EUNSUPPORTED,
+                         "2D gradient: leaf-level expansion order too large for the evaluation kernel");
             k_eval_grad<KER><<<gr, kExpThreads, gsm, st>>>(A, S->d_leaves_l0.get(), T.loff[2].get(), T.lent[2].get(),
-                                                            mp, lc, g, maxP);
+                                                            mp, lc, g, Pg);
             CFMM_LAUNCHED();
         }
     }

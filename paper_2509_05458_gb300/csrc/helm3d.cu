@@ -67,6 +67,7 @@ constexpr int kH3Threads = 256;
 constexpr int kH3MaxP = kMaxP3Top;   // expansion order limit of this path
 constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
 constexpr int kM2LChunk3 = 32;       // List-2 entries per block when a list is split
+constexpr int kTr3FlatMaxP = 23;     // largest order of the flat coaxial work
 
 // ---------------------------------------------------------------------------
 // Per-device tables shared by all plans: D_n (row-major, n <= Pmax), the Z
@@ -1265,6 +1266,113 @@ __device__ __forceinline__ cd cpow_int(cd x, int m) {
     return r;
 }
 
+// Coaxial translation with the work flattened over the block (equal input
+// and output orders P, all columns of T^m in shared memory at once):
+//   1. the columns of every m advance together: at step c' thread items are
+//      the (m, row) pairs of column c = m + c' + 1 (rows c..NR-c, NR = 2P),
+//      from the two previous columns of the same m (the recurrence of the
+//      file comment, in the stable direction);
+//   2. rows <= P of each column go to a compact lower triangle per m
+//      (rows r = m..P, columns c = m..r, at (r-m)(r-m+1)/2 + c - m, m-blocks
+//      one after the other);
+//   3. the product out_n^{+-m} = sum_{c<=n} T_{n c} a_c + (2n+1)(-1)^n
+//      sum_{r>n} T_{r n} a~_r, one thread item per (m, n, sign), m-major, so
+//      the lanes of a warp share a loop length.
+// The per-warp path below does the same work with one warp per m, whose lanes
+// idle as the columns shorten.
+__host__ __device__ inline size_t tr3h_tri_off(int P, int m) {
+    size_t o = 0;
+    for (int q = 0; q < m; ++q) o += (size_t)(P - q + 1) * (P - q + 2) / 2;
+    return o;
+}
+__host__ __device__ inline size_t tr3h_flat_cols(int P) {
+    return (size_t)3 * (P + 1) * (2 * P + 2) + tr3h_tri_off(P, P + 1);
+}
+
+__device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict__ sect, cd* __restrict__ cols,
+                          const cd* __restrict__ a, const cd* __restrict__ wb, cd* __restrict__ bb) {
+    const int L = NR + 2;                       // column length
+    cd* tri = cols + (size_t)3 * (P + 1) * L;
+    auto col = [&](int k, int m) { return cols + ((size_t)k * (P + 1) + m) * L; };
+    // columns c = m (sectorial) in buffer 1, c = m - 1 (zero) in buffer 0
+    for (int t = threadIdx.x; t < (P + 1) * L; t += blockDim.x) {
+        int m = t / L, r = t - m * L;
+        col(0, m)[r] = cd{0, 0};
+        col(1, m)[r] = (r >= m && r <= NR - m) ? sect[(size_t)m * (NR + 1) + r] : cd{0, 0};
+    }
+    __syncthreads();
+    // column c = m into the triangles (rows m..P)
+    for (int t = threadIdx.x; t < (P + 1) * (P + 1); t += blockDim.x) {
+        int m = t / (P + 1), r = t - m * (P + 1);
+        if (r >= m) tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2] = col(1, m)[r];
+    }
+    int kp = 0, kc = 1, kn = 2;
+    for (int cp = 0; cp < P; ++cp) {
+        // items (m, r): m <= P - 1 - cp, r in [m + cp + 1, NR - m - cp - 1]
+        int K = NR - 2 * cp - 1;                // rows of m = 0
+        int nitem = 0;
+        for (int m = 0; m <= P - 1 - cp; ++m) nitem += K - 2 * m;
+        for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
+            int m = 0, rem = t;
+            while (rem >= K - 2 * m) {
+                rem -= K - 2 * m;
+                ++m;
+            }
+            int c = m + cp, r = c + 1 + rem;
+            const cd* prv = col(kp, m);
+            const cd* cur = col(kc, m);
+            double ac = __ldg(A.al + nmi(c, m)), ib = __ldg(A.ibe + nmi(c, m));
+            cd v = rmac(ac * prv[r], -__ldg(A.al + nmi(r + 1, m)), cur[r + 1]);
+            v = rmac(v, __ldg(A.be + nmi(r - 1, m)), cur[r - 1]);
+            col(kn, m)[r] = ib * v;
+        }
+        __syncthreads();
+        // rows c + 1 .. P of column c + 1 into the triangles
+        int ns = 0;
+        for (int m = 0; m <= P - 1 - cp; ++m) ns += P - (m + cp);
+        for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+            int m = 0, rem = t;
+            while (rem >= P - (m + cp)) {
+                rem -= P - (m + cp);
+                ++m;
+            }
+            int c1 = m + cp + 1, r = c1 + rem;
+            tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2 + (c1 - m)] = col(kn, m)[r];
+        }
+        int k0 = kp;
+        kp = kc;
+        kc = kn;
+        kn = k0;
+    }
+    __syncthreads();
+    // product: items (m, n, sign), m-major
+    int nitem = (P + 1) * (P + 1);
+    for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
+        int m = 0, rem = t;
+        while (true) {
+            int cnt = m == 0 ? P + 1 : 2 * (P - m + 1);
+            if (rem < cnt) break;
+            rem -= cnt;
+            ++m;
+        }
+        int nout = P - m + 1;
+        int n = m + (rem % nout);
+        int mm = rem < nout ? m : -m;
+        const cd* T = tri + tr3h_tri_off(P, m);
+        cd sp = {0, 0};
+        const cd* Tr = T + (size_t)(n - m) * (n - m + 1) / 2 - m;    // Tr[c] = T_{n c}
+        for (int c = m; c <= n; ++c) sp = cmac(sp, Tr[c], a[nmi(c, mm)]);
+        if (n < P) {
+            cd up = {0, 0};
+            for (int r = n + 1; r <= P; ++r)
+                up = cmac(up, T[(size_t)(r - m) * (r - m + 1) / 2 + (n - m)], wb[nmi(r, mm)]);
+            double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
+            sp += g * up;
+        }
+        bb[nmi(n, mm)] = sp;
+    }
+}
+
 // One translation per destination box and source; the destination box's
 // result is accumulated in shared memory and written (mode 0, 1) or added
 // (mode 2) at the end. Shared layout: acc[Ko], a[Km], bb[Km], wb[Km],
@@ -1274,7 +1382,7 @@ __device__ __forceinline__ cd cpow_int(cd x, int m) {
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
                        cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl,
-                       int nrhs, int nchunk, int acc_glob) {
+                       int nrhs, int nchunk, int acc_glob, int flat) {
     extern __shared__ cd sm[];
     int Pm = max(Pi, Po), Pn = min(Pi, Po);
     int Ki = (Pi + 1) * (Pi + 1), Ko = (Po + 1) * (Po + 1), Km = (Pm + 1) * (Pm + 1);
@@ -1293,7 +1401,7 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     cd* pwei = pwai + (2 * Pm + 1);
     cd* sect = pwei + (2 * Pm + 1);
     cd* cols = sect + (size_t)(Pn + 1) * (NR + 1);
-    size_t wsz = (size_t)nwarp * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
+    size_t wsz = flat ? tr3h_flat_cols(Po) : (size_t)nwarp * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
     double* Dsm = (double*)(cols + wsz);
     if (gscr) {
         // large orders: the coaxial work arrays live in this block's slice of
@@ -1403,6 +1511,9 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             }
         }
         __syncthreads();
+        if (flat) {
+            coax_flat(A, Po, NR, sect, cols, a, wb, bb);
+        } else
         for (int m = wid; m <= Pn; m += nwarp) {
             cd* cm1 = cols + (size_t)wid * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
             cd* c0 = cm1 + (NR + 2);
@@ -1624,12 +1735,13 @@ size_t tr3h_dh(int P) {
     return nd;
 }
 
-size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true, bool acc_in_smem = true) {
+size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true, bool acc_in_smem = true,
+                 bool flat = false) {
     int Pm = std::max(Pi, Po);
     size_t Km = (size_t)(Pm + 1) * (Pm + 1), Ko = (size_t)(Po + 1) * (Po + 1);
     int NR = Pi + Po;
-    size_t c = (acc_in_smem ? Ko : 0) + 3 * Km + (NR + 1) + 4 * (2 * Pm + 1) +
-               (work_in_smem ? tr3h_work(Pi, Po) : 0);
+    size_t work = flat ? (size_t)(Po + 1) * (NR + 1) + tr3h_flat_cols(Po) : tr3h_work(Pi, Po);
+    size_t c = (acc_in_smem ? Ko : 0) + 3 * Km + (NR + 1) + 4 * (2 * Pm + 1) + (work_in_smem ? work : 0);
     size_t bytes = c * sizeof(cd);
     if (d_in_smem) bytes += tr3h_dh(Pm) * sizeof(double);
     return bytes;
@@ -1936,7 +2048,11 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
                          int chunk) {
         if (nb <= 0) return;
-        size_t smem = tr3h_smem(Pi, Po, true);
+        // the flat coaxial work (equal orders, everything in shared memory with
+        // the rotation table) for the translations of the lower levels
+        int flat = (Pi == Po && Pi <= kTr3FlatMaxP && tr3h_smem(Pi, Po, true, true, true, true) <= (size_t)kH3Smem)
+                       ? 1 : 0;
+        size_t smem = tr3h_smem(Pi, Po, true, true, true, flat != 0);
         int dsm = 1;
         cd* gs = nullptr;
         if (smem > (size_t)kH3Smem) {
@@ -1993,7 +2109,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             CFMM_LAUNCHED();
         }
         k_tr3h<<<g, threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
-                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg);
+                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg, flat);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
             k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,

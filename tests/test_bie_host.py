@@ -50,3 +50,23 @@ def test_dense_nystrom_reproduces_point_source_field():
     assert e1 < 5e-6 and e2 < 5e-7
     assert e1 / e2 > 4.0                       # trapezoidal rule on a C^2 kernel: about h^3
     assert np.max(np.abs(sig[:3])) < 1e-7 * np.max(np.abs(sig))  # exponential decay at the truncation
+
+
+@pytest.mark.parametrize("restart", [5, 60])
+def test_gmres_solves_complex_system(restart):
+    """The solver the BIE demo uses, on a dense complex system with a known
+    solution (CPU torch tensors): the iterate solves A x = b to the requested
+    residual, also across restarts."""
+    import torch
+    from paper_2509_05458_gb300.bie import gmres
+    rng = np.random.default_rng(3)
+    n = 40
+    A = np.eye(n) * (2.0 + 1.0j) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    x0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    b = A @ x0
+    At = torch.from_numpy(A)
+    x, its, hist = gmres(lambda v: At @ v, torch.from_numpy(b), tol=1e-13, restart=restart, maxiter=500)
+    x = x.numpy()
+    assert hist[-1] <= 1e-13
+    assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(x - x0) <= 1e-11 * np.linalg.norm(x0)
