@@ -33,7 +33,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["curve2d", "surface3d", "densities", "halton", "Geometry",
-           "curve2d_short", "curve2d_long", "plane3d", "plane3d_uneven", "wobble2d", "wobble3d", "psi_abt"]
+           "curve2d_short", "curve2d_long", "plane3d", "plane3d_uneven", "wobble2d", "wobble3d", "psi_abt",
+           "isotropic_pair3d"]
 
 
 class Geometry:
@@ -205,3 +206,27 @@ def wobble3d(n, half=25.0, a=0.2, b=0.75, t0=12.0):
     re = np.stack([u, v, z], axis=1)
     im = np.stack([psi_abt(u, a, b, t0), psi_abt(v, a, b, t0), np.zeros_like(u)], axis=1)
     return Geometry(re, im, meta=dict(family="wobble3d", n=n, a=a, b=b, t0=t0))
+
+
+def isotropic_pair3d(seed=5, n_cluster=12, half=0.04):
+    """A 3D point set whose tree (leaf size 8, separation 2) has a List-2 pair
+    at level 3 with an isotropic complex shift: eight corner points fix the
+    root cube [0, 8]^3 (width W = 8 (1 + 2^-20), level-3 boxes of width
+    w = W/8), and two clusters of n_cluster points sit around the centres of
+    the level-3 boxes (2, 3, 1) and (3, 3, 4), the second with imaginary part
+    (0, w, 0). The complexified centres then differ by d = (w, i w, 3 w), so
+    d1^2 + d2^2 = 0 with (d1, d2) != 0; the imaginary slope between the
+    clusters is 1/sqrt(10)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W = 8.0 * (1.0 + 2.0 ** -20)
+    lo = 4.0 - W / 2.0
+    w = W / 8.0
+    corners = np.array([[x, y, z] for x in (0.0, 8.0) for y in (0.0, 8.0) for z in (0.0, 8.0)])
+    ca = lo + (np.array([2, 3, 1]) + 0.5) * w
+    cb = lo + (np.array([3, 3, 4]) + 0.5) * w
+    a = ca + rng.uniform(-half, half, (n_cluster, 3))
+    b = cb + rng.uniform(-half, half, (n_cluster, 3))
+    re = np.concatenate([corners, a, b])
+    im = np.zeros_like(re)
+    im[8 + n_cluster:, 1] = w
+    return Geometry(re, im, meta={"family": "isotropic_pair3d", "w": w})

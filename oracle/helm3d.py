@@ -343,6 +343,35 @@ def _mscale(P, e, sign):
 
 
 DEGENERATE = {"count": 0}
+# a shift with |d1^2 + d2^2| <= DEGEN_TOL * sum |d_i|^2 and (d1, d2) != 0 (an
+# isotropic complex direction in the xy-plane) is translated in a frame turned
+# by a fixed real rotation (see ``translate``)
+DEGEN_TOL = 1e-8
+
+
+def _fixed_frame(d):
+    """Frame index k per shift: -1 = none; 0, 1 = the real rotation Q_k with
+    Q_0 d = (-d3, d2, d1), Q_1 d = (-d3, -d1, d2) (the rotation of ``translate``
+    with e = i^k and alpha = pi/2), chosen for a larger |(Q d)_1^2 + (Q d)_2^2|."""
+    s2 = d[:, 0] ** 2 + d[:, 1] ** 2
+    nrm2 = np.sum(np.abs(d) ** 2, axis=-1)
+    xy = (d[:, 0] != 0) | (d[:, 1] != 0)
+    bad = xy & (np.abs(s2) <= DEGEN_TOL * nrm2)
+    k = np.where(np.abs(d[:, 2] ** 2 + d[:, 1] ** 2) >= np.abs(d[:, 2] ** 2 + d[:, 0] ** 2), 0, 1)
+    return np.where(bad, k, -1)
+
+
+def _rot_frame(c, P, e, ca, sa, sign):
+    """Coefficients in the frame of the rotation x' = R_y(alpha) R_z(-beta) x
+    (e = e^{i beta}, ca = cos alpha, sa = sin alpha; sign = +1) or back
+    (sign = -1): E(e) then the y-rotation by projection, or the reverse."""
+    Ry = np.zeros((e.shape[0], 3, 3), complex)
+    Ry[:, 0, 0], Ry[:, 0, 2], Ry[:, 1, 1] = ca, -sa, 1.0
+    Ry[:, 2, 0], Ry[:, 2, 2] = sa, ca
+    ext = (slice(None),) + (None,) * (c.ndim - 2) + (slice(None),)
+    if sign > 0:
+        return rotate_proj(c * _mscale(P, e, 1)[ext], P, Ry)
+    return rotate_proj(c, P, np.transpose(Ry, (0, 2, 1))) * _mscale(P, e, -1)[ext]
 
 
 def translate(c, P_in, P_out, d, rho_s, kappa, kind_in, kind_out, coaxial="projection"):
@@ -350,28 +379,48 @@ def translate(c, P_in, P_out, d, rho_s, kappa, kind_in, kind_out, coaxial="proje
 
     c: [B, ..., (P_in+1)^2], d: complex [B, 3]. coaxial = "projection" (step 3
     as the paper does it) or "exact" (``zshift_exact``).
+
+    Rotation to the z-axis: e = (d1 + i d2)/s, s^2 = d1^2 + d2^2, and
+    cos alpha = d3/t, sin alpha = s/t. With s = 0 and d1 = d2 = 0 the shift is
+    already on the z-axis (beta = 0). When s^2 is zero or nearly zero while
+    (d1, d2) is not (an isotropic complex direction: e and 1/e blow up), the
+    expansion is first turned by the fixed real rotation Q_k of ``_fixed_frame``
+    and the shift Q_k d is translated in that frame, then the result is turned
+    back; in exact arithmetic this is the same operator.
     """
     c = np.asarray(c, complex)
     d = np.asarray(d, complex).reshape(-1, 3)
+    fr = _fixed_frame(d)
+    DEGENERATE["count"] += int(np.sum(fr >= 0))
+    if np.any(fr >= 0):
+        # shift in the fixed frame; the expansion turned into it
+        dq = d.copy()
+        q0, q1 = fr == 0, fr == 1
+        dq[q0] = np.stack([-d[q0, 2], d[q0, 1], d[q0, 0]], axis=-1)
+        dq[q1] = np.stack([-d[q1, 2], -d[q1, 0], d[q1, 1]], axis=-1)
+        sel = fr >= 0
+        ek = np.where(fr == 1, 1j, 1.0 + 0j)[sel]
+        one, zero = np.ones(ek.shape[0]), np.zeros(ek.shape[0])
+        cq = c.copy()
+        cq[sel] = _rot_frame(c[sel], P_in, ek, zero, one, 1)
+        out = _translate_frame(cq, P_in, P_out, dq, rho_s, kappa, kind_in, kind_out, coaxial)
+        out[sel] = _rot_frame(out[sel], P_out, ek, zero, one, -1)
+        return out
+    return _translate_frame(c, P_in, P_out, d, rho_s, kappa, kind_in, kind_out, coaxial)
+
+
+def _translate_frame(c, P_in, P_out, d, rho_s, kappa, kind_in, kind_out, coaxial):
     s2 = d[:, 0] ** 2 + d[:, 1] ** 2
     tt = np.sqrt(np.sum(d * d, axis=-1))
     flat = s2 == 0
     s = np.where(flat, 0.0, np.sqrt(s2))
     e = np.where(flat, 1.0 + 0j, (d[:, 0] + 1j * d[:, 1]) / np.where(flat, 1.0, s))
-    DEGENERATE["count"] += int(np.sum((~flat) & (np.abs(s2) <= 1e-8 * np.abs(tt * tt))))
-    ca, sa = d[:, 2] / tt, s / tt
-    Ry = np.zeros((d.shape[0], 3, 3), complex)
-    Ry[:, 0, 0], Ry[:, 0, 2], Ry[:, 1, 1] = ca, -sa, 1.0
-    Ry[:, 2, 0], Ry[:, 2, 2] = sa, ca
-    ext = (slice(None),) + (None,) * (c.ndim - 2) + (slice(None),)
-    c1 = c * _mscale(P_in, e, 1)[ext]
-    c2 = rotate_proj(c1, P_in, Ry)
+    c2 = _rot_frame(c, P_in, e, d[:, 2] / tt, s / tt, 1)
     if coaxial == "exact":
         c3 = zshift_exact(c2, P_in, P_out, tt, kappa, kind_in, kind_out)
     else:
         c3 = zshift(c2, P_in, P_out, tt, rho_s, kappa, kind_in, kind_out)
-    c4 = rotate_proj(c3, P_out, np.transpose(Ry, (0, 2, 1)))
-    return c4 * _mscale(P_out, e, -1)[ext]
+    return _rot_frame(c3, P_out, e, d[:, 2] / tt, s / tt, -1)
 
 
 class Helmholtz3D:

@@ -269,3 +269,80 @@ def test_laplace_multipole_from_schmidt_harmonics():
             e = (-1.0) ** m if m < 0 else 1.0
             ref = e / s * (sig[0] @ Z[idx(n, -m)])
             assert abs(M[idx(n, m)] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def _shifts(rng, n):
+    # imaginary parts small enough that |e| = |(d1 + i d2)/s| stays near 1: the
+    # direct rotation scales coefficient m by e^m, so |e| far from 1 makes it
+    # (not the fixed frame) lose digits
+    re = rng.normal(size=(n, 3))
+    return re * (1.0 + 0.1j * rng.normal(size=(n, 3)))
+
+
+@pytest.mark.parametrize("kinds", [("h", "h"), ("h", "j"), ("j", "j")])
+def test_fixed_frame_equals_standard_rotation(monkeypatch, kinds):
+    """The fixed-frame translation (turn by Q_k, translate Q_k d, turn back) is
+    the same operator as the direct rotation to the z-axis: forced on generic
+    shifts (both frames k = 0, 1), it reproduces the standard path to 1e-12."""
+    rng = np.random.default_rng(7)
+    P = 12
+    d = _shifts(rng, 8) * 2.0
+    d[:4, 1] *= 0.2       # mostly frame 1
+    d[4:, 0] *= 0.2       # mostly frame 0
+    c = rng.normal(size=(8, (P + 1) ** 2)) + 1j * rng.normal(size=(8, (P + 1) ** 2))
+    monkeypatch.setattr(H, "DEGEN_TOL", -1.0)
+    ref = H.translate(c, P, P, d, 0.5, KAPPA, kinds[0], kinds[1], coaxial="exact")
+    monkeypatch.setattr(H, "DEGEN_TOL", np.inf)
+    fr = H._fixed_frame(d)
+    assert set(fr) == {0, 1}
+    out = H.translate(c, P, P, d, 0.5, KAPPA, kinds[0], kinds[1], coaxial="exact")
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_isotropic_shift_translations(monkeypatch):
+    """Shifts with d1^2 + d2^2 = 0 and (d1, d2) != 0 (isotropic complex
+    directions, where e = (d1 + i d2)/s is undefined): M2M and M2L through the
+    fixed frame reproduce the direct sum; the plain rotation (beta = 0, as for
+    a shift on the z-axis) does not."""
+    rng = np.random.default_rng(8)
+    P = 18
+    ops = H.Helmholtz3D(KAPPA, _W(), "exact")
+    sig = rng.normal(size=(1, 30)) + 1j * rng.normal(size=(1, 30))
+    src = _cluster(rng, np.zeros(3), 30, half=0.25, slope=0.0)
+    M = ops.p2m(P, src, sig)
+    # M2M to c_new = d: d1^2 + d2^2 = 0.09 - 0.09 = 0
+    d = np.array([0.3, 0.3j, 0.6])
+    trg = _cluster(rng, np.array([4.0, 1.0, -1.0]), 10, slope=0.0)
+    u0 = direct(3, 1, KAPPA, src, trg, sigma=sig[0])
+    n0 = H.DEGENERATE["count"]
+    Mn = ops.m2m(P, P, M, -d, 0)      # a = c_child - c_parent
+    assert H.DEGENERATE["count"] == n0 + 1
+    assert relerr_l2(ops.m2p(P, Mn, trg - d)[0], u0) < 1e-8
+    # M2L to a target box around t: t1^2 + t2^2 = 2.25 - 2.25 = 0
+    t = np.array([1.5, 1.5j, 3.0])
+    trg2 = _cluster(rng, np.zeros(3), 10, half=0.25, slope=0.0) + t
+    u2 = direct(3, 1, KAPPA, src, trg2, sigma=sig[0])
+    L = ops.m2l(P, M, t, 0)
+    assert relerr_l2(ops.l2p(P, L, trg2 - t)[0], u2) < 1e-8
+    monkeypatch.setattr(H, "DEGEN_TOL", -1.0)
+    Lb = ops.m2l(P, M, t, 0)
+    assert relerr_l2(ops.l2p(P, Lb, trg2 - t)[0], u2) > 1e-3
+
+
+def test_isotropic_pair_in_fmm(monkeypatch):
+    """An FMM whose tree holds a List-2 pair with an isotropic complex shift
+    (cfmm_inputs.isotropic_pair3d): the fixed frame is taken for that pair
+    (both directions) and the result meets the direct sum; without it the
+    M2L of that pair is wrong."""
+    from cfmm_inputs import isotropic_pair3d
+    g = isotropic_pair3d()
+    pts = g.re + 1j * g.im
+    dens = densities(g.n, seed=4, nrhs=1, ncomp=1)[0, 0]
+    u0 = direct(3, 1, 1.0, pts, pts, sigma=dens)
+    n0 = H.DEGENERATE["count"]
+    u, _ = H.apply(g.re, g.im, 1.0, 1e-10, 8, k=2, sigma=dens, coaxial="exact")
+    assert H.DEGENERATE["count"] - n0 == 2
+    assert relerr_paper(u, u0, dens) <= 1e-10
+    monkeypatch.setattr(H, "DEGEN_TOL", -1.0)
+    ub, _ = H.apply(g.re, g.im, 1.0, 1e-10, 8, k=2, sigma=dens, coaxial="exact")
+    assert relerr_paper(ub, u0, dens) > 1e-4
