@@ -72,6 +72,8 @@ enum {
     CFMM_AUTO = 2    /* MIXED when eps >= 1e-5, else FP64                      */
 };
 
+enum { CFMM_TOP_FIT = -1 };
+
 typedef struct cfmm_opts {
     int leaf_size;      /* N_s, max points per leaf (Sec. 6.1); 0 = default 64  */
     int sep;            /* separation k = 1..3 of Sec. 6.2/6.5; 0 = default 1;  */
@@ -79,7 +81,11 @@ typedef struct cfmm_opts {
                         /* Lipschitz limit, times 2, is at least the plan's     */
                         /* Lipschitz estimate (3 if none)                       */
     int precision;      /* CFMM_FP64 / CFMM_MIXED / CFMM_AUTO                   */
-    int top_level;      /* top expansion level l0; <= 0 = automatic rule        */
+    int top_level;      /* top expansion level l0; 0 = automatic rule; > 0 =    */
+                        /* that level; CFMM_TOP_FIT (-1) = the rule's level,    */
+                        /* then deeper until the 3D Helmholtz order there is    */
+                        /* within this library's limit (63; without it such a  */
+                        /* plan fails with CFMM_EUNSUPPORTED)                   */
     void* stream;       /* cudaStream_t the plan runs on; NULL = legacy stream  */
 } cfmm_opts;
 

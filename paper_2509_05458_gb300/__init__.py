@@ -17,11 +17,12 @@ import os
 import numpy as np
 
 __all__ = ["LAPLACE", "HELMHOLTZ", "SLP", "DLP", "GREEN_SCALE", "FP64", "MIXED", "AUTO",
-           "Plan", "plan", "plan_targets", "Batch", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
+           "TOP_FIT", "Plan", "plan", "plan_targets", "Batch", "direct", "direct_noalloc", "lib", "launch_count", "CfmmError", "library_path"]
 
 LAPLACE, HELMHOLTZ = 0, 1
 SLP, DLP, GREEN_SCALE = 1 << 4, 1 << 5, 1 << 6
 FP64, MIXED, AUTO = 0, 1, 2
+TOP_FIT = -1   # top_level: the rule's level, deeper until the 3D Helmholtz order fits the library's limit
 # status codes (include/cfmm.h)
 OK, EINVAL, ENONFINITE, EGEOM, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 

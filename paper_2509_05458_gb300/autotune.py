@@ -21,19 +21,19 @@ from . import CfmmError, plan as make_plan
 _CACHE = {}
 
 
-def _bucket(dim, kernel, precision, n, eps, kappa, width, sep=1):
-    return (dim, kernel & 0xF, precision, sep, int(round(math.log2(max(n, 1)))),
+def _bucket(dim, kernel, precision, n, eps, kappa, width, sep=1, top_level=0):
+    return (dim, kernel & 0xF, precision, sep, top_level, int(round(math.log2(max(n, 1)))),
             int(round(math.log10(eps))), int(round(math.log2(1.0 + kappa * width))))
 
 
 def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=None,
                    precision=0, candidates=(32, 48, 64, 96, 128, 192), reps=3, stream=None,
-                   use_cache=True, sep=1):
+                   use_cache=True, sep=1, top_level=0):
     """Returns (best_leaf_size, {leaf_size: median apply ms}). Inputs are CUDA tensors."""
     import torch
     n = int(pts_re.shape[0])
     width = float((pts_re.max(0).values - pts_re.min(0).values).max())
-    key = _bucket(dim, kernel, precision, n, eps, kappa, width, sep)
+    key = _bucket(dim, kernel, precision, n, eps, kappa, width, sep, top_level)
     if use_cache and key in _CACHE:
         return _CACHE[key]
     dev = pts_re.device
@@ -46,7 +46,7 @@ def tune_leaf_size(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re=None, nrm_im=
     for ls in candidates:
         try:
             p = make_plan(dim, kernel, kappa, eps, pts_re, pts_im, nrm_re, nrm_im, leaf_size=ls, sep=sep,
-                          precision=precision, stream=stream)
+                          precision=precision, stream=stream, top_level=top_level)
         except CfmmError:
             continue          # a candidate the plan rejects (e.g. an order limit) is skipped
         out = p.apply(dens)

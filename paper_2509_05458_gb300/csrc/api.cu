@@ -522,6 +522,7 @@ static cfmm_plan_t plan_common(int dim, int kernel, double k, double eps, const 
         CFMM_REQUIRE(leaf <= 4096, CFMM_EINVAL, "leaf_size must be <= 4096");
         CFMM_REQUIRE(sep <= 3, CFMM_EINVAL, "sep must be 1, 2 or 3 (or < 0 for automatic)");
         CFMM_REQUIRE(o.precision >= 0 && o.precision <= 2, CFMM_EINVAL, "bad precision mode");
+        CFMM_REQUIRE(o.top_level >= CFMM_TOP_FIT, CFMM_EINVAL, "top_level must be >= -1 (CFMM_TOP_FIT)");
         int64_t n = m + ntrg;
         P = new cfmm_plan_s();
         P->dim = dim;

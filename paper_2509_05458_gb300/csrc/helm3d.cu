@@ -68,6 +68,10 @@ constexpr int kH3MaxP = kMaxP3Top;   // expansion order limit of this path
 constexpr int kH3Smem = 220 * 1024;  // dynamic shared memory ceiling per block
 constexpr int kM2LChunk3 = 32;       // List-2 entries per block when a list is split
 constexpr int kTr3FlatMaxP = 23;     // largest order of the flat coaxial work
+constexpr double kDegenTol = 1e-8;   // |d1^2 + d2^2| <= this * sum |d_i|^2: fixed-frame translation
+constexpr int kTriMaxP = 40;         // largest M2L order whose coaxial operators are built ahead (k_tr3h_tri)
+constexpr int kTriThreads = 128;     // threads of k_tr3h_tri
+constexpr size_t kTriBudget = (size_t)6 << 30;   // bytes of operators per M2L launch range
 
 // ---------------------------------------------------------------------------
 // Per-device tables shared by all plans: D_n (row-major, n <= Pmax), the Z
@@ -1214,12 +1218,40 @@ __device__ __forceinline__ void d_pass(const double* Dh, const int64_t* Dhoff, c
     }
 }
 
+// The fixed real rotation Q_k (k = 0, 1) of the fixed-frame translation,
+// applied in place to the coefficients x (order P) through wb and tmp: the
+// rotation sequence of the translation kernels with e = i^k and alpha = pi/2,
+// whose diagonal factors are powers of i (no tables). Ends with a barrier.
+__device__ void rot_fixed(const Tr3hArgs& A, const double* Dh, cd* x, cd* wb, cd* tmp, int P, int Pm, int k) {
+    w_pass(A.knm, x, wb, P, 1 + k, 0, nullptr, Pm);
+    __syncthreads();
+    d_pass(Dh, A.Dhoff, wb, tmp, P, 0, 0, nullptr, Pm, 0);
+    __syncthreads();
+    w_pass(A.knm, tmp, wb, P, 3, 0, nullptr, Pm);
+    __syncthreads();
+    d_pass(Dh, A.Dhoff, wb, x, P, 1, 0, nullptr, Pm, 0);
+    __syncthreads();
+}
+
+// Its inverse from x into out (added when accum != 0); x and tmp are
+// overwritten. Needs a barrier before (x written) and leaves out unsynchronised.
+__device__ void rot_fixed_inv(const Tr3hArgs& A, const double* Dh, cd* x, cd* wb, cd* tmp, cd* out, int P, int Pm,
+                              int k, int accum) {
+    w_pass(A.knm, x, wb, P, 1, 0, nullptr, Pm);
+    __syncthreads();
+    d_pass(Dh, A.Dhoff, wb, tmp, P, 0, 0, nullptr, Pm, 0);
+    __syncthreads();
+    w_pass(A.knm, tmp, wb, P, 1, 0, nullptr, Pm);
+    __syncthreads();
+    d_pass(Dh, A.Dhoff, wb, out, P, (1 - k) & 3, 0, nullptr, Pm, accum);
+}
+
 // Per-shift quantities of a launch, one thread per (destination, source)
 // pair: e = e^{i beta}, e_a = e^{i alpha} and f_l(kappa t), l <= NR. Pair p
 // of the launch is list entry qfirst + p (mode 1), child box qfirst + p
 // (mode 0) or destination box lo + p (mode 2).
 __global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, int NR, int use_h,
-                           cd* __restrict__ sc, cd* __restrict__ fl) {
+                           cd* __restrict__ sc, cd* __restrict__ fl, int* __restrict__ fb) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npair) return;
     int b, s;
@@ -1237,6 +1269,25 @@ __global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, 
     cd d[3];
     for (int k = 0; k < 3; ++k) d[k] = cd{A.cre[3 * b + k] - A.cre[3 * s + k], A.cim[3 * b + k] - A.cim[3 * s + k]};
     cd s2 = d[0] * d[0] + d[1] * d[1];
+    // an isotropic complex direction in the xy-plane (s^2 = 0 or nearly, with
+    // (d1, d2) != 0) has no z-rotation angle: the pair is translated in the
+    // frame of the fixed real rotation Q_k (Q_0 d = (-d3, d2, d1), Q_1 d =
+    // (-d3, -d1, d2)), the one with the larger |(Q d)_1^2 + (Q d)_2^2|
+    int fr = -1;
+    {
+        double n2 = cabs2(d[0]) + cabs2(d[1]) + cabs2(d[2]);
+        bool xy = d[0].x != 0.0 || d[0].y != 0.0 || d[1].x != 0.0 || d[1].y != 0.0;
+        if (xy && cabs2(s2) <= (kDegenTol * n2) * (kDegenTol * n2)) {
+            cd a0 = d[2] * d[2] + d[1] * d[1], a1 = d[2] * d[2] + d[0] * d[0];
+            fr = cabs2(a0) >= cabs2(a1) ? 0 : 1;
+            cd q1 = fr == 0 ? d[1] : -d[0], q2 = fr == 0 ? d[0] : d[1];
+            d[0] = -d[2];
+            d[1] = q1;
+            d[2] = q2;
+            s2 = d[0] * d[0] + d[1] * d[1];
+        }
+    }
+    fb[p] = fr;
     cd t = csqrt_p(s2 + d[2] * d[2]);
     cd sq = {0, 0}, e = {1, 0};
     if (!(s2.x == 0.0 && s2.y == 0.0)) {
@@ -1285,8 +1336,41 @@ __host__ __device__ inline size_t tr3h_tri_off(int P, int m) {
     for (int q = 0; q < m; ++q) o += (size_t)(P - q + 1) * (P - q + 2) / 2;
     return o;
 }
+__host__ __device__ inline size_t tr3h_tri_size(int P) { return (size_t)(P + 1) * (P + 2) * (P + 3) / 6; }
 __host__ __device__ inline size_t tr3h_flat_cols(int P) {
     return (size_t)3 * (P + 1) * (2 * P + 2) + tr3h_tri_off(P, P + 1);
+}
+
+// out_n^{+-m} = sum_{c<=n} T_{n c} a_c + (2n+1)(-1)^n sum_{r>n} T_{r n} a~_r with
+// the compact triangles tri (shared or global memory): one thread item per
+// (m, n, sign), m-major, so the lanes of a warp share a loop length
+__device__ void coax_product(int P, const cd* __restrict__ tri, const cd* __restrict__ a, const cd* __restrict__ wb,
+                             cd* __restrict__ bb) {
+    int nitem = (P + 1) * (P + 1);
+    for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
+        int m = 0, rem = t;
+        while (true) {
+            int cnt = m == 0 ? P + 1 : 2 * (P - m + 1);
+            if (rem < cnt) break;
+            rem -= cnt;
+            ++m;
+        }
+        int nout = P - m + 1;
+        int n = m + (rem % nout);
+        int mm = rem < nout ? m : -m;
+        const cd* T = tri + tr3h_tri_off(P, m);
+        cd sp = {0, 0};
+        const cd* Tr = T + (size_t)(n - m) * (n - m + 1) / 2 - m;    // Tr[c] = T_{n c}
+        for (int c = m; c <= n; ++c) sp = cmac(sp, Tr[c], a[nmi(c, mm)]);
+        if (n < P) {
+            cd up = {0, 0};
+            for (int r = n + 1; r <= P; ++r)
+                up = cmac(up, T[(size_t)(r - m) * (r - m + 1) / 2 + (n - m)], wb[nmi(r, mm)]);
+            double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
+            sp += g * up;
+        }
+        bb[nmi(n, mm)] = sp;
+    }
 }
 
 __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict__ sect, cd* __restrict__ cols,
@@ -1345,31 +1429,92 @@ __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict
         kn = k0;
     }
     __syncthreads();
-    // product: items (m, n, sign), m-major
-    int nitem = (P + 1) * (P + 1);
-    for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
-        int m = 0, rem = t;
-        while (true) {
-            int cnt = m == 0 ? P + 1 : 2 * (P - m + 1);
-            if (rem < cnt) break;
-            rem -= cnt;
-            ++m;
+    coax_product(P, tri, a, wb, bb);
+}
+
+// The coaxial operators of the M2L pairs of a launch (equal orders P), built
+// once per pair for every right-hand side: one block per pair writes the
+// compact triangles T^m (the layout of tr3h_tri_off, tr3h_tri_size entries)
+// to tri. The sectorial columns T_{r m}^m (r = m..NR - m) come from the
+// recurrence over m (one step per m, rows over the block's threads), then the
+// columns of every m advance together, two buffers per m: the next column
+// overwrites the one before the current one in place (each row reads only its
+// own entry of it). Shared memory: the radial sequence, 2 (P+1) (NR+2)
+// complex values and P+1 offsets.
+__global__ void k_tr3h_tri(Tr3hArgs A, int P, int npair, const cd* __restrict__ fl, cd* __restrict__ tri) {
+    extern __shared__ cd sm[];
+    const int NR = 2 * P, L = NR + 2;
+    cd* f = sm;
+    cd* cols = f + (NR + 1);
+    int* moff = (int*)(cols + (size_t)2 * (P + 1) * L);
+    auto col = [&](int k, int m) { return cols + ((size_t)k * (P + 1) + m) * L; };
+    const size_t tsz = tr3h_tri_size(P);
+    for (int p = blockIdx.x; p < npair; p += gridDim.x) {
+        __syncthreads();
+        cd* T = tri + (size_t)p * tsz;
+        for (int l = threadIdx.x; l <= NR; l += blockDim.x) f[l] = fl[(size_t)p * (NR + 1) + l];
+        for (int m = threadIdx.x; m <= P; m += blockDim.x) moff[m] = (int)tr3h_tri_off(P, m);
+        for (int t = threadIdx.x; t < 2 * (P + 1) * L; t += blockDim.x) cols[t] = cd{0, 0};
+        __syncthreads();
+        // sectorial columns into buffer 1 (buffer 0 stays zero: the column
+        // before the first)
+        for (int r = threadIdx.x; r <= NR; r += blockDim.x) {
+            double sg = (r & 1) ? -1.0 : 1.0;
+            col(1, 0)[r] = (sg * (2.0 * r + 1.0)) * f[r];
         }
-        int nout = P - m + 1;
-        int n = m + (rem % nout);
-        int mm = rem < nout ? m : -m;
-        const cd* T = tri + tr3h_tri_off(P, m);
-        cd sp = {0, 0};
-        const cd* Tr = T + (size_t)(n - m) * (n - m + 1) / 2 - m;    // Tr[c] = T_{n c}
-        for (int c = m; c <= n; ++c) sp = cmac(sp, Tr[c], a[nmi(c, mm)]);
-        if (n < P) {
-            cd up = {0, 0};
-            for (int r = n + 1; r <= P; ++r)
-                up = cmac(up, T[(size_t)(r - m) * (r - m + 1) / 2 + (n - m)], wb[nmi(r, mm)]);
-            double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
-            sp += g * up;
+        __syncthreads();
+        for (int m = 1; m <= P; ++m) {
+            const cd* pv = col(1, m - 1);
+            cd* cur = col(1, m);
+            int mm = m - 1;
+            double inu = 1.0 / __ldg(A.nu + nmi(mm, mm));
+            for (int r = m + threadIdx.x; r <= NR - m; r += blockDim.x) {
+                double mu1 = __ldg(A.mu + nmi(r + 1, mm)), nu1 = __ldg(A.nu + nmi(r - 1, mm));
+                cur[r] = inu * (mu1 * pv[r + 1] + nu1 * pv[r - 1]);
+            }
+            __syncthreads();
         }
-        bb[nmi(n, mm)] = sp;
+        // column c = m of every m into the triangles (rows m..P)
+        for (int t = threadIdx.x; t < (P + 1) * (P + 1); t += blockDim.x) {
+            int m = t / (P + 1), r = t - m * (P + 1);
+            if (r >= m) T[moff[m] + (r - m) * (r - m + 1) / 2] = col(1, m)[r];
+        }
+        int kp = 0, kc = 1;
+        for (int cp = 0; cp < P; ++cp) {
+            // items (m, r): m <= P - 1 - cp, r in [m + cp + 1, NR - m - cp - 1]
+            int K = NR - 2 * cp - 1;
+            int nitem = (P - cp) * (K - (P - 1 - cp));
+            for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
+                int m = 0, rem = t;
+                while (rem >= K - 2 * m) {
+                    rem -= K - 2 * m;
+                    ++m;
+                }
+                int c = m + cp, r = c + 1 + rem;
+                cd* prv = col(kp, m);
+                const cd* cur = col(kc, m);
+                double ac = __ldg(A.al + nmi(c, m)), ib = __ldg(A.ibe + nmi(c, m));
+                cd v = rmac(ac * prv[r], -__ldg(A.al + nmi(r + 1, m)), cur[r + 1]);
+                v = rmac(v, __ldg(A.be + nmi(r - 1, m)), cur[r - 1]);
+                prv[r] = ib * v;
+            }
+            __syncthreads();
+            // rows c + 1 .. P of column c + 1 into the triangles
+            int ns = 0;
+            for (int m = 0; m <= P - 1 - cp; ++m) ns += P - (m + cp);
+            for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+                int m = 0, rem = t;
+                while (rem >= P - (m + cp)) {
+                    rem -= P - (m + cp);
+                    ++m;
+                }
+                int c1 = m + cp + 1, r = c1 + rem;
+                T[moff[m] + (r - m) * (r - m + 1) / 2 + (c1 - m)] = col(kp, m)[r];
+            }
+            int k0 = kp;
+            kp = kc;
+            kc = k0;
+        }
     }
 }
 
@@ -1382,7 +1527,8 @@ __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
                        cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl,
-                       int nrhs, int nchunk, int acc_glob, int flat) {
+                       int nrhs, int nchunk, int acc_glob, int flat, const int* __restrict__ fb,
+                       int ops_g, const cd* __restrict__ trig) {
     extern __shared__ cd sm[];
     int Pm = max(Pi, Po), Pn = min(Pi, Po);
     int Ki = (Pi + 1) * (Pi + 1), Ko = (Po + 1) * (Po + 1), Km = (Pm + 1) * (Pm + 1);
@@ -1403,6 +1549,9 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     cd* cols = sect + (size_t)(Pn + 1) * (NR + 1);
     size_t wsz = flat ? tr3h_flat_cols(Po) : (size_t)nwarp * ((size_t)3 * (NR + 2) + (size_t)(Pm + 1) * (Pn + 1));
     double* Dsm = (double*)(cols + wsz);
+    // ops_g: the coaxial operators come from trig (the launch was sized without
+    // coaxial work arrays, also when it has no pairs and trig is null)
+    if (ops_g) Dsm = (double*)(pwei + (2 * Pm + 1));
     if (gscr) {
         // large orders: the coaxial work arrays live in this block's slice of
         // global scratch instead of shared memory
@@ -1422,8 +1571,10 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
     // global scratch slice is reused by its items
     int64_t nitem = (int64_t)nb * nrhs * nchunk;
     for (int64_t item = blockIdx.x; item < nitem; item += gridDim.x) {
-    int bx = (int)(item % nb);
-    int rhs = (int)((item / nb) % nrhs);
+    // with operators from trig the right-hand sides of a box are neighbours,
+    // so the blocks that read a pair's operators run close together (L2)
+    int bx = ops_g ? (int)((item / nrhs) % nb) : (int)(item % nb);
+    int rhs = ops_g ? (int)(item % nrhs) : (int)((item / nb) % nrhs);
     int zc = (int)(item / ((int64_t)nb * nrhs));
     int b = lo + bx;
     if (mode == 0 && A.leaf[b]) continue;    // a leaf keeps its P2M expansion
@@ -1454,7 +1605,8 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         int p = mode == 1 ? q - qfirst : mode == 0 ? q - qfirst : b - lo;
         const cd* src = in + (int64_t)rhs * A.ncoef + A.eoff[s];
         for (int k = threadIdx.x; k < Ki; k += blockDim.x) a[k] = src[k];
-        for (int l = threadIdx.x; l <= NR; l += blockDim.x) f[l] = fl[(size_t)p * (NR + 1) + l];
+        if (!ops_g)
+            for (int l = threadIdx.x; l <= NR; l += blockDim.x) f[l] = fl[(size_t)p * (NR + 1) + l];
         {
             // powers of e, e_a and of their inverses, m in [-Pm, Pm]: warp w < 4
             // takes one of the four sequences, a lane per |m|
@@ -1474,6 +1626,9 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             pwai[Pm + m] = pwa[Pm - m];
             pwei[Pm + m] = pwe[Pm - m];
         }
+        // (0) a pair in the fixed frame: turn the input into it
+        int fr = __ldg(fb + p);
+        if (fr >= 0) rot_fixed(A, Dh, a, wb, bb, Pi, Pm, fr);
         // (1) forward rotation: x = Phi E(e) c; y = D x; x' = S E(e_a) y; u = D x'; c~ = i^m u
         w_pass(A.knm, a, wb, Pi, 1, 0, pwe, Pm);
         __syncthreads();
@@ -1492,7 +1647,7 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             wb[k] = ((n & 1) ? -sc : sc) * a[k];
         }
         for (int k = threadIdx.x; k < Ko; k += blockDim.x) bb[k] = cd{0, 0};
-        if (wid == 0) {
+        if (wid == 0 && !ops_g) {
             for (int r = lane; r <= NR; r += 32) {
                 double sg = (r & 1) ? -1.0 : 1.0;
                 sect[r] = (sg * (2.0 * r + 1.0)) * f[r];
@@ -1511,7 +1666,9 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
             }
         }
         __syncthreads();
-        if (flat) {
+        if (ops_g) {
+            coax_product(Po, trig + (size_t)p * tr3h_tri_size(Po), a, wb, bb);
+        } else if (flat) {
             coax_flat(A, Po, NR, sect, cols, a, wb, bb);
         } else
         for (int m = wid; m <= Pn; m += nwarp) {
@@ -1571,7 +1728,14 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         __syncthreads();
         w_pass(A.knm, a, wb, Po, 0, 1, pwai, Pm);
         __syncthreads();
-        d_pass(Dh, A.Dhoff, wb, acc, Po, 1, 0, pwei, Pm, 1);
+        if (fr >= 0) {
+            // (4) out of the fixed frame, added to the accumulator
+            d_pass(Dh, A.Dhoff, wb, a, Po, 1, 0, pwei, Pm, 0);
+            __syncthreads();
+            rot_fixed_inv(A, Dh, a, wb, bb, acc, Po, Pm, fr, 1);
+        } else {
+            d_pass(Dh, A.Dhoff, wb, acc, Po, 1, 0, pwei, Pm, 1);
+        }
     }
     __syncthreads();
     if (part) {
@@ -1612,7 +1776,8 @@ __global__ void k_tr3h_reduce(const cd* __restrict__ part, int nchunk, int nb, i
 __global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const double* __restrict__ lsm,
                        const double* __restrict__ lsd, const double* __restrict__ fact,
                        const double* __restrict__ ifact, const cd* __restrict__ in, cd* __restrict__ out,
-                       int qfirst, const cd* __restrict__ sc, const cd* __restrict__ tt) {
+                       int qfirst, const cd* __restrict__ sc, const cd* __restrict__ tt,
+                       const int* __restrict__ fb) {
     extern __shared__ cd sm[];
     int b = lo + blockIdx.x;
     if (mode == 0 && A.leaf[b]) return;
@@ -1674,6 +1839,8 @@ __global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const
             pwai[P + m] = pwa[P - m];
             pwei[P + m] = pwe[P - m];
         }
+        int fr = __ldg(fb + p);
+        if (fr >= 0) rot_fixed(A, Dh, a, wb, bb, P, P, fr);
         // forward rotation
         w_pass(A.knm, a, wb, P, 1, 0, pwe, P);
         __syncthreads();
@@ -1711,6 +1878,10 @@ __global__ void k_tr3l(Tr3hArgs A, int mode, int lo, int P, int d_in_smem, const
         __syncthreads();
         d_pass(Dh, A.Dhoff, wb, bb, P, 1, 0, pwei, P, 0);
         __syncthreads();
+        if (fr >= 0) {
+            rot_fixed_inv(A, Dh, bb, wb, a, bb, P, P, fr, 0);
+            __syncthreads();
+        }
         for (int k = threadIdx.x; k < K; k += blockDim.x) acc[k] += (out_local ? __ldg(lsm + k) : __ldg(lsd + k)) * bb[k];
     }
     __syncthreads();
@@ -1747,6 +1918,12 @@ size_t tr3h_smem(int Pi, int Po, bool d_in_smem, bool work_in_smem = true, bool 
     return bytes;
 }
 
+// shared memory of k_tr3h_tri: radial sequence, two column buffers per m,
+// triangle offsets
+size_t tri_build_smem(int P) {
+    return sizeof(cd) * ((size_t)(2 * P + 1) + (size_t)2 * (P + 1) * (2 * P + 2)) + sizeof(int) * (size_t)(P + 1);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1777,6 +1954,8 @@ struct Helm3dState {
     std::vector<int> l2off;      // host copy of the List-2 offsets
     DevBuf<int> qbox;            // owner box of each List-2 entry
     DevBuf<cd> pre_sc, pre_fl;   // per-pair prologue of a translation launch
+    DevBuf<int> pre_fb;          // per pair: fixed frame k, or -1
+    DevBuf<cd> tri;              // coaxial operators of the M2L pairs of a launch range
     std::vector<int> level_off;
     int lvl_of_lo(int lo) const {
         for (size_t l = 0; l + 1 < level_off.size(); ++l)
@@ -1944,7 +2123,7 @@ void helm3d_setup(cfmm_plan_s* P) {
                                   cudaMemcpyHostToDevice, st));
     CFMM_CUDA(cudaStreamSynchronize(st));
     for (auto f : {(const void*)k_p2x3h, (const void*)k_p2x3h_slp<false>, (const void*)k_eval3h, (const void*)k_tr3h,
-                   (const void*)k_eval3h_grad})
+                   (const void*)k_eval3h_grad, (const void*)k_tr3h_tri})
         CFMM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kH3Smem));
 }
 
@@ -2045,23 +2224,23 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
                 T.loff[1].get(), T.lent[1].get(), T.parent.get(), T.leaf.get(), S->qbox.get()};
     int nsm = 0;
     CFMM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device));
-    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
-                         int chunk) {
+    auto launch_range = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
+                            int chunk, bool tri) {
         if (nb <= 0) return;
         // the flat coaxial work (equal orders, everything in shared memory with
         // the rotation table) for the translations of the lower levels
-        int flat = (Pi == Po && Pi <= kTr3FlatMaxP && tr3h_smem(Pi, Po, true, true, true, true) <= (size_t)kH3Smem)
-                       ? 1 : 0;
-        size_t smem = tr3h_smem(Pi, Po, true, true, true, flat != 0);
+        int flat = (!tri && Pi == Po && Pi <= kTr3FlatMaxP &&
+                    tr3h_smem(Pi, Po, true, true, true, true) <= (size_t)kH3Smem) ? 1 : 0;
+        size_t smem = tri ? tr3h_smem(Pi, Po, true, false) : tr3h_smem(Pi, Po, true, true, true, flat != 0);
         int dsm = 1;
         cd* gs = nullptr;
         if (smem > (size_t)kH3Smem) {
-            smem = tr3h_smem(Pi, Po, false);
+            smem = tr3h_smem(Pi, Po, false, !tri);
             dsm = 0;
         }
         int64_t nitem = (int64_t)nb * nrhs * nchunk, G = nitem;
         int accg = 0, threads = kH3Threads;
-        if (smem > (size_t)kH3Smem) {
+        if (!tri && smem > (size_t)kH3Smem) {
             // coaxial work arrays (and for the largest orders the accumulator)
             // in global scratch: one slice per resident block, the blocks
             // stride over the work items
@@ -2103,18 +2282,45 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         int NR = Pi + Po;
         S->pre_sc.alloc((size_t)2 * std::max(npair, 1));
         S->pre_fl.alloc((size_t)(NR + 1) * std::max(npair, 1));
+        S->pre_fb.alloc((size_t)std::max(npair, 1));
         if (npair > 0) {
             k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, NR, use_h, S->pre_sc.get(),
-                                                           S->pre_fl.get());
+                                                           S->pre_fl.get(), S->pre_fb.get());
             CFMM_LAUNCHED();
         }
+        const cd* trig = nullptr;
+        if (tri && npair > 0) {
+            S->tri.alloc(tr3h_tri_size(Pi) * (size_t)npair);
+            k_tr3h_tri<<<npair, kTriThreads, tri_build_smem(Pi), st>>>(TA, Pi, npair, S->pre_fl.get(), S->tri.get());
+            CFMM_LAUNCHED();
+            trig = S->tri.get();
+        }
         k_tr3h<<<g, threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
-                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg, flat);
+                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg, flat,
+                                            S->pre_fb.get(), tri ? 1 : 0, trig);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
             k_tr3h_reduce<<<dim3(nb, nrhs), 256, 0, st>>>(pp, nchunk, nb, (int)Ko, lo, S->exp_off.get(), S->ncoef,
                                                           out);
             CFMM_LAUNCHED();
+        }
+    };
+    auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
+                         int chunk) {
+        // M2L at equal orders up to kTriMaxP: the coaxial operators of the
+        // level's pairs are built first by k_tr3h_tri (in HBM, once for every
+        // right-hand side), over box ranges whose operators fit kTriBudget
+        bool tri = mode == 1 && Pi == Po && Pi <= kTriMaxP && tri_build_smem(Pi) <= (size_t)kH3Smem;
+        if (!tri) {
+            launch_range(mode, lo, nb, Pi, Po, use_h, in, out, nchunk, chunk, false);
+            return;
+        }
+        int64_t cap = std::max<int64_t>(1, (int64_t)(kTriBudget / (tr3h_tri_size(Pi) * sizeof(cd))));
+        for (int b0 = lo; b0 < lo + nb;) {
+            int b1 = b0 + 1;
+            while (b1 < lo + nb && S->l2off[b1 + 1] - S->l2off[b0] <= cap) ++b1;
+            launch_range(mode, b0, b1 - b0, Pi, Po, use_h, in, out, nchunk, chunk, true);
+            b0 = b1;
         }
     };
     // (2) M2M: parents at level l from children at l + 1 (leaf parents get zeros
@@ -2192,6 +2398,7 @@ struct Lap3Tr {
     std::vector<int> l2off, level_off;
     DevBuf<int> qbox;
     DevBuf<cd> sc, tt;
+    DevBuf<int> fb;
 };
 
 Lap3Tr* lap3_tr_create(cfmm_plan_s* P, int Pord) {
@@ -2277,8 +2484,10 @@ void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const 
     }
     L->sc.alloc((size_t)2 * std::max(npair, 1));
     L->tt.alloc((size_t)std::max(npair, 1));
+    L->fb.alloc((size_t)std::max(npair, 1));
     if (npair > 0) {
-        k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, -1, 0, L->sc.get(), L->tt.get());
+        k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, -1, 0, L->sc.get(), L->tt.get(),
+                                                       L->fb.get());
         CFMM_LAUNCHED();
     }
     size_t K = (size_t)(Pord + 1) * (Pord + 1);
@@ -2289,7 +2498,7 @@ void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const 
     CFMM_REQUIRE(smem <= (size_t)kH3Smem, CFMM_EUNSUPPORTED, "3D Laplace translation exceeds shared memory");
     dim3 g(nb, nrhs);
     k_tr3l<<<g, kH3Threads, smem, st>>>(TA, mode, lo, Pord, dsm, TB->lsm.get(), TB->lsd.get(), TB->fact.get(),
-                                        TB->ifact.get(), in, out, qfirst, L->sc.get(), L->tt.get());
+                                        TB->ifact.get(), in, out, qfirst, L->sc.get(), L->tt.get(), L->fb.get());
     CFMM_LAUNCHED();
 }
 

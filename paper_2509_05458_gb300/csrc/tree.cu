@@ -1335,6 +1335,11 @@ void build_tree(cfmm_plan_s* P, const double* re, const double* im, const double
                 }
                 l0 = m;
             }
+            // CFMM_TOP_FIT: deeper while the 3D order at l0 exceeds the limit of
+            // the translation kernels (the order falls with the box width)
+            if (top_level_opt == -1 && dim == 3)
+                while (l0 < B && nterms_helm3d(P->sep, P->eps * 0.01, P->kappa, std::ldexp(P->W, -l0)) > kMaxP3Top)
+                    ++l0;
         }
         // boxes are stored level-major, so the leaf with the smallest box index
         // is the coarsest; when no leaf lies above l0 the forced refinement

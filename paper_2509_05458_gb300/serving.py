@@ -111,7 +111,13 @@ def estimate_bytes(req: Request) -> int:
     per_point = 8 * 4 * dim + 12 + 16 * 4          # points/normals, keys/perm, densities, results
     helm = (req.kernel & 0xF) == 1
     per_point += 2500 if helm else 400               # expansions and translation tables
-    return int(n * per_point + (96 << 20))           # + plan-construction scratch
+    extra = 0
+    if helm and dim == 3:
+        # M2L coaxial operators built ahead for a level (about 4.4 kB per point
+        # at leaf 256, growing as the leaves shrink), capped by the library's
+        # per-launch operator budget
+        extra = min(6 << 30, int(n * 4500 * 256 / max(req.leaf_size, 1)))
+    return int(n * per_point + extra + (96 << 20))   # + plan-construction scratch
 
 
 class Server:

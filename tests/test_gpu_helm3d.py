@@ -148,3 +148,26 @@ def test_helm3d_explicit_top_level(cuda, kap, eps, leaf):
         pts = g.re + 1j * g.im
         u0 = direct(3, 1, kap, pts, pts, sigma=dens[0, 0])
         assert relerr_paper(u[0], u0, dens[0].reshape(-1)) <= eps
+
+
+def test_helm3d_top_fit(cuda):
+    """CFMM_TOP_FIT: where the rule's top level needs an order above the
+    library's limit, the plan takes the first deeper level whose order fits;
+    the oracle, given that level explicitly, agrees to 1e-12."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    kap, eps, leaf = 25.0, 1e-6, 64
+    T0 = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True)
+    o0 = H.expansion_orders(T0, kap, eps)
+    assert o0[T0.l0] > GPU_MAX_ORDER_3D
+    top = T0.l0
+    while o0[top] > GPU_MAX_ORDER_3D:
+        top += 1
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2, top_level=cf.TOP_FIT)
+    assert p.info()["l0"] == top
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True, top_level=top)
+    assert list(p.orders()) == H.expansion_orders(T, kap, eps)
+    dens = densities(g.n, seed=11, nrhs=1, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
+    assert relerr_l2(u[0], uo[0]) <= 1e-12
