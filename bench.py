@@ -634,7 +634,8 @@ def run_batch(args):
     kt = mixed["kt"]
     dom = int(np.argmax(kt))
     work = dict(mixed["work"])
-    work["m2l_flops"] *= nrhs[0]
+    # right-hand-side work times nrhs; the per-pair operators once
+    work["m2l_flops"] = (work["m2l_flops"] - work["m2l_flops_shared"]) * nrhs[0] + work["m2l_flops_shared"]
     work["p2p_pairs"] *= nrhs[0]
     roof = dominant_roofline("M2L", kt[3], work, FP64_PEAK_GFLOPS)
     roof["longest_step"] = {"step": STEP_NAMES[dom], "ms": float(kt[dom])}
@@ -876,6 +877,7 @@ def work_model(p, W=None):
     off, _ = p.export_list(2)
     cnt = np.diff(off)
     m2l_flops = 0
+    m2l_shared = 0          # per-pair work done once for every right-hand side
     pairs_per_level = {}
     for l in range(inf["nlevels"]):
         npairs = int(cnt[t["level"] == l].sum())
@@ -886,9 +888,12 @@ def work_model(p, W=None):
             else:
                 m2l_flops += npairs * (m2l_flops_pair_3d(int(P[l])) if W["KERNEL"]
                                        else m2l_flops_pair_lap3d(int(P[l])))
+                if W["KERNEL"] and int(P[l]) <= 40:
+                    # the coaxial operators of these pairs are built once (k_tr3h_tri)
+                    m2l_shared += npairs * m2l_flops_coax_3d(int(P[l]))
     return {"p2p_pairs": int(inf["p2p_pairs"]), "m2l_pairs": int(inf["m2l_pairs"]),
             "m2l_pairs_per_level": pairs_per_level, "orders": [int(x) for x in P],
-            "m2l_flops": int(m2l_flops)}
+            "m2l_flops": int(m2l_flops), "m2l_flops_shared": int(m2l_shared)}
 
 
 def m2l_flops_pair_3d(P):
@@ -901,6 +906,12 @@ def m2l_flops_pair_3d(P):
     rec = 12 * P * (P + 1) * (2 * P + 1) // 6
     app = 8 * sum((1 + (m > 0)) * (P - m + 1) ** 2 for m in range(P + 1))
     return rot + rec + app
+
+
+def m2l_flops_coax_3d(P):
+    """The coaxial-recurrence part of m2l_flops_pair_3d (the per-pair operators,
+    independent of the right-hand side)."""
+    return 12 * P * (P + 1) * (2 * P + 1) // 6
 
 
 def m2l_flops_pair_lap3d(P):
