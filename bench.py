@@ -78,7 +78,7 @@ WORKLOADS = {
                            "+ 32 uneven geometries, one CUDA graph)",
                     WORKLOAD="batched 3D Helmholtz SLP k=15, eps=1e-6: plane-with-bump surface N=2e5 (Halton in "
                              "[-20,20]^2, slope 0.4) with 64 RHS, plus 32 surfaces of N log-uniform in [1e4, 2e5], "
-                             "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; separation per "
+                             "bump widths U[0.5,3], imaginary slopes U[0.2,0.8], 1 RHS each; plans at eps/10; separation per "
                              "geometry from its Lipschitz estimate; top level moved down where the rule's order "
                              "exceeds 63; leaf sizes from the autotuner per geometry"),
 }
@@ -514,6 +514,9 @@ def run_batch(args):
     torch.cuda.set_device(dev)
     geoms = [plane3d(N_POINTS, seed=0)] + plane3d_uneven()
     nrhs = [64] + [1] * (len(geoms) - 1)
+    # one digit of headroom in the plans: at eps itself the top-level
+    # cancellation of the steepest small surface reaches 1.07e-6
+    PLAN_EPS = EPS / 10
     kernel = cf.HELMHOLTZ | cf.SLP
     main = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -525,16 +528,18 @@ def run_batch(args):
     evals = sum(g.n * r for g, r in zip(geoms, nrhs))
 
     def build(precision):
-        cands = (128, 192, 256, 384) if precision == cf.MIXED else (64, 96, 128, 192)
+        # leaf sizes above 256 make the complex64 near field's error grow past
+        # eps on the steepest surfaces, so the mixed candidates stop there
+        cands = (128, 192, 256) if precision == cf.MIXED else (64, 96, 128, 192)
         plans, outs, leaves, streams = [], [], [], []
         for i, g in enumerate(geoms):
             s = torch.cuda.Stream(device=dev)
             # separation from each geometry's Lipschitz estimate; the top level
             # moved down where the rule's level needs an order above the
             # translation kernels' limit (low slopes over 40 x 40 at k = 15)
-            leaf, _ = tune_leaf_size(3, kernel, KAPPA, EPS, pts_re[i], pts_im[i], precision=precision,
+            leaf, _ = tune_leaf_size(3, kernel, KAPPA, PLAN_EPS, pts_re[i], pts_im[i], precision=precision,
                                      candidates=cands, reps=2, stream=s, sep=SEP, top_level=cf.TOP_FIT)
-            p = cf.plan(3, kernel, KAPPA, EPS, pts_re[i], pts_im[i], leaf_size=leaf, sep=SEP,
+            p = cf.plan(3, kernel, KAPPA, PLAN_EPS, pts_re[i], pts_im[i], leaf_size=leaf, sep=SEP,
                         precision=precision, stream=s, top_level=cf.TOP_FIT)
             plans.append(p)
             outs.append(torch.empty((nrhs[i], g.n), dtype=torch.complex128, device=dev))
@@ -654,7 +659,7 @@ def run_batch(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "geometries": len(geoms), "points": [g.n for g in geoms],
-                   "nrhs": nrhs, "point_evaluations_per_step": evals, "kappa": KAPPA, "eps": EPS, "sep": SEP,
+                   "nrhs": nrhs, "point_evaluations_per_step": evals, "kappa": KAPPA, "eps": EPS, "plan_eps": PLAN_EPS, "sep": SEP,
                    "leaf_sizes": mixed["leaves"], "precision": "MIXED (near field complex64, translations FP64)",
                    "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) before every timed step"},
         "accuracy": mixed["acc"],
@@ -675,6 +680,12 @@ def run_batch(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, WORKLOADS["batch3d"])
     print(json.dumps(line), flush=True)
+
+
+def _serve_summary(runs):
+    """points/s over a pass's streams and the last stream's latency quantiles."""
+    return {"value": sum(r["evaluations"] for r in runs) / sum(r["wall_s"] for r in runs),
+            "p50_s": runs[-1]["p50_s"], "p99_s": runs[-1]["p99_s"]}
 
 
 def run_serve(args):
@@ -718,13 +729,20 @@ def run_serve(args):
     _barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    for name, prec in (("auto", AUTO), ("fp64", FP64)):
-        if name == "fp64" and args.precision == "mixed":
-            continue
+    # the full stream in AUTO; the comparison with plain FP64 on its first
+    # fp64_requests requests (the same requests and arrival times), with AUTO
+    # re-run on that prefix, so both throughputs cover the same work
+    nfp = args.requests if args.fp64_requests <= 0 else min(args.fp64_requests, args.requests)
+    legs = [("auto", AUTO, args.requests)]
+    if args.precision != "mixed":
+        if nfp < args.requests:
+            legs.append(("auto_prefix", AUTO, nfp))
+        legs.append(("fp64", FP64, nfp))
+    for name, prec, nreq in legs:
         runs = []
         for k in range(args.steps):
             reqs = make_stream(args.requests, seed=7 + 1000 * k + rank, rate_hz=rate, nmin=1000, nmax=args.nmax,
-                               dims=dims, lazy=True, precision=prec)
+                               dims=dims, lazy=True, precision=prec)[:nreq]
             t0 = time.perf_counter()
             res = srv.run(reqs, keep_outputs=False)
             torch.cuda.synchronize()
@@ -766,10 +784,13 @@ def run_serve(args):
         "errors": sum(r["errors"] for r in main),
         "error_kinds": main[-1]["error_kinds"],
         "streams": main,
-        "fp64_same_stream": ({"value": sum(r["evaluations"] for r in passes["fp64"]) /
+        "fp64_same_stream": ({"requests": nfp,
+                              "value": sum(r["evaluations"] for r in passes["fp64"]) /
                               sum(r["wall_s"] for r in passes["fp64"]),
                               "p50_s": passes["fp64"][-1]["p50_s"], "p99_s": passes["fp64"][-1]["p99_s"],
-                              "errors": sum(r["errors"] for r in passes["fp64"]), "streams": passes["fp64"]}
+                              "errors": sum(r["errors"] for r in passes["fp64"]), "streams": passes["fp64"],
+                              "auto_on_same_requests": _serve_summary(passes["auto_prefix" if "auto_prefix" in passes
+                                                                          else "auto"])}
                              if "fp64" in passes else None),
         "e2e": {"value": evals * ws / wall, "unit": "points/s",
                 "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -1041,6 +1062,8 @@ def main():
                     help="helm3d: the 3D Helmholtz surface headline (with the 3D Laplace and 2D lines); lap3d / "
                          "helm2d: those alone; batch3d: the batched 3D Helmholtz line; serve: the serving loop")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests per stream")
+    ap.add_argument("--fp64-requests", type=int, default=0,
+                    help="serve: the FP64 comparison on the first N requests of the stream (0 = all)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (Hz); 0 = calibrated")
     ap.add_argument("--nmax", type=int, default=1_000_000, help="serve: largest request size")
     ap.add_argument("--slots", type=int, default=4, help="serve: requests in flight")

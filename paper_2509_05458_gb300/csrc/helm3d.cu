@@ -1251,7 +1251,8 @@ __device__ void rot_fixed_inv(const Tr3hArgs& A, const double* Dh, cd* x, cd* wb
 // of the launch is list entry qfirst + p (mode 1), child box qfirst + p
 // (mode 0) or destination box lo + p (mode 2).
 __global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, int NR, int use_h,
-                           cd* __restrict__ sc, cd* __restrict__ fl, int* __restrict__ fb) {
+                           cd* __restrict__ sc, cd* __restrict__ fl, int* __restrict__ fb, int Pm,
+                           cd* __restrict__ pwt) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npair) return;
     int b, s;
@@ -1294,8 +1295,26 @@ __global__ void k_tr3h_pre(Tr3hArgs A, int mode, int lo, int qfirst, int npair, 
         sq = csqrt_p(s2);
         e = (d[0] + mul_i(d[1])) / sq;
     }
+    cd ea = (d[2] + mul_i(sq)) / t;
     sc[2 * (size_t)p] = e;
-    sc[2 * (size_t)p + 1] = (d[2] + mul_i(sq)) / t;
+    sc[2 * (size_t)p + 1] = ea;
+    if (pwt) {
+        // e^m and e_a^m for m in [-Pm, Pm] (running products), for the
+        // translation kernel's diagonal factors
+        int W = 2 * Pm + 1;
+        cd* pe = pwt + (size_t)p * 2 * W;
+        for (int q = 0; q < 2; ++q) {
+            cd* dst = pe + q * W;
+            cd x = q ? ea : e, ix = cinv(x), v = {1, 0}, iv = {1, 0};
+            dst[Pm] = v;
+            for (int m = 1; m <= Pm; ++m) {
+                v = v * x;
+                iv = iv * ix;
+                dst[Pm + m] = v;
+                dst[Pm - m] = iv;
+            }
+        }
+    }
     if (NR < 0) {                      // Laplace: only t
         fl[p] = t;
         return;
@@ -1336,40 +1355,58 @@ __host__ __device__ inline size_t tr3h_tri_off(int P, int m) {
     for (int q = 0; q < m; ++q) o += (size_t)(P - q + 1) * (P - q + 2) / 2;
     return o;
 }
+// g_c = (-1)^c (2c + 1), the column factor of the stored coaxial triangles
+__device__ __forceinline__ double coax_g(int c) { return (c & 1) ? -(2.0 * c + 1.0) : (2.0 * c + 1.0); }
 __host__ __device__ inline size_t tr3h_tri_size(int P) { return (size_t)(P + 1) * (P + 2) * (P + 3) / 6; }
 __host__ __device__ inline size_t tr3h_flat_cols(int P) {
     return (size_t)3 * (P + 1) * (2 * P + 2) + tr3h_tri_off(P, P + 1);
 }
 
-// out_n^{+-m} = sum_{c<=n} T_{n c} a_c + (2n+1)(-1)^n sum_{r>n} T_{r n} a~_r with
-// the compact triangles tri (shared or global memory): one thread item per
-// (m, n, sign), m-major, so the lanes of a warp share a loop length
-__device__ void coax_product(int P, const cd* __restrict__ tri, const cd* __restrict__ a, const cd* __restrict__ wb,
-                             cd* __restrict__ bb) {
-    int nitem = (P + 1) * (P + 1);
+// out_n^{+-m} = sum_{c<=n} T_{n c} a_c + (2n+1)(-1)^n sum_{r>n} T_{r n} a~_r from
+// the compact triangles tri (shared or global memory) holding T'_{r c} =
+// g_c T_{r c}, g_c = (-1)^c (2c+1): with a~_c = a_c / g_c both sums read the same
+// vector a~, out_n = sum_{c<=n} T'_{n c} a~_c + sum_{r>n} T'_{r n} a~_r, one loop of
+// P - m + 1 terms for every n of a given m (row n of the triangle, then its
+// column n). One thread item per (m >= 0, n) computes both signs of m from the
+// same operator entries and writes them as the first pass of the back rotation
+// would (w+- of Phi out, see w_pass), so that pass is not run. m-major items.
+__device__ void coax_product_w(int P, const cd* __restrict__ tri, const cd* __restrict__ wb, cd* __restrict__ wout) {
+    int nitem = (P + 1) * (P + 2) / 2;
     for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
         int m = 0, rem = t;
-        while (true) {
-            int cnt = m == 0 ? P + 1 : 2 * (P - m + 1);
-            if (rem < cnt) break;
-            rem -= cnt;
+        while (rem >= P - m + 1) {
+            rem -= P - m + 1;
             ++m;
         }
-        int nout = P - m + 1;
-        int n = m + (rem % nout);
-        int mm = rem < nout ? m : -m;
+        int n = m + rem;
         const cd* T = tri + tr3h_tri_off(P, m);
-        cd sp = {0, 0};
-        const cd* Tr = T + (size_t)(n - m) * (n - m + 1) / 2 - m;    // Tr[c] = T_{n c}
-        for (int c = m; c <= n; ++c) sp = cmac(sp, Tr[c], a[nmi(c, mm)]);
-        if (n < P) {
-            cd up = {0, 0};
-            for (int r = n + 1; r <= P; ++r)
-                up = cmac(up, T[(size_t)(r - m) * (r - m + 1) / 2 + (n - m)], wb[nmi(r, mm)]);
-            double g = (n & 1) ? -(2.0 * n + 1.0) : (2.0 * n + 1.0);
-            sp += g * up;
+        const int k0 = n - m;                               // row n holds columns m..n
+        const int rowb = k0 * (k0 + 1) / 2;
+        cd sp = {0, 0}, sn = {0, 0};
+        for (int j = 0; j <= P - m; ++j) {
+            int idx, k;
+            if (j <= k0) {
+                idx = rowb + j;                             // T'_{n, m+j}
+                k = m + j;
+            } else {
+                int r = n + (j - k0);                       // T'_{r, n}
+                idx = (r - m) * (r - m + 1) / 2 + k0;
+                k = r;
+            }
+            cd tv = T[idx];
+            sp = cmac(sp, tv, wb[nmi(k, m)]);
+            if (m > 0) sn = cmac(sn, tv, wb[nmi(k, -m)]);
         }
-        bb[nmi(n, mm)] = sp;
+        // w+- of x = Phi out: x_{+-m} = i^{+-m} out_{+-m}
+        cd xp = mul_ipow(m, sp);
+        if (m == 0) {
+            wout[nmi(n, 0)] = xp;
+            continue;
+        }
+        cd xm = mul_ipow(-m, sn);
+        if (m & 1) xm = -xm;
+        wout[nmi(n, m)] = xp + xm;
+        wout[nmi(n, -m)] = xp - xm;
     }
 }
 
@@ -1388,7 +1425,7 @@ __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict
     // column c = m into the triangles (rows m..P)
     for (int t = threadIdx.x; t < (P + 1) * (P + 1); t += blockDim.x) {
         int m = t / (P + 1), r = t - m * (P + 1);
-        if (r >= m) tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2] = col(1, m)[r];
+        if (r >= m) tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2] = coax_g(m) * col(1, m)[r];
     }
     int kp = 0, kc = 1, kn = 2;
     for (int cp = 0; cp < P; ++cp) {
@@ -1421,7 +1458,7 @@ __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict
                 ++m;
             }
             int c1 = m + cp + 1, r = c1 + rem;
-            tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2 + (c1 - m)] = col(kn, m)[r];
+            tri[tr3h_tri_off(P, m) + (size_t)(r - m) * (r - m + 1) / 2 + (c1 - m)] = coax_g(c1) * col(kn, m)[r];
         }
         int k0 = kp;
         kp = kc;
@@ -1429,7 +1466,7 @@ __device__ void coax_flat(const Tr3hArgs& A, int P, int NR, const cd* __restrict
         kn = k0;
     }
     __syncthreads();
-    coax_product(P, tri, a, wb, bb);
+    coax_product_w(P, tri, wb, bb);
 }
 
 // The coaxial operators of the M2L pairs of a launch (equal orders P), built
@@ -1477,7 +1514,7 @@ __global__ void k_tr3h_tri(Tr3hArgs A, int P, int npair, const cd* __restrict__ 
         // column c = m of every m into the triangles (rows m..P)
         for (int t = threadIdx.x; t < (P + 1) * (P + 1); t += blockDim.x) {
             int m = t / (P + 1), r = t - m * (P + 1);
-            if (r >= m) T[moff[m] + (r - m) * (r - m + 1) / 2] = col(1, m)[r];
+            if (r >= m) T[moff[m] + (r - m) * (r - m + 1) / 2] = coax_g(m) * col(1, m)[r];
         }
         int kp = 0, kc = 1;
         for (int cp = 0; cp < P; ++cp) {
@@ -1509,7 +1546,7 @@ __global__ void k_tr3h_tri(Tr3hArgs A, int P, int npair, const cd* __restrict__ 
                     ++m;
                 }
                 int c1 = m + cp + 1, r = c1 + rem;
-                T[moff[m] + (r - m) * (r - m + 1) / 2 + (c1 - m)] = col(kp, m)[r];
+                T[moff[m] + (r - m) * (r - m + 1) / 2 + (c1 - m)] = coax_g(c1) * col(kp, m)[r];
             }
             int k0 = kp;
             kp = kc;
@@ -1526,7 +1563,7 @@ __global__ void k_tr3h_tri(Tr3hArgs A, int P, int npair, const cd* __restrict__ 
 // in global scratch for large orders), then (when it fits) the Dh table.
 __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int use_h, int d_in_smem,
                        cd* __restrict__ gscr, const cd* __restrict__ in, cd* __restrict__ out, int chunk,
-                       cd* __restrict__ part, int qfirst, const cd* __restrict__ sc, const cd* __restrict__ fl,
+                       cd* __restrict__ part, int qfirst, const cd* __restrict__ pwt, const cd* __restrict__ fl,
                        int nrhs, int nchunk, int acc_glob, int flat, const int* __restrict__ fb,
                        int ops_g, const cd* __restrict__ trig) {
     extern __shared__ cd sm[];
@@ -1608,18 +1645,10 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         if (!ops_g)
             for (int l = threadIdx.x; l <= NR; l += blockDim.x) f[l] = fl[(size_t)p * (NR + 1) + l];
         {
-            // powers of e, e_a and of their inverses, m in [-Pm, Pm]: warp w < 4
-            // takes one of the four sequences, a lane per |m|
-            int w4 = threadIdx.x >> 5, ln = threadIdx.x & 31;
-            if (w4 < 4) {
-                cd x = sc[2 * (size_t)p + (w4 >> 1)];
-                if (w4 & 1) x = cinv(x);
-                cd* dst = (w4 >> 1) ? pwa : pwe;
-                for (int m = ln; m <= Pm; m += 32) {
-                    cd v = cpow_int(x, m);
-                    dst[Pm + ((w4 & 1) ? -m : m)] = v;
-                }
-            }
+            // powers of e and e_a, m in [-Pm, Pm], from the prologue (pwe and pwa
+            // are adjacent)
+            const cd* pt = pwt + (size_t)p * 2 * (2 * Pm + 1);
+            for (int k = threadIdx.x; k < 2 * (2 * Pm + 1); k += blockDim.x) pwe[k] = pt[k];
         }
         __syncthreads();
         for (int m = threadIdx.x - Pm; m <= Pm; m += blockDim.x) {
@@ -1667,7 +1696,7 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         }
         __syncthreads();
         if (ops_g) {
-            coax_product(Po, trig + (size_t)p * tr3h_tri_size(Po), a, wb, bb);
+            coax_product_w(Po, trig + (size_t)p * tr3h_tri_size(Po), wb, bb);
         } else if (flat) {
             coax_flat(A, Po, NR, sect, cols, a, wb, bb);
         } else
@@ -1722,9 +1751,14 @@ __global__ void k_tr3h(Tr3hArgs A, int mode, int lo, int nb, int Pi, int Po, int
         }
         __syncthreads();
         // (3) back rotation: x = Phi c'; y = D x; x' = S E(1/e_a) y; u = D x'; acc += E(1/e) i^m u
-        w_pass(A.knm, bb, wb, Po, 1, 0, nullptr, Pm);
-        __syncthreads();
-        d_pass(Dh, A.Dhoff, wb, a, Po, 0, 0, nullptr, Pm, 0);
+        // (the flat and operator paths left w+- of Phi c' in bb already)
+        if (ops_g || flat) {
+            d_pass(Dh, A.Dhoff, bb, a, Po, 0, 0, nullptr, Pm, 0);
+        } else {
+            w_pass(A.knm, bb, wb, Po, 1, 0, nullptr, Pm);
+            __syncthreads();
+            d_pass(Dh, A.Dhoff, wb, a, Po, 0, 0, nullptr, Pm, 0);
+        }
         __syncthreads();
         w_pass(A.knm, a, wb, Po, 0, 1, pwai, Pm);
         __syncthreads();
@@ -1955,6 +1989,7 @@ struct Helm3dState {
     DevBuf<int> qbox;            // owner box of each List-2 entry
     DevBuf<cd> pre_sc, pre_fl;   // per-pair prologue of a translation launch
     DevBuf<int> pre_fb;          // per pair: fixed frame k, or -1
+    DevBuf<cd> pre_pw;           // per pair: e^m, e_a^m for m in [-Pm, Pm]
     DevBuf<cd> tri;              // coaxial operators of the M2L pairs of a launch range
     std::vector<int> level_off;
     int lvl_of_lo(int lo) const {
@@ -2283,9 +2318,11 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
         S->pre_sc.alloc((size_t)2 * std::max(npair, 1));
         S->pre_fl.alloc((size_t)(NR + 1) * std::max(npair, 1));
         S->pre_fb.alloc((size_t)std::max(npair, 1));
+        int Pmx = std::max(Pi, Po);
+        S->pre_pw.alloc((size_t)2 * (2 * Pmx + 1) * std::max(npair, 1));
         if (npair > 0) {
             k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, NR, use_h, S->pre_sc.get(),
-                                                           S->pre_fl.get(), S->pre_fb.get());
+                                                           S->pre_fl.get(), S->pre_fb.get(), Pmx, S->pre_pw.get());
             CFMM_LAUNCHED();
         }
         const cd* trig = nullptr;
@@ -2296,7 +2333,7 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
             trig = S->tri.get();
         }
         k_tr3h<<<g, threads, smem, st>>>(TA, mode, lo, nb, Pi, Po, use_h, dsm, gs, in, out, chunk, pp,
-                                            qfirst, S->pre_sc.get(), S->pre_fl.get(), nrhs, nchunk, accg, flat,
+                                            qfirst, S->pre_pw.get(), S->pre_fl.get(), nrhs, nchunk, accg, flat,
                                             S->pre_fb.get(), tri ? 1 : 0, trig);
         CFMM_LAUNCHED();
         if (nchunk > 1) {
@@ -2487,7 +2524,7 @@ void lap3_tr_launch(Lap3Tr* L, cfmm_plan_s* P, int mode, int l, int Pord, const 
     L->fb.alloc((size_t)std::max(npair, 1));
     if (npair > 0) {
         k_tr3h_pre<<<(npair + 127) / 128, 128, 0, st>>>(TA, mode, lo, qfirst, npair, -1, 0, L->sc.get(), L->tt.get(),
-                                                       L->fb.get());
+                                                       L->fb.get(), 0, nullptr);
         CFMM_LAUNCHED();
     }
     size_t K = (size_t)(Pord + 1) * (Pord + 1);
