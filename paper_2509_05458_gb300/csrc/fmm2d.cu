@@ -1237,10 +1237,10 @@ void fmm2d_setup(cfmm_plan_s* P) {
             for (int l = 0; l < T.nlevels; ++l) {
                 S->lvl_chunk0[l] = (int)cb.size();
                 S->lvl_part0[l] = pslot;
-                // chunk length: at most kM2LChunk entries, shorter when the level has
-                // too few entries to give every SM two blocks (a coarse top level)
-                int ent = loff[T.level_off[l + 1]] - loff[T.level_off[l]];
-                int clen = std::max(4, std::min(kM2LChunk, ent / (2 * num_sms())));
+                // chunks of kM2LChunk entries (shorter chunks fill more SMs at a coarse
+                // top level but spread each block's fixed per-coefficient work over
+                // fewer sources: measured slower)
+                int clen = kM2LChunk;
                 for (int b = T.level_off[l]; b < T.level_off[l + 1]; ++b) {
                     bc0[b] = (int)cb.size();
                     if (l < S->l0) continue;
