@@ -399,7 +399,7 @@ def rooflines(W, r):
     m2l["achieved"] = work["m2l_flops"] / (kt[3] / 1e3) / 1e9 if kt[3] > 0 else None
     m2l["frac"] = m2l["achieved"] / FP64_PEAK_GFLOPS if m2l["achieved"] else None
     if W["DIM"] == 3 and W["KERNEL"]:
-        prof = profile_figures("ncu_tr3h_helm3d_k10_n1e6.txt", TR3H_SOURCES)
+        prof = profile_figures("m2l_traffic_helm3d_k10_n1e6.txt", TR3H_SOURCES)
         if prof and "dram_bytes_per_apply" in prof:
             m2l["traffic"] = int(float(prof["dram_bytes_per_apply"]))
             m2l["traffic_source"] = prof["_path"]

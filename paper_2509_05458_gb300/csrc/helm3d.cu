@@ -70,6 +70,7 @@ constexpr int kM2LChunk3 = 32;       // List-2 entries per block when a list is 
 constexpr int kTr3FlatMaxP = 23;     // largest order of the flat coaxial work
 constexpr double kDegenTol = 1e-8;   // |d1^2 + d2^2| <= this * sum |d_i|^2: fixed-frame translation
 constexpr int kTriMaxP = 40;         // largest M2L order whose coaxial operators are built ahead (k_tr3h_tri)
+constexpr int kTriMaxPMulti = 56;    // the same with several right-hand sides (operators shared by all)
 constexpr int kTriThreads = 128;     // threads of k_tr3h_tri
 constexpr size_t kTriBudget = (size_t)6 << 30;   // bytes of operators per M2L launch range
 
@@ -2344,10 +2345,12 @@ void helm3d_apply(cfmm_plan_s* P, const cd* sigma, const cd* tau, int64_t dstrid
     };
     auto launch_tr = [&](int mode, int lo, int nb, int Pi, int Po, int use_h, const cd* in, cd* out, int nchunk,
                          int chunk) {
-        // M2L at equal orders up to kTriMaxP: the coaxial operators of the
-        // level's pairs are built first by k_tr3h_tri (in HBM, once for every
-        // right-hand side), over box ranges whose operators fit kTriBudget
-        bool tri = mode == 1 && Pi == Po && Pi <= kTriMaxP && tri_build_smem(Pi) <= (size_t)kH3Smem;
+        // M2L at equal orders up to kTriMaxP (kTriMaxPMulti with several
+        // right-hand sides): the coaxial operators of the level's pairs are
+        // built first by k_tr3h_tri (in HBM, once for every right-hand side),
+        // over box ranges whose operators fit kTriBudget
+        bool tri = mode == 1 && Pi == Po && (Pi <= kTriMaxP || (nrhs > 1 && Pi <= kTriMaxPMulti)) &&
+                   tri_build_smem(Pi) <= (size_t)kH3Smem && tr3h_smem(Pi, Po, false, false) <= (size_t)kH3Smem;
         if (!tri) {
             launch_range(mode, lo, nb, Pi, Po, use_h, in, out, nchunk, chunk, false);
             return;

@@ -171,3 +171,22 @@ def test_helm3d_top_fit(cuda):
     u = p.apply(to_dev(dens, cuda)).cpu().numpy()
     uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
     assert relerr_l2(u[0], uo[0]) <= 1e-12
+
+
+def test_helm3d_operators_built_ahead_multi_rhs(cuda):
+    """Several right-hand sides at a top-level order above 40 (P = 50 at the
+    explicit top level 2, kappa = 20): the M2L operators are built once for all
+    right-hand sides; each right-hand side matches the oracle to 1e-12."""
+    import paper_2509_05458_gb300 as cf
+    g = _geom()
+    kap, eps, leaf, top = 20.0, 1e-6, 64, 2
+    p = gpu_plan(cf, g, cf.HELMHOLTZ, kap, eps, cuda, leaf, sep=2, top_level=top)
+    T = tr.build_tree(g.re, g.im, leaf, k=2, kappa=kap, eps=eps, helmholtz=True, top_level=top)
+    orders = H.expansion_orders(T, kap, eps)
+    assert 40 < orders[T.l0] <= 56
+    assert list(p.orders()) == orders
+    dens = densities(g.n, seed=12, nrhs=3, ncomp=1)
+    u = p.apply(to_dev(dens, cuda)).cpu().numpy()
+    uo, _ = H.apply(g.re, g.im, kap, eps, leaf, k=2, sigma=dens[:, 0], T=T, coaxial="exact")
+    for r in range(3):
+        assert relerr_l2(u[r], uo[r]) <= 1e-12
