@@ -725,6 +725,9 @@ def run_serve(args):
         svc = (time.perf_counter() - t0) / len(sample)
         rate = 0.8 / svc
         calib = {"sample_requests": len(sample), "mean_service_s": svc, "rate_hz": rate}
+        # progress on stderr (a stream at 80% load runs about 1.25 x its total
+        # service time, so a cut-off run still leaves these figures)
+        print(json.dumps({"serve_calibration": calib}), file=sys.stderr, flush=True)
     passes = {}
     clocks = ClockSampler(local)
     _barrier(ws)
@@ -752,6 +755,9 @@ def run_serve(args):
             st["evaluations"] = sum(r.points for r in res if r.error is None)
             st["evaluations_requested"] = sum(r.n * r.nrhs for r in reqs)
             runs.append(st)
+            print(json.dumps({"serve_pass": name, "requests": nreq, "wall_s": wall,
+                              "points_per_s": st["evaluations"] / wall if wall > 0 else None,
+                              "p50_s": st.get("p50_s"), "p99_s": st.get("p99_s")}), file=sys.stderr, flush=True)
         passes[name] = runs
     _barrier(ws)
     clk = clocks.stop()
