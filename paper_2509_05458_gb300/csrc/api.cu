@@ -266,17 +266,6 @@ void ensure_device_tables() {
     done[dev] = 1;
 }
 
-int num_sms() {
-    static std::mutex mu;
-    static std::vector<int> cache;
-    int dev = 0;
-    CFMM_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
-    if (!cache[dev]) CFMM_CUDA(cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev));
-    return cache[dev];
-}
-
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;

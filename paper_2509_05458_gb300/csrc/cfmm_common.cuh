@@ -261,8 +261,6 @@ struct LagRule {
 };
 const LagRule& host_lag_rule();
 void ensure_device_tables();   // per device, idempotent
-// streaming multiprocessors of the current device (cached per device)
-int num_sms();
 
 // Tree and list storage of a plan (device pointers unless noted).
 struct TreeDev {
