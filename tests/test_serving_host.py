@@ -47,6 +47,21 @@ def test_memory_estimate_grows_with_size_and_kernel():
     assert estimate_bytes(req(100_000, 1)) > big     # Helmholtz tables cost more
 
 
+def test_memory_estimate_counts_3d_helmholtz_operators():
+    """3D Helmholtz plans hold the M2L coaxial operators of a level (more with
+    smaller leaves), bounded by the library's per-launch operator budget."""
+    def req(n, dim, kernel, leaf):
+        x = np.zeros((n, dim))
+        return Request(0, dim, kernel, 5.0, 1e-6, x, x, [np.zeros((1, n), complex)], leaf_size=leaf)
+    lap, helm = estimate_bytes(req(200_000, 3, 0, 64)), estimate_bytes(req(200_000, 3, 1, 64))
+    assert helm - lap > 200_000 * 4500       # the operators on top of the expansions
+    assert estimate_bytes(req(200_000, 3, 1, 32)) > helm > estimate_bytes(req(200_000, 3, 1, 256))
+    huge = estimate_bytes(req(10_000_000, 3, 1, 16)) - estimate_bytes(req(10_000_000, 3, 0, 16))
+    assert huge < 10_000_000 * 2500 + (6 << 30) + (1 << 20)   # operator term capped at 6 GiB
+    # 2D plans have no such term
+    assert estimate_bytes(req(200_000, 2, 1, 64)) < helm
+
+
 def test_summary_percentiles_and_errors():
     res = [Result(i, [np.zeros(10, complex)], arrival=0.0, admitted=0.0, done=float(i + 1)) for i in range(100)]
     res.append(Result(100, [], 0.0, 0.0, 1.0, error="CfmmError: cfmm error -1: eps must be in [1e-15, 0.1]"))
